@@ -1,0 +1,17 @@
+"""FP64 CPU oracle for the randomized QB / RSVD / ID / CUR path.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, plain reference the CUDA
+library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import it; the library package never
+does, and it shares no code, tables or helpers with the CUDA sources.
+
+Contents
+--------
+philox   counter-based Philox4x32-10 stream and the Box-Muller Gaussian test
+         matrix Omega (written from Salmon et al., SC'11, and Box & Muller 1958).
+rsvd     the algorithms of Voronin & Martinsson (RSVDPACK), step by step in
+         FP64: orth (Householder QR), the range finder with power scheme,
+         the QB step, Algorithm 5 (RSVD version II), k-step column-pivoted QR,
+         the QB-route randomized ID and the CUR of Algorithm 3.
+"""
+from . import philox, rsvd  # noqa: F401

@@ -1,0 +1,242 @@
+"""Plain FP64 reference of the randomized QB / RSVD / ID / CUR path (oracle side).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Every function takes the
+stored input promoted to float64 and follows the paper's steps in the paper's
+order; library primitives (matmul, LAPACK Householder QR, LAPACK SVD,
+triangular solve) serve as single steps.  Nothing here is blocked, fused or
+reordered.
+
+Readings of points the paper leaves open (each is also taken by the CUDA side):
+* orth(Y) is the Q of a Householder QR with diag(R) >= 0 (Sec. 2.1 defines orth
+  as an unpivoted QR; the sign makes Q unique).
+* The power scheme re-orthonormalises before every product with A or A^T
+  (s = 1 in Alg. 5; Sec. 3.2); general s follows Alg. 5's mod tests.
+* Singular values are returned in descending order; each pair (u_j, v_j) is
+  sign-flipped so that the entry of largest magnitude of v_j is positive
+  (ties: lowest index).
+* Column-pivoted QR runs k steps only; the pivot is the column of largest
+  exactly recomputed residual norm, ties broken by the lowest original column
+  index; columns are exchanged like LAPACK (pivot position j <-> p).
+* T = S11^{-1} S12 by plain back substitution (Sec. 3.5 mentions an unspecified
+  "stabilized version"; it is not used).
+"""
+import numpy as np
+import scipy.linalg as sla
+
+from . import philox
+
+
+# ---------------------------------------------------------------------------
+# orth: unpivoted QR (Sec. 2.1 notation; Fig. 1 step 3)
+# ---------------------------------------------------------------------------
+def qr_pos(Y):
+    """Economic Householder QR of Y (m x l, m >= l) with diag(R) >= 0."""
+    Q, R = np.linalg.qr(np.asarray(Y, dtype=np.float64), mode="reduced")
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d[None, :], R * d[:, None]
+
+
+def orth(Y):
+    return qr_pos(Y)[0]
+
+
+# ---------------------------------------------------------------------------
+# Range finder with the power scheme, and the QB step (Alg. 5; Sec. 3.2, 3.4)
+# ---------------------------------------------------------------------------
+def range_finder(A, l, q, seed, rounding="f64", s=1, Omega=None):
+    """Q (m x l) with orthonormal columns spanning (A A^*)^q A Omega (Alg. 5)."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[1]
+    if Omega is None:
+        Omega = philox.omega(n, l, seed, rounding)
+    Y = A @ Omega                                   # samples Y = A R
+    for j in range(1, q + 1):
+        if (2 * j - 2) % s == 0:
+            Y = orth(Y)
+        Z = A.T @ Y                                 # Z = A^* Y
+        if (2 * j - 1) % s == 0:
+            Z = orth(Z)
+        Y = A @ Z                                   # Y = A Z
+    return orth(Y)                                  # [Q, ~] = qr(Y, 0)
+
+
+def qb(A, k, p, q, seed, rounding="f64", s=1, Omega=None):
+    """Q (m x l) and Bt = A^* Q (n x l) = B^* with B = Q^* A (Alg. 5; Fig. 1 step 4)."""
+    A = np.asarray(A, dtype=np.float64)
+    Q = range_finder(A, k + p, q, seed, rounding, s, Omega)
+    Bt = A.T @ Q
+    return Q, Bt
+
+
+# ---------------------------------------------------------------------------
+# RSVD version II (Alg. 5; Sec. 3.4)
+# ---------------------------------------------------------------------------
+def normalize_signs(U, V):
+    """Flip (u_j, v_j) so the largest-magnitude entry of v_j is positive."""
+    U = U.copy()
+    V = V.copy()
+    for j in range(V.shape[1]):
+        i = int(np.argmax(np.abs(V[:, j])))        # first maximum = lowest index
+        if V[i, j] < 0:
+            U[:, j] = -U[:, j]
+            V[:, j] = -V[:, j]
+    return U, V
+
+
+def svd_from_qb(Q, Bt, k):
+    """Steps after the QB step of Alg. 5: QR of Bt, SVD of the l x l R-hat, lift."""
+    Qh, Rh = qr_pos(Bt)                             # [Q^, R^] = qr(Bt, 0)
+    Uh, S, VhT = np.linalg.svd(Rh)                  # R^ = U^ Sigma V^*
+    Vh = VhT.T
+    U = Q @ Vh[:, :k]                               # U_k = Q V^
+    V = Qh @ Uh[:, :k]                              # V_k = Q^ U^
+    U, V = normalize_signs(U, V)
+    return U, S[:k].copy(), V, S
+
+
+def rsvd(A, k, p, q, seed, rounding="f64", s=1, Omega=None):
+    """Rank-k approximate SVD A ~ U diag(S) V^T by Alg. 5 (RSVD version II).
+
+    Returns U (m x k), S (k,), V (n x k) and the l singular values of R-hat.
+    """
+    Q, Bt = qb(A, k, p, q, seed, rounding, s, Omega)
+    return svd_from_qb(Q, Bt, k)
+
+
+# ---------------------------------------------------------------------------
+# Column-pivoted QR, k steps (Sec. 2.3; Alg. 1 first step)
+# ---------------------------------------------------------------------------
+def cpqr(M, ksteps):
+    """k steps of Householder QR with column pivoting on M (r x n).
+
+    Returns
+      perm   int64 (n,): M[:, perm] ~ Q S, i.e. P = I(:, perm)
+      S      (ksteps, n) float64: first ksteps rows of the triangular factor,
+             columns in pivot (position) order; S[:, :ksteps] is upper triangular
+      S22    (r - ksteps, n - ksteps): the remainder block after ksteps steps
+      gaps   (ksteps,): relative gap (nu1 - nu2) / nu1 between the largest and
+             second-largest residual column norms at each step (inf if single)
+    """
+    W = np.array(M, dtype=np.float64, copy=True)
+    r, n = W.shape
+    if not (0 <= ksteps <= min(r, n)):
+        raise ValueError("ksteps out of range")
+    perm = np.arange(n, dtype=np.int64)
+    gaps = np.empty(ksteps)
+    for j in range(ksteps):
+        nrm2 = np.sum(W[j:, j:] ** 2, axis=0)       # exact residual norms^2
+        vmax = nrm2.max()
+        cand = np.flatnonzero(nrm2 == vmax)
+        pos = j + int(cand[np.argmin(perm[j + cand])])
+        if nrm2.size > 1:
+            nu = np.sqrt(np.sort(nrm2)[::-1])
+            gaps[j] = (nu[0] - nu[1]) / nu[0] if nu[0] > 0 else 0.0
+        else:
+            gaps[j] = np.inf
+        if pos != j:                                # exchange positions j and pos
+            W[:, [j, pos]] = W[:, [pos, j]]
+            perm[[j, pos]] = perm[[pos, j]]
+        x = W[j:, j].copy()
+        normx = np.sqrt(np.sum(x * x))
+        if normx == 0.0:
+            continue
+        beta = -normx if x[0] >= 0 else normx       # H x = beta e1
+        v = x
+        v[0] -= beta
+        vv = np.dot(v, v)
+        if vv > 0:
+            W[j:, j:] -= np.outer(v, (2.0 / vv) * (v @ W[j:, j:]))
+        W[j, j] = beta
+        W[j + 1:, j] = 0.0
+    return perm, W[:ksteps, :].copy(), W[ksteps:, ksteps:].copy(), gaps
+
+
+# ---------------------------------------------------------------------------
+# One-sided ID (Sec. 2.4; Alg. 1) and the QB-route randomized ID (Sec. 3.5)
+# ---------------------------------------------------------------------------
+def id_from_matrix(M, k):
+    """Column ID of M: J (n,) and T = S11^{-1} S12 (k x (n-k))."""
+    perm, S, _, gaps = cpqr(M, k)
+    S11 = S[:, :k]
+    S12 = S[:, k:]
+    T = sla.solve_triangular(S11, S12, lower=False)
+    return perm, T, gaps
+
+
+def interpolation_matrix_t(J, T, k):
+    """V^* = [I_k  T] P^T as a dense k x n array (Eq. for V in Sec. 2.4)."""
+    n = J.size
+    Vs = np.zeros((k, n))
+    Vs[np.arange(k), J[:k]] = 1.0
+    Vs[:, J[k:]] = T
+    return Vs
+
+
+def rid(A, k, p, q, seed, rounding="f64", s=1, Omega=None):
+    """Randomized ID through the QB step: ID of B = Q^* A (Sec. 3.5, last part).
+
+    Returns J (n,), T (k x (n-k)), pivot gaps, and (Q, Bt).
+    """
+    Q, Bt = qb(A, k, p, q, seed, rounding, s, Omega)
+    J, T, gaps = id_from_matrix(Bt.T, k)
+    return J, T, gaps, (Q, Bt)
+
+
+# ---------------------------------------------------------------------------
+# CUR through the two-sided ID (Sec. 2.5; Alg. 2, Alg. 3; Sec. 3.6)
+# ---------------------------------------------------------------------------
+def cur_from_id(A, J, T, k):
+    """Row ID of C = A(:, J[:k]) by k-step CPQR of C^*, then U = V^* R^dagger.
+
+    R^dagger is taken through the Householder QR of R^* = Q_R R_R:
+    R^dagger = Q_R R_R^{-T}.  Returns I (k,), U (k x k), row gaps.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    C = A[:, J[:k]]
+    Jr, _, _, rgaps = cpqr(C.T, k)
+    I = Jr[:k].copy()
+    R = A[I, :]
+    Vs = interpolation_matrix_t(J, T, k)
+    QR_, RR = qr_pos(R.T)
+    Mk = Vs @ QR_
+    U = sla.solve_triangular(RR, Mk.T, lower=False).T   # U R_R^T = V^* Q_R
+    return I, U, rgaps
+
+
+def rcur(A, k, p, q, seed, rounding="f64", s=1, Omega=None):
+    """Randomized CUR: A ~ A(:, Jc) U A(Ir, :).  Returns Jc (k,), Ir (k,), U,
+    plus the full column permutation J, T and both gap arrays."""
+    J, T, cgaps, _ = rid(A, k, p, q, seed, rounding, s, Omega)
+    I, U, rgaps = cur_from_id(A, J, T, k)
+    return J[:k].copy(), I, U, J, T, cgaps, rgaps
+
+
+# ---------------------------------------------------------------------------
+# Error measures used by the tests and the bench (plain definitions)
+# ---------------------------------------------------------------------------
+def rel_err_svd(A, U, S, V, block=4096):
+    """||A - U diag(S) V^T||_F / ||A||_F in FP64, row block by row block."""
+    A = np.asarray(A)
+    num = 0.0
+    den = 0.0
+    VS = np.asarray(V, dtype=np.float64) * np.asarray(S, dtype=np.float64)[None, :]
+    for i0 in range(0, A.shape[0], block):
+        Ab = np.asarray(A[i0:i0 + block], dtype=np.float64)
+        D = Ab - np.asarray(U[i0:i0 + block], dtype=np.float64) @ VS.T
+        num += float(np.sum(D * D))
+        den += float(np.sum(Ab * Ab))
+    return np.sqrt(num / den)
+
+
+def rel_err_id(A, J, T, k):
+    A = np.asarray(A, dtype=np.float64)
+    Vs = interpolation_matrix_t(J, T, k)
+    D = A - A[:, J[:k]] @ Vs
+    return np.linalg.norm(D) / np.linalg.norm(A)
+
+
+def rel_err_cur(A, Jc, Ir, U):
+    A = np.asarray(A, dtype=np.float64)
+    D = A - A[:, Jc] @ U @ A[Ir, :]
+    return np.linalg.norm(D) / np.linalg.norm(A)
