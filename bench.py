@@ -1,0 +1,343 @@
+"""Benchmark: randomized SVD + ID + CUR from one QB sketch on GB300.
+
+One step = the whole path on one synthetic matrix: range finder with q power
+iterations (A Omega with Omega generated in-kernel, CholeskyQR re-
+orthonormalisation, A^T Y, A Z), the QB step Bt = A^T Q, the small SVD of B
+(Alg. 5), the k-step pivoted QR of B for the ID and the CUR (Alg. 3).
+
+Workload (default): FP32 A = G1 diag(1/j) G2^T + 1e-4 N(0,1), m = 50000,
+n = 20000, r = 2000, k = 200, p = 20, q = 2 (4 GB row-major, larger than L2).
+
+JSON line fields: value = algorithmic TFLOP/s of the step (flop count of every
+step of the path, dominated by the 2q+2 passes over A at 2 m n l flops each)
+divided by the measured step time; roofline = the dominant tensor-core kernel
+class (CUDA events recorded by the library on its own stream) against the
+measured HBM copy bandwidth; e2e = the same metric with A copied from pinned
+host memory and the outputs copied back inside the timed region;
+cpu_baseline = the FP64 oracle on a bounded sample of the same recipe.
+With --impl reference the oracle itself is the timed arm (host cores).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QB-sketch TFLOP/s & % roofline; mixed-prec/batched vs FP32 at equal rel. error"
+UNIT = "TFLOP/s"
+
+
+def step_flops(m, n, k, p, q, with_id=True, with_cur=True):
+    """Algorithmic flops of one step (plain definitions, no split products)."""
+    l = k + p
+    f = 2.0 * m * n * l * (2 * q + 2)                       # A Omega, power steps, Bt
+    n_orth_m = q + 1                                        # orth of m x l samples
+    n_orth_n = q + 1                                        # orth of n x l (power + Bt)
+    f += n_orth_m * 2 * 2.0 * m * l * l + n_orth_n * 2 * 2.0 * n * l * l   # CholQR2
+    f += 2.0 * (m + n) * l * k                              # lift U = Q Vh, V = Qh Uh
+    f += 3.0 * l ** 3 * 8                                   # Jacobi sweeps (~8)
+    if with_id:
+        f += 4.0 * k * l * n + k * k * (n - k)              # CPQR(B), T = S11^-1 S12
+    if with_cur:
+        f += 4.0 * k * k * m + 4.0 * n * k * k + 2.0 * k * k * (n - k)
+    return f
+
+
+def a_pass_bytes(m, n, elem=4):
+    return float(m) * n * elem
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        med = float(np.median(sm)) if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(cfg, frac_rows=25, frac_cols=5, budget_s=30.0):
+    """The FP64 oracle on a bounded sample of the same recipe (m/frac_rows x n/frac_cols)."""
+    from oracle import rsvd as orc
+    from synth import make_matrix_np, spectrum
+    m = max(cfg["m"] // frac_rows, cfg["k"] + cfg["p"] + 8)
+    n = max(cfg["n"] // frac_cols, cfg["k"] + cfg["p"] + 8)
+    r = min(cfg["r"], n)
+    A = make_matrix_np(m, n, spectrum(cfg["spectrum"], r), noise=cfg["noise"],
+                       seed=cfg["a_seed"], dtype=cfg["dtype"]).astype(np.float64)
+    k, p, q = cfg["k"], cfg["p"], cfg["q"]
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        orc.rsvd(A, k, p, q, cfg["omega_seed"], rounding="bf16")
+        orc.rcur(A, k, p, q, cfg["omega_seed"], rounding="bf16")
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    fl = step_flops(m, n, k, p, q)
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return {"value": fl / dt / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "FP64 numpy oracle (OpenBLAS threads on all affinity cores), RSVD + ID + "
+                      "CUR of the same recipe at m=%d n=%d k=%d p=%d q=%d (1/%d of the rows, "
+                      "1/%d of the columns), %.2f s per step" % (m, n, k, p, q, frac_rows,
+                                                                 frac_cols, dt)}
+
+
+def run_reference(args, cfg, world, rank):
+    """--impl reference: the oracle on the host cores, rank 0 only."""
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    samples = []
+    for _ in range(max(1, min(args.steps, 3))):
+        samples.append(cpu_oracle_sample(cfg, budget_s=20.0))
+    v = float(np.median([s["value"] for s in samples]))
+    base = samples[0]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": len(samples), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "sample": base["sample"]},
+            "cpu_baseline": dict(base, value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2_f32_50000x20000")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    from synth import config as get_config
+    cfg = get_config(args.config)
+    cfg["name"] = args.config
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, cfg, world, rank)
+
+    import torch
+    import paper_1502_05366_gb300 as rs
+    from synth import make_matrix_torch, spectrum
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m, n, k, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["q"]
+    tdt = {"float32": torch.float32, "float64": torch.float64}[cfg["dtype"]]
+    A = make_matrix_torch(m, n, spectrum(cfg["spectrum"], cfg["r"]), noise=cfg["noise"],
+                          seed=cfg["a_seed"] + rank, dtype=cfg["dtype"], device=dev)
+    torch.cuda.synchronize()
+    plan = rs.Plan(m, n, k, p, q, tdt, dev)
+    seed = cfg["omega_seed"]
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.run(A, seed)
+    torch.cuda.synchronize()
+    rs.check_info(plan.info, "warmup")
+
+    # ---------------- timed region (device-resident inputs) ----------------
+    rs.trace_enable(True)
+    rs.trace_read()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = rs.kernel_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.run(A, seed)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = rs.kernel_launch_count() - launches0
+    clk = clocks.stop()
+    trace = rs.trace_read()
+    rs.trace_enable(False)
+    rs.check_info(plan.info, "timed steps")
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms, world, dev)
+    flops = step_flops(m, n, k, p, q)
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # ---------------- roofline of the dominant kernel class ----------------
+    peaks, peak_kind = load_peaks()
+    apass = {c: trace[c] for c in ("a_omega", "a_w", "at_w")}
+    dom = max(trace, key=lambda c: trace[c][0])
+    roof = None
+    if dom in apass and trace[dom][1] > 0:
+        avg_ms = trace[dom][0] / trace[dom][1]
+        achieved = a_pass_bytes(m, n) / (avg_ms * 1e-3) / 1e9
+        roof = {"kernel": "tc_gemm_kernel (%s)" % dom, "bound": "hbm",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peak_kind + " (STREAM-style copy)",
+                "avg_launch_ms": avg_ms, "launches": trace[dom][1]}
+    breakdown = {c: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                 for c, v in trace.items()}
+    pass_ms = sum(v[0] for c, v in trace.items() if c in apass) / args.steps
+    qb_flops = 2.0 * m * n * (k + p) * (2 * q + 2)
+
+    # ---------------- end to end: host A in, host outputs out ----------------
+    A_host = A.cpu().pin_memory()
+    outs = [t for t in (plan.U, plan.S, plan.V, plan.J, plan.T, plan.Jc, plan.Ir, plan.Ucur)
+            if t is not None]
+    outs_host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+    h2d = A_host.numel() * A_host.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in outs)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        A.copy_(A_host, non_blocking=True)
+        plan.run(A, seed)
+        for h, d in zip(outs_host, outs):
+            h.copy_(d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.e2e_steps, world, dev)
+    e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_oracle_sample(cfg)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "m": m, "n": n, "k": k, "p": p, "q": q,
+                       "spectrum": "sigma_j = 1/j, r = %d, noise %g" % (cfg["r"], cfg["noise"]),
+                       "precision": "fp32 storage; split-bf16 tcgen05 products, fp32 accumulate",
+                       "step": "QB sketch + SVD + ID + CUR from one sketch",
+                       "l2": "A (%.1f GB) larger than L2 on every pass" % (4.0 * m * n / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "qb_sketch": {"a_pass_ms_per_step": pass_ms,
+                          "a_pass_tflops": qb_flops / (pass_ms * 1e-3) / 1e12 if pass_ms else None,
+                          "a_passes_per_step": 2 * q + 2},
+            "roofline": roof,
+            "kernels": breakdown,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,274 @@
+/*
+ * rsvd.h - C ABI of the GB300 (sm_103a) randomized QB / RSVD / ID / CUR library.
+ *
+ * The operations are those of Voronin & Martinsson, "RSVDPACK: an implementation
+ * of randomized algorithms for computing the singular value, interpolative, and
+ * CUR decompositions of matrices on multi-core and GPU architectures":
+ *   - randomized range finder with the power scheme (Fig. 1 steps 1-3, Sec. 3.2,
+ *     Alg. 5 first part),
+ *   - the QB step B = Q^* A (Fig. 1 step 4; realised as Bt = A^* Q as in Alg. 5),
+ *   - the small SVD of B through the QR of Bt (Alg. 5, "RSVD version II"),
+ *   - the randomized ID from B (Sec. 3.5, last part; Sec. 2.4; Alg. 1),
+ *   - the CUR through the two-sided ID (Sec. 2.5, Sec. 3.6; Alg. 2 and 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Matrices are dense and ROW-MAJOR: element (i, j) of an r x c matrix X with
+ * leading dimension ldx sits at X[i*ldx + j], ldx >= c.  Indices are 0-based.
+ * l = k + p is the sketch width.  "dtype" is an rsvd_dtype naming the element
+ * type of A; floating outputs have the same type as A for RSVD_F64 (double) and
+ * are float for RSVD_F32 (and RSVD_BF16, where supported).  Singular values are
+ * always double.
+ *
+ * Ownership: every pointer is caller-owned DEVICE memory on the current CUDA
+ * device, except `opts` (host memory, may be NULL for defaults).  The library
+ * allocates nothing, never synchronises the host with the device, and enqueues
+ * all work on `stream` (a cudaStream_t; NULL = legacy default stream).  Scratch
+ * space is the caller's `work` buffer of `work_bytes` bytes, 256-byte aligned,
+ * sized by the matching *_workspace_size() query; its contents on entry do not
+ * matter and on exit are undefined.
+ *
+ * Errors: argument errors are reported synchronously by the return value and
+ * nothing is launched (RSVD_ERR_INVALID_ARG, RSVD_ERR_WORKSPACE,
+ * RSVD_ERR_UNSUPPORTED); a failed launch returns RSVD_ERR_CUDA.  Numerical
+ * failures detected on the device (Cholesky breakdown, Jacobi non-convergence,
+ * non-finite values, a bounded wait that ran out) are written, as an
+ * rsvd_status value, into the caller's device integer *d_info, which the call
+ * first resets to 0 in stream order; outputs are then unspecified.  d_info may
+ * be NULL when the caller does not want the code.
+ *
+ * Randomness: Omega is never stored.  Its entries are Gaussian samples
+ * generated inside the kernels from the Philox4x32-10 counter stream (Salmon et
+ * al., SC'11) keyed by `seed`, with counter (row i, column j / 4, tag 0, 0) and
+ * the Box-Muller transform on words (x0,x1) -> columns 4q, 4q+1 and (x2,x3) ->
+ * 4q+2, 4q+3, uniforms u = (2*(x >> 9) + 1) * 2^-24.  For RSVD_F64 inputs the
+ * samples are computed in double; for RSVD_F32 inputs in float and rounded to
+ * bf16 (nearest even), so the tensor cores consume them exactly.  Results are
+ * reproducible for a given seed, sizes and GPU.
+ */
+#ifndef RSVD_H
+#define RSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RSVD_OK = 0,
+  RSVD_ERR_INVALID_ARG = 1,    /* bad size, leading dimension, pointer or option  */
+  RSVD_ERR_WORKSPACE = 2,      /* work_bytes below the *_workspace_size() value    */
+  RSVD_ERR_CUDA = 3,           /* a CUDA runtime/driver call or launch failed       */
+  RSVD_ERR_UNSUPPORTED = 4,    /* valid request outside what this build implements  */
+  RSVD_ERR_NOT_SPD = 5,        /* device: Gram matrix not positive definite         */
+  RSVD_ERR_NO_CONVERGENCE = 6, /* device: Jacobi SVD exceeded max_sweeps            */
+  RSVD_ERR_NUMERIC = 7,        /* device: NaN or Inf met                            */
+  RSVD_ERR_TIMEOUT = 8         /* device: a bounded wait ran out                    */
+} rsvd_status;
+
+typedef enum { RSVD_F32 = 0, RSVD_F64 = 1, RSVD_BF16 = 2 } rsvd_dtype;
+
+typedef enum {
+  RSVD_PREC_TC = 0,   /* FP32 inputs: tcgen05 tensor-core products of bf16 splits
+                         (two-term split of each fp32 operand, fp32 accumulation) */
+  RSVD_PREC_SIMT = 1  /* FP32 inputs: plain fp32 FMA kernels (slower; cross-check) */
+} rsvd_precision;
+
+/* Options.  Pass NULL for the defaults set by rsvd_opts_default(). */
+typedef struct {
+  int s;           /* orthonormalisation frequency of the power scheme (Alg. 5):
+                      orth before the product number t (t = 0, 1, ...) when
+                      t mod s == 0; default 1 (orth before every product)        */
+  int max_sweeps;  /* sweep limit of the one-sided Jacobi SVD; default 30        */
+  int precision;   /* rsvd_precision; default RSVD_PREC_TC                        */
+  int reserved[13];/* must be zero                                                */
+} rsvd_opts;
+
+/* Fills *opts with the defaults.  Host only. */
+void rsvd_opts_default(rsvd_opts* opts);
+
+/* Static string naming a status code.  Host only. */
+const char* rsvd_status_string(int status);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int rsvd_version(void);
+
+/* -------------------------------------------------------------------------
+ * Workspace queries.  Return the byte count the matching call needs, or 0
+ * when the arguments are invalid.  Host only; nothing is launched.
+ * ------------------------------------------------------------------------- */
+size_t rsvd_qb_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                              const rsvd_opts* opts);
+size_t rsvd_svd_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                               const rsvd_opts* opts);
+size_t rsvd_id_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                              const rsvd_opts* opts);
+size_t rsvd_cur_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                               const rsvd_opts* opts);
+size_t rsvd_svd_id_cur_workspace_size(int64_t m, int64_t n, int k, int p, int q,
+                                      int dtype, const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
+ * rsvd_qb - randomized range finder and QB step (Alg. 5 up to Bt = A^* Q;
+ * Fig. 1 steps 1-4; power scheme of Sec. 3.2).
+ *   Y = A Omega; for j = 1..q: Y <- orth(Y), Z = A^* Y, Z <- orth(Z), Y = A Z
+ *   (orth placement by opts->s); Q = orth(Y); Bt = A^* Q.
+ * In:  A  m x n (dtype), lda >= n; 1 <= k, p >= 0, l = k+p <= min(m, n), q >= 0.
+ * Out: Q  m x l, orthonormal columns (ldq >= l);
+ *      Bt n x l = B^* with B = Q^* A (ldbt >= l).
+ * orth is an unpivoted QR whose Q is unique by diag(R) > 0 (CholeskyQR with
+ * an adaptive shift and two or three passes).
+ * ------------------------------------------------------------------------- */
+rsvd_status rsvd_qb(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                    const void* A, int64_t lda, void* Q, int64_t ldq, void* Bt,
+                    int64_t ldbt, void* work, size_t work_bytes, int* d_info,
+                    void* stream, const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
+ * rsvd_svd - rank-k approximate SVD A ~ U diag(S) V^T by Alg. 5 (RSVD version
+ * II, Sec. 3.4): QB step, [Qh, Rh] = qr(Bt), Rh = Uh Sigma Vh^T (one-sided
+ * Jacobi), U = Q Vh(:, 1:k), V = Qh Uh(:, 1:k).
+ * Out: U m x k (ldu >= k), S k singular values in descending order (double),
+ *      V n x k (ldv >= k).  Each pair (u_j, v_j) is signed so that the entry of
+ *      largest magnitude of v_j is positive (ties: lowest row index).
+ * ------------------------------------------------------------------------- */
+rsvd_status rsvd_svd(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                     const void* A, int64_t lda, void* U, int64_t ldu, double* S,
+                     void* V, int64_t ldv, void* work, size_t work_bytes, int* d_info,
+                     void* stream, const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
+ * rsvd_id - rank-k column interpolative decomposition through the QB step
+ * (Sec. 3.5, last part): k steps of column-pivoted QR (FP64 Householder, pivot
+ * = largest residual column norm, ties to the lowest column index, LAPACK-style
+ * exchanges) of B = Bt^T (l x n), T = S11^{-1} S12 by back substitution.
+ * Out: J  n int32, the column permutation; J[0:k] is the skeleton;
+ *      T  k x (n-k) (ldt >= n-k): A(:, J[k+c]) ~ sum_i A(:, J[i]) T[i][c].
+ * ------------------------------------------------------------------------- */
+rsvd_status rsvd_id(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                    const void* A, int64_t lda, int32_t* J, void* T, int64_t ldt,
+                    void* work, size_t work_bytes, int* d_info, void* stream,
+                    const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
+ * rsvd_cur - rank-k CUR A ~ A(:, Jc) U A(Ir, :) (Sec. 3.6; Alg. 2, 3): the
+ * randomized ID above, then a k-step pivoted QR of C^* with C = A(:, Jc)
+ * (row ID), R = A(Ir, :), and U = V^* R^dagger with R^dagger = Q_R R_R^{-T}
+ * from the QR of R^*.
+ * Out: Jc k int32, Ir k int32, U k x k (ldu >= k).
+ * ------------------------------------------------------------------------- */
+rsvd_status rsvd_cur(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                     const void* A, int64_t lda, int32_t* Jc, int32_t* Ir, void* U,
+                     int64_t ldu, void* work, size_t work_bytes, int* d_info,
+                     void* stream, const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
+ * rsvd_svd_id_cur - RSVD, ID and CUR from ONE sketch: one QB step feeds the
+ * small SVD (as rsvd_svd), the ID (as rsvd_id) and the CUR (as rsvd_cur).
+ * Any output group may be skipped by passing NULL for all its pointers
+ * (U,S,V | J,T | Jc,Ir,Ucur).  Outputs as in the three calls above.
+ * ------------------------------------------------------------------------- */
+rsvd_status rsvd_svd_id_cur(int64_t m, int64_t n, int k, int p, int q, uint64_t seed,
+                            int dtype, const void* A, int64_t lda,
+                            void* U, int64_t ldu, double* S, void* V, int64_t ldv,
+                            int32_t* J, void* T, int64_t ldt,
+                            int32_t* Jc, int32_t* Ir, void* Ucur, int64_t lducur,
+                            void* work, size_t work_bytes, int* d_info, void* stream,
+                            const rsvd_opts* opts);
+
+/* =========================================================================
+ * Step-level entry points (one per step of the path; same conventions).
+ * ========================================================================= */
+
+/* Omega itself, n x l (ldo >= l), exactly as the sketch kernels generate it
+ * (Fig. 1 step 1): double for RSVD_F64, float holding bf16 values for RSVD_F32.
+ * Intended for checking the stream; the path never stores Omega. */
+rsvd_status rsvd_omega(int64_t n, int l, uint64_t seed, int dtype, void* Omega,
+                       int64_t ldo, void* stream);
+
+/* The raw Philox4x32-10 words behind Omega: out is n x ceil(l/4) x 4 uint32,
+ * word t of counter (i, q, 0, 0) at out[(i*ceil(l/4) + q)*4 + t]. */
+rsvd_status rsvd_omega_words(int64_t n, int l, uint64_t seed, uint32_t* out,
+                             void* stream);
+
+size_t rsvd_sample_workspace_size(int64_t m, int64_t n, int l, int dtype,
+                                  const rsvd_opts* opts);
+/* Sample matrix Y = A Omega (Fig. 1 step 2), Y m x l (ldy >= l). */
+rsvd_status rsvd_sample(int64_t m, int64_t n, int l, uint64_t seed, int dtype,
+                        const void* A, int64_t lda, void* Y, int64_t ldy, void* work,
+                        size_t work_bytes, void* stream, const rsvd_opts* opts);
+
+size_t rsvd_apply_workspace_size(int64_t m, int64_t n, int l, int dtype,
+                                 const rsvd_opts* opts);
+/* Power-scheme half steps (Sec. 3.2):
+ *   trans = 0: Y = A X with X n x l (ldx >= l), Y m x l (ldy >= l);
+ *   trans = 1: Y = A^* X with X m x l, Y n x l.
+ * X and Y have A's floating type (float for RSVD_F32). */
+rsvd_status rsvd_apply(int64_t m, int64_t n, int l, int trans, int dtype, const void* A,
+                       int64_t lda, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                       void* work, size_t work_bytes, void* stream,
+                       const rsvd_opts* opts);
+
+size_t rsvd_orth_workspace_size(int64_t rows, int l, int dtype, const rsvd_opts* opts);
+/* orth(X) (Sec. 2.1): X rows x l (rows >= l) -> Q rows x l with orthonormal
+ * columns and upper-triangular R (l x l, ldr >= l; may be NULL) with X = Q R,
+ * diag(R) > 0.  Q may alias X only when ldq == ldx. */
+rsvd_status rsvd_orth(int64_t rows, int l, int dtype, const void* X, int64_t ldx,
+                      void* Q, int64_t ldq, void* R, int64_t ldr, void* work,
+                      size_t work_bytes, int* d_info, void* stream,
+                      const rsvd_opts* opts);
+
+size_t rsvd_small_svd_workspace_size(int l, int dtype, const rsvd_opts* opts);
+/* SVD of a small square matrix M (l x l, ldm >= l) by one-sided Jacobi
+ * (the core step of Alg. 5): M = Uh diag(Sh) Vh^T with Sh descending.
+ * Uh, Vh l x l (ld >= l); Sh l doubles. */
+rsvd_status rsvd_small_svd(int l, int dtype, const void* M, int64_t ldm, void* Uh,
+                           int64_t lduh, double* Sh, void* Vh, int64_t ldvh, void* work,
+                           size_t work_bytes, int* d_info, void* stream,
+                           const rsvd_opts* opts);
+
+size_t rsvd_cpqr_workspace_size(int r, int64_t n, int k);
+/* Column ID of an explicit matrix (Sec. 2.3, 2.4; Alg. 1): M r x n in double
+ * (ldm >= n), k steps of the pivoted QR described at rsvd_id.
+ * Out: J n int32; T k x (n-k) double (ldt >= n-k); gaps (may be NULL) k
+ * doubles, (nu1 - nu2) / nu1 of the two largest residual norms at each step
+ * (+inf when one candidate remains). */
+rsvd_status rsvd_cpqr_id(int r, int64_t n, int k, const double* M, int64_t ldm,
+                         int32_t* J, double* T, int64_t ldt, double* gaps, void* work,
+                         size_t work_bytes, int* d_info, void* stream);
+
+/* =========================================================================
+ * Tracing aids (host only; not part of the paper's method).
+ * ========================================================================= */
+
+/* Kernel classes timed when tracing is enabled. */
+enum {
+  RSVD_TRACE_A_OMEGA = 0, /* sketch Y = A Omega (tensor cores, Omega in-kernel)      */
+  RSVD_TRACE_A_W = 1,     /* power step Y = A Z (tensor cores)                       */
+  RSVD_TRACE_AT_W = 2,    /* power step Z = A^T Y and QB step Bt = A^T Q             */
+  RSVD_TRACE_GRAM = 3,    /* Gram X^T X of CholeskyQR                                */
+  RSVD_TRACE_APPLY = 4,   /* X R^-1 of CholeskyQR                                    */
+  RSVD_TRACE_REDUCE = 5,  /* fixed-order sum of the stream-K partial tiles           */
+  RSVD_TRACE_CPQR = 6,    /* column-pivoted QR of ID / CUR                           */
+  RSVD_TRACE_CLASSES = 7
+};
+
+/* Turns on (1) or off (0) CUDA-event timing of the classes above.  While on,
+ * every traced launch records a start and an end event on its own stream. */
+rsvd_status rsvd_trace_enable(int enable);
+
+/* Synchronises with the recorded events, writes per class the summed duration
+ * in milliseconds and the number of launches (arrays of nclass entries), and
+ * clears the records.  Returns RSVD_TRACE_CLASSES, or -1 on bad arguments. */
+int rsvd_trace_read(double* ms, int64_t* launches, int nclass);
+
+/* Number of kernels the library has launched since it was loaded. */
+int64_t rsvd_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSVD_H */

@@ -1,0 +1,446 @@
+"""Python binding of librsvd.so: randomized QB / RSVD / ID / CUR on one GB300.
+
+Argument marshalling only.  Every step of the computation runs in the CUDA
+kernels of librsvd.so (C ABI declared in include/rsvd.h); this module turns
+torch CUDA tensors into pointers, sizes and the current stream, allocates the
+outputs and the workspace with torch, and raises on a non-OK status.  There is
+no fallback: importing works without the library, but every call fails loudly
+when librsvd.so has not been built.
+
+Functions (names follow the C ABI):
+  qb, svd, id, cur, svd_id_cur       - the routines of the paper's Alg. 5 / Sec. 3.5-3.6
+  omega, omega_words                 - the Philox Gaussian test matrix (checking aid)
+  sample, apply, orth, small_svd     - the individual steps of the path
+  cpqr_id                            - column ID of an explicit FP64 matrix (Alg. 1)
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librsvd.so")
+
+F32, F64, BF16 = 0, 1, 2
+PREC_TC, PREC_SIMT = 0, 1
+
+STATUS = {
+    0: "RSVD_OK", 1: "RSVD_ERR_INVALID_ARG", 2: "RSVD_ERR_WORKSPACE", 3: "RSVD_ERR_CUDA",
+    4: "RSVD_ERR_UNSUPPORTED", 5: "RSVD_ERR_NOT_SPD", 6: "RSVD_ERR_NO_CONVERGENCE",
+    7: "RSVD_ERR_NUMERIC", 8: "RSVD_ERR_TIMEOUT",
+}
+
+
+class RsvdError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = int(code)
+        super().__init__("%s: %s" % (where, STATUS.get(self.code, str(code))))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int), ("max_sweeps", ctypes.c_int),
+                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 13)]
+
+
+_lib = None
+_c_i64 = ctypes.c_int64
+_c_int = ctypes.c_int
+_c_u64 = ctypes.c_uint64
+_c_size = ctypes.c_size_t
+_vp = ctypes.c_void_p
+_OPTP = ctypes.POINTER(Opts)
+
+_SIGS = {
+    "rsvd_opts_default": (None, [_OPTP]),
+    "rsvd_status_string": (ctypes.c_char_p, [_c_int]),
+    "rsvd_version": (_c_int, []),
+    "rsvd_qb_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int, _OPTP]),
+    "rsvd_svd_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int, _OPTP]),
+    "rsvd_id_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int, _OPTP]),
+    "rsvd_cur_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int, _OPTP]),
+    "rsvd_svd_id_cur_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int,
+                                                 _OPTP]),
+    "rsvd_qb": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int, _vp, _c_i64,
+                         _vp, _c_i64, _vp, _c_i64, _vp, _c_size, _vp, _vp, _OPTP]),
+    "rsvd_svd": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int, _vp, _c_i64,
+                          _vp, _c_i64, _vp, _vp, _c_i64, _vp, _c_size, _vp, _vp, _OPTP]),
+    "rsvd_id": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int, _vp, _c_i64,
+                         _vp, _vp, _c_i64, _vp, _c_size, _vp, _vp, _OPTP]),
+    "rsvd_cur": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int, _vp, _c_i64,
+                          _vp, _vp, _vp, _c_i64, _vp, _c_size, _vp, _vp, _OPTP]),
+    "rsvd_svd_id_cur": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int, _vp,
+                                 _c_i64, _vp, _c_i64, _vp, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
+                                 _vp, _vp, _c_i64, _vp, _c_size, _vp, _vp, _OPTP]),
+    "rsvd_omega": (_c_int, [_c_i64, _c_int, _c_u64, _c_int, _vp, _c_i64, _vp]),
+    "rsvd_omega_words": (_c_int, [_c_i64, _c_int, _c_u64, _vp, _vp]),
+    "rsvd_sample_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _OPTP]),
+    "rsvd_sample": (_c_int, [_c_i64, _c_i64, _c_int, _c_u64, _c_int, _vp, _c_i64, _vp, _c_i64,
+                             _vp, _c_size, _vp, _OPTP]),
+    "rsvd_apply_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _OPTP]),
+    "rsvd_apply": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _vp, _c_i64, _vp, _c_i64,
+                            _vp, _c_i64, _vp, _c_size, _vp, _OPTP]),
+    "rsvd_orth_workspace_size": (_c_size, [_c_i64, _c_int, _c_int, _OPTP]),
+    "rsvd_orth": (_c_int, [_c_i64, _c_int, _c_int, _vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _vp,
+                           _c_size, _vp, _vp, _OPTP]),
+    "rsvd_small_svd_workspace_size": (_c_size, [_c_int, _c_int, _OPTP]),
+    "rsvd_small_svd": (_c_int, [_c_int, _c_int, _vp, _c_i64, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
+                                _c_size, _vp, _vp, _OPTP]),
+    "rsvd_cpqr_workspace_size": (_c_size, [_c_int, _c_i64, _c_int]),
+    "rsvd_trace_enable": (_c_int, [_c_int]),
+    "rsvd_trace_read": (_c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_i64), _c_int]),
+    "rsvd_kernel_launch_count": (_c_i64, []),
+    "rsvd_cpqr_id": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp, _vp,
+                              _c_size, _vp, _vp]),
+}
+
+
+def lib():
+    """The loaded librsvd.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("librsvd.so is not built (run __graft_entry__.build() or "
+                               "python paper_1502_05366_gb300/build.py); there is no fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+TRACE_CLASSES = ["a_omega", "a_w", "at_w", "gram", "orth_apply", "reduce", "cpqr"]
+
+
+def trace_enable(on=True):
+    lib().rsvd_trace_enable(1 if on else 0)
+
+
+def trace_read():
+    """{class: (total ms, launches)} of the traced kernels since the last read."""
+    n = len(TRACE_CLASSES)
+    ms = (ctypes.c_double * n)()
+    cnt = (_c_i64 * n)()
+    lib().rsvd_trace_read(ms, cnt, n)
+    return {TRACE_CLASSES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def kernel_launch_count():
+    return int(lib().rsvd_kernel_launch_count())
+
+
+def make_opts(s=1, max_sweeps=30, precision=PREC_TC):
+    o = Opts()
+    lib().rsvd_opts_default(ctypes.byref(o))
+    o.s, o.max_sweeps, o.precision = int(s), int(max_sweeps), int(precision)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# tensor plumbing
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError("unsupported dtype %s (float32 or float64)" % t.dtype)
+
+
+def _check_matrix(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dim() != 2 or t.stride(1) != 1 or t.stride(0) < t.shape[1]:
+        raise ValueError("%s must be a row-major 2-D tensor (unit column stride)" % name)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _work(nbytes, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _raise(st, where):
+    if st != 0:
+        raise RsvdError(st, where)
+
+
+def _info(device):
+    return _torch().zeros(1, dtype=_torch().int32, device=device)
+
+
+def check_info(info, where="device"):
+    """Synchronises and raises if the device-side status is not OK."""
+    v = int(info.item())
+    if v != 0:
+        raise RsvdError(v, where)
+
+
+def _opts_ptr(opts):
+    return ctypes.byref(opts) if opts is not None else None
+
+
+# ---------------------------------------------------------------------------
+# routines
+# ---------------------------------------------------------------------------
+def qb(A, k, p, q, seed, opts=None, check=True):
+    """(Q, Bt) with Q m x l orthonormal and Bt = A^T Q (n x l); l = k + p."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    l = k + p
+    dt = _dtype_code(A)
+    Q = torch.empty(m, l, dtype=A.dtype, device=A.device)
+    Bt = torch.empty(n, l, dtype=A.dtype, device=A.device)
+    ws = lib().rsvd_qb_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_qb_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    st = lib().rsvd_qb(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(Q), l, _ptr(Bt), l,
+                       _ptr(W), W.numel(), _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_qb")
+    if check:
+        check_info(info, "rsvd_qb")
+    return Q, Bt
+
+
+def svd(A, k, p, q, seed, opts=None, check=True):
+    """(U, S, V): A ~ U diag(S) V^T, U m x k, S k (float64), V n x k (Alg. 5)."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    U = torch.empty(m, k, dtype=A.dtype, device=A.device)
+    V = torch.empty(n, k, dtype=A.dtype, device=A.device)
+    S = torch.empty(k, dtype=torch.float64, device=A.device)
+    ws = lib().rsvd_svd_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_svd_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    st = lib().rsvd_svd(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(U), k, _ptr(S),
+                        _ptr(V), k, _ptr(W), W.numel(), _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_svd")
+    if check:
+        check_info(info, "rsvd_svd")
+    return U, S, V
+
+
+def id(A, k, p, q, seed, opts=None, check=True):  # noqa: A001 - the paper's name
+    """(J, T): J n int32 permutation (J[:k] skeleton), T k x (n-k)."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    J = torch.empty(n, dtype=torch.int32, device=A.device)
+    T = torch.empty(k, max(n - k, 1), dtype=A.dtype, device=A.device)
+    ws = lib().rsvd_id_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_id_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    st = lib().rsvd_id(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(J), _ptr(T),
+                       T.stride(0), _ptr(W), W.numel(), _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_id")
+    if check:
+        check_info(info, "rsvd_id")
+    return J, T[:, : n - k]
+
+
+def cur(A, k, p, q, seed, opts=None, check=True):
+    """(Jc, Ir, U): A ~ A[:, Jc] U A[Ir, :] (Alg. 3)."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    Jc = torch.empty(k, dtype=torch.int32, device=A.device)
+    Ir = torch.empty(k, dtype=torch.int32, device=A.device)
+    U = torch.empty(k, k, dtype=A.dtype, device=A.device)
+    ws = lib().rsvd_cur_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_cur_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    st = lib().rsvd_cur(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(Jc), _ptr(Ir),
+                        _ptr(U), k, _ptr(W), W.numel(), _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_cur")
+    if check:
+        check_info(info, "rsvd_cur")
+    return Jc, Ir, U
+
+
+class Plan:
+    """Pre-allocated outputs and workspace for repeated rsvd_svd_id_cur calls."""
+
+    def __init__(self, m, n, k, p, q, dtype, device, opts=None, with_svd=True, with_id=True,
+                 with_cur=True):
+        torch = _torch()
+        self.m, self.n, self.k, self.p, self.q = m, n, k, p, q
+        self.dt = {torch.float32: F32, torch.float64: F64}[dtype]
+        self.opts = opts
+        dev = torch.device(device)
+        self.U = torch.empty(m, k, dtype=dtype, device=dev) if with_svd else None
+        self.S = torch.empty(k, dtype=torch.float64, device=dev) if with_svd else None
+        self.V = torch.empty(n, k, dtype=dtype, device=dev) if with_svd else None
+        self.J = torch.empty(n, dtype=torch.int32, device=dev) if with_id else None
+        self.T = torch.empty(k, n - k, dtype=dtype, device=dev) if with_id else None
+        self.Jc = torch.empty(k, dtype=torch.int32, device=dev) if with_cur else None
+        self.Ir = torch.empty(k, dtype=torch.int32, device=dev) if with_cur else None
+        self.Ucur = torch.empty(k, k, dtype=dtype, device=dev) if with_cur else None
+        ws = lib().rsvd_svd_id_cur_workspace_size(m, n, k, p, q, self.dt, _opts_ptr(opts))
+        if ws == 0:
+            raise RsvdError(1, "rsvd_svd_id_cur_workspace_size")
+        self.work = _work(ws, dev)
+        self.info = _info(dev)
+
+    def run(self, A, seed):
+        _check_matrix(A, "A")
+        k = self.k
+        st = lib().rsvd_svd_id_cur(
+            self.m, self.n, k, self.p, self.q, seed, self.dt, _ptr(A), A.stride(0),
+            _ptr(self.U), k, _ptr(self.S), _ptr(self.V), k, _ptr(self.J), _ptr(self.T),
+            self.n - k, _ptr(self.Jc), _ptr(self.Ir), _ptr(self.Ucur), k, _ptr(self.work),
+            self.work.numel(), _ptr(self.info), _stream(), _opts_ptr(self.opts))
+        _raise(st, "rsvd_svd_id_cur")
+
+
+def svd_id_cur(A, k, p, q, seed, opts=None, check=True):
+    """RSVD, ID and CUR from one sketch: dict of U, S, V, J, T, Jc, Ir, Ucur."""
+    _check_matrix(A, "A")
+    m, n = A.shape
+    plan = Plan(m, n, k, p, q, A.dtype, A.device, opts)
+    plan.run(A, seed)
+    if check:
+        check_info(plan.info, "rsvd_svd_id_cur")
+    return dict(U=plan.U, S=plan.S, V=plan.V, J=plan.J, T=plan.T, Jc=plan.Jc, Ir=plan.Ir,
+                Ucur=plan.Ucur)
+
+
+# ---------------------------------------------------------------------------
+# step-level calls
+# ---------------------------------------------------------------------------
+def omega(n, l, seed, dtype, device="cuda"):
+    torch = _torch()
+    Om = torch.empty(n, l, dtype=dtype, device=device)
+    dt = {torch.float32: F32, torch.float64: F64}[dtype]
+    _raise(lib().rsvd_omega(n, l, seed, dt, _ptr(Om), l, _stream()), "rsvd_omega")
+    return Om
+
+
+def omega_words(n, l, seed, device="cuda"):
+    torch = _torch()
+    nq = (l + 3) // 4
+    out = torch.empty(n, nq, 4, dtype=torch.int32, device=device)
+    _raise(lib().rsvd_omega_words(n, l, seed, _ptr(out), _stream()), "rsvd_omega_words")
+    return out
+
+
+def sample(A, l, seed, opts=None):
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    Y = torch.empty(m, l, dtype=A.dtype, device=A.device)
+    ws = lib().rsvd_sample_workspace_size(m, n, l, dt, _opts_ptr(opts))
+    W = _work(ws, A.device)
+    st = lib().rsvd_sample(m, n, l, seed, dt, _ptr(A), A.stride(0), _ptr(Y), l, _ptr(W),
+                           W.numel(), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_sample")
+    return Y
+
+
+def apply(A, X, trans, opts=None):
+    torch = _torch()
+    _check_matrix(A, "A")
+    _check_matrix(X, "X")
+    m, n = A.shape
+    l = X.shape[1]
+    dt = _dtype_code(A)
+    rows = n if trans else m
+    Y = torch.empty(rows, l, dtype=A.dtype, device=A.device)
+    ws = lib().rsvd_apply_workspace_size(m, n, l, dt, _opts_ptr(opts))
+    W = _work(ws, A.device)
+    st = lib().rsvd_apply(m, n, l, int(trans), dt, _ptr(A), A.stride(0), _ptr(X), X.stride(0),
+                          _ptr(Y), l, _ptr(W), W.numel(), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_apply")
+    return Y
+
+
+def orth(X, opts=None, check=True):
+    torch = _torch()
+    _check_matrix(X, "X")
+    rows, l = X.shape
+    dt = _dtype_code(X)
+    Q = torch.empty(rows, l, dtype=X.dtype, device=X.device)
+    R = torch.empty(l, l, dtype=X.dtype, device=X.device)
+    ws = lib().rsvd_orth_workspace_size(rows, l, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_orth_workspace_size")
+    W = _work(ws, X.device)
+    info = _info(X.device)
+    st = lib().rsvd_orth(rows, l, dt, _ptr(X), X.stride(0), _ptr(Q), l, _ptr(R), l, _ptr(W),
+                         W.numel(), _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_orth")
+    if check:
+        check_info(info, "rsvd_orth")
+    return Q, R
+
+
+def small_svd(M, opts=None, check=True):
+    torch = _torch()
+    _check_matrix(M, "M")
+    l = M.shape[0]
+    dt = _dtype_code(M)
+    Uh = torch.empty(l, l, dtype=M.dtype, device=M.device)
+    Vh = torch.empty(l, l, dtype=M.dtype, device=M.device)
+    Sh = torch.empty(l, dtype=torch.float64, device=M.device)
+    ws = lib().rsvd_small_svd_workspace_size(l, dt, _opts_ptr(opts))
+    W = _work(ws, M.device)
+    info = _info(M.device)
+    st = lib().rsvd_small_svd(l, dt, _ptr(M), M.stride(0), _ptr(Uh), l, _ptr(Sh), _ptr(Vh), l,
+                              _ptr(W), W.numel(), _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_small_svd")
+    if check:
+        check_info(info, "rsvd_small_svd")
+    return Uh, Sh, Vh
+
+
+def cpqr_id(M, k, check=True):
+    """Column ID of an explicit float64 CUDA matrix M (r x n): (J, T, gaps)."""
+    torch = _torch()
+    _check_matrix(M, "M")
+    if M.dtype != torch.float64:
+        raise TypeError("cpqr_id takes float64")
+    r, n = M.shape
+    J = torch.empty(n, dtype=torch.int32, device=M.device)
+    T = torch.empty(k, max(n - k, 1), dtype=torch.float64, device=M.device)
+    gaps = torch.empty(k, dtype=torch.float64, device=M.device)
+    ws = lib().rsvd_cpqr_workspace_size(r, n, k)
+    if ws == 0:
+        raise RsvdError(1, "rsvd_cpqr_workspace_size")
+    W = _work(ws, M.device)
+    info = _info(M.device)
+    st = lib().rsvd_cpqr_id(r, n, k, _ptr(M), M.stride(0), _ptr(J), _ptr(T), T.stride(0),
+                            _ptr(gaps), _ptr(W), W.numel(), _ptr(info), _stream())
+    _raise(st, "rsvd_cpqr_id")
+    if check:
+        check_info(info, "rsvd_cpqr_id")
+    return J, T[:, : n - k], gaps

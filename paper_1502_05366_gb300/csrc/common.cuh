@@ -1,0 +1,153 @@
+// Shared device helpers for the randomized QB / RSVD / ID / CUR kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "rsvd.h"
+
+#define RSVD_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return RSVD_ERR_CUDA;              \
+  } while (0)
+
+#define RSVD_LAUNCH_CHECK()                                   \
+  do {                                                        \
+    cudaError_t _e = cudaGetLastError();                      \
+    if (_e != cudaSuccess) return RSVD_ERR_CUDA;              \
+  } while (0)
+
+namespace rsvd {
+
+// Host-side count of kernel launches made by the library (tracing aid), and
+// CUDA-event records around selected kernels when tracing is enabled.
+void count_launch();
+int trace_begin(int cls, cudaStream_t s);
+void trace_end(int idx, cudaStream_t s);
+
+// First device-side error wins; later ones are dropped.
+__device__ __forceinline__ void set_info(int* d_info, int code) {
+  if (d_info) atomicCAS(d_info, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).  One round maps counter
+// (c0, c1, c2, c3) with key (k0, k1) to
+//   (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+// M0 = 0xD2511F53, M1 = 0xCD9E8D57; the key is bumped by the Weyl constants
+// 0x9E3779B9, 0xBB67AE85 between rounds.
+// ---------------------------------------------------------------------------
+struct Words4 {
+  uint32_t x0, x1, x2, x3;
+};
+
+__device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return Words4{c0, c1, c2, c3};
+}
+
+// Counter layout of Omega: (row i, column quad j/4, tag, batch); key = seed.
+__device__ __forceinline__ Words4 omega_words(uint64_t seed, uint32_t row, uint32_t quad,
+                                              uint32_t tag = 0, uint32_t batch = 0) {
+  return philox4x32_10(row, quad, tag, batch, (uint32_t)(seed & 0xffffffffu),
+                       (uint32_t)(seed >> 32));
+}
+
+// u = (2*(x >> 9) + 1) * 2^-24: odd multiples of 2^-24 in (0, 1), exact in fp32.
+__device__ __forceinline__ float word_to_uniform_f(uint32_t x) {
+  return (float)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f;
+}
+__device__ __forceinline__ double word_to_uniform_d(uint32_t x) {
+  return (double)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8;
+}
+
+// Box-Muller (Box & Muller 1958) on the four words: (x0,x1) -> z0, z1 and
+// (x2,x3) -> z2, z3.  Single precision with CUDA's logf / sqrtf / sincospif.
+__device__ __forceinline__ void gauss4_f(const Words4& w, float z[4]) {
+  const float r0 = sqrtf(-2.0f * logf(word_to_uniform_f(w.x0)));
+  const float r1 = sqrtf(-2.0f * logf(word_to_uniform_f(w.x2)));
+  float s0, c0, s1, c1;
+  sincospif(2.0f * word_to_uniform_f(w.x1), &s0, &c0);
+  sincospif(2.0f * word_to_uniform_f(w.x3), &s1, &c1);
+  z[0] = r0 * c0;
+  z[1] = r0 * s0;
+  z[2] = r1 * c1;
+  z[3] = r1 * s1;
+}
+
+__device__ __forceinline__ void gauss4_d(const Words4& w, double z[4]) {
+  const double r0 = sqrt(-2.0 * log(word_to_uniform_d(w.x0)));
+  const double r1 = sqrt(-2.0 * log(word_to_uniform_d(w.x2)));
+  double s0, c0, s1, c1;
+  sincospi(2.0 * word_to_uniform_d(w.x1), &s0, &c0);
+  sincospi(2.0 * word_to_uniform_d(w.x3), &s1, &c1);
+  z[0] = r0 * c0;
+  z[1] = r0 * s0;
+  z[2] = r1 * c1;
+  z[3] = r1 * s1;
+}
+
+// fp32 -> bf16 (nearest even) -> fp32.
+__device__ __forceinline__ float round_bf16(float x) {
+  return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+// Omega entries for the quad (row, quad) in the arithmetic type T:
+// double for FP64 inputs, bf16-rounded float for FP32 inputs.
+template <typename T>
+struct OmegaGen;
+
+template <>
+struct OmegaGen<float> {
+  __device__ __forceinline__ static void quad(uint64_t seed, uint32_t row, uint32_t quad,
+                                              float z[4]) {
+    gauss4_f(omega_words(seed, row, quad), z);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) z[t] = round_bf16(z[t]);
+  }
+};
+
+template <>
+struct OmegaGen<double> {
+  __device__ __forceinline__ static void quad(uint64_t seed, uint32_t row, uint32_t quad,
+                                              double z[4]) {
+    gauss4_d(omega_words(seed, row, quad), z);
+  }
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) {
+  return (a + b - 1) / b;
+}
+__host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) {
+  return ceil_div(a, b) * b;
+}
+
+}  // namespace rsvd

@@ -1,0 +1,694 @@
+// tcgen05 (5th-generation tensor core) GEMMs for the passes over A.
+//
+//   form 0:  Y (rows x L) = A (rows x K) W       sketch Y = A Omega (Fig. 1 step 2),
+//                                                power step Y = A Z, orth apply X R^-1
+//   form 1:  Z (rows x L) = A^T W, A is K x rows  power step Z = A^* Y (Sec. 3.2),
+//                                                QB step Bt = A^* Q (Alg. 5), Gram X^T X
+//
+// Arithmetic: every fp32 entry x of A is split as x ~ a0 + a1 with a0 = bf16(x),
+// a1 = bf16(x - a0) (16 significant bits).  W comes in NW bf16 terms:
+//   NW = 1  Omega, bf16-exact by construction:      a0 w0 + a1 w0
+//   NW = 2  stored matrix of generic data (Q, Z, X): a0 w0 + a1 w0 + a0 w1
+//   NW = 3  the l x l factor R^-1 of CholeskyQR:     a0 w0 + a1 w0 + a0 w1 + a0 w2
+//   NW = 4  Gram X^T X (W = split of X itself):      a0 w0 + a1 w0 + a0 w1 + a1 w1
+// For two different matrices the dropped term a1 w1 and the rounding residuals
+// are independent from entry to entry and only add noise of relative size
+// 2^-17.  R^-1 is one fixed matrix applied to every row, so its rounding would
+// bias the result: it keeps 24 bits.  In a Gram both factors carry the same
+// residual a1 and sum_i a1_i^2 is a positive bias on the diagonal: kept.  The products run as
+// tcgen05.mma kind::f16 with fp32 accumulation in tensor memory (TMEM).
+//
+// Data flow per CTA (one CTA per SM, persistent, stream-K over the flattened
+// (tile, k-chunk) iteration space so that every SM gets the same share):
+//   warp 0      TMA producer: fp32 A tile (128 x 32) and the W hi/lo tiles
+//   warp 1      MMA issuer (one thread) and TMEM owner
+//   warps 4-7   converters: fp32 A tile (shared) -> bf16 hi/lo rows -> TMEM
+//               (tcgen05.st), then the epilogue (tcgen05.ld -> partial tile)
+//   warps 8-15  (Omega only) Philox/Box-Muller generators writing the bf16
+//               Omega tile straight into the swizzled K-major shared layout
+// Partial tiles are summed in a fixed order by tc_reduce_kernel, which writes
+// the fp32 result and, on request, the transposed bf16 hi/lo split that the
+// next GEMM consumes.
+//
+// Every mbarrier wait is bounded (~1 s of clock): on expiry the kernel records
+// RSVD_ERR_TIMEOUT, every role leaves its loop, the producer waits (bounded)
+// for its own copies in flight, TMEM is freed and the CTA returns.
+#include <cuda.h>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsvd {
+
+namespace {
+constexpr int BM = 128;             // output rows per tile (MMA M)
+constexpr int BK = 32;              // K per stage
+constexpr int MAXST = 4;            // stages (3 when W has three bf16 terms)
+constexpr int A_STAGE_BYTES = BM * BK * 4;   // 16 KB fp32
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TMEM_A0 = 256;   // first TMEM column of the A stages
+constexpr int NCONV = 4;            // converter / epilogue warps (4..7)
+constexpr int NGEN = 8;             // Omega generator warps (8..15)
+constexpr long long WAIT_LIMIT = 2000000000LL;   // cycles
+
+__host__ __device__ constexpr int w_tile_bytes(int L) { return L * BK * 2; }
+__host__ __device__ constexpr int stages_for(int nw) { return nw == 3 ? 3 : 4; }
+// W tiles per stage: Omega 1, stored 2, R^-1 3, Gram 2.  Omega keeps two slots
+// in the layout for simplicity.
+__host__ __device__ constexpr int w_tiles(int nw) { return nw == 1 ? 2 : (nw == 4 ? 2 : nw); }
+__host__ __device__ constexpr int stage_bytes(int L, int nw) {
+  return A_STAGE_BYTES + w_tiles(nw) * w_tile_bytes(L);
+}
+}  // namespace
+
+struct TcParams {
+  int64_t rows, K;
+  int L, lvalid;
+  uint64_t seed;
+  int64_t tiles, kiters, total;
+  int maxseg;
+  float* part;
+  const int* skip;
+  int* d_info;
+};
+
+// ------------------------------- PTX helpers --------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the CTA aborted or the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* d_info) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_LIMIT) {
+      *abort_flag = 1;
+      set_info(d_info, RSVD_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, "
+      "%10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// D[tmem] (+)= A[tmem] * B[smem desc], kind::f16 (bf16 inputs, fp32 accumulate).
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups of
+// 512 bytes (SBO), version 1 (bit 46), layout code 4 in bits 61-63.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512u >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1u << 46;                 // descriptor version
+  d |= (uint64_t)4u << 61;                 // SWIZZLE_64B
+  return d;
+}
+// Instruction descriptor: D f32, A bf16, B bf16, both K-major, N and M.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_elem), "f"(lo_elem));
+  return r;
+}
+
+// 32 fp32 values of one A row -> 16 hi words and 16 lo words (2 bf16 each).
+__device__ __forceinline__ void split_row(const float (&x)[32], uint32_t (&hi)[16],
+                                          uint32_t (&lo)[16]) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const float a = x[2 * e], b = x[2 * e + 1];
+    const uint32_t h = pack_bf16x2(a, b);
+    const float ha = __uint_as_float(h << 16), hb = __uint_as_float(h & 0xFFFF0000u);
+    hi[e] = h;
+    lo[e] = pack_bf16x2(a - ha, b - hb);
+  }
+}
+
+// Stream-K bounds of CTA b.
+__device__ __forceinline__ int64_t sk_start(int64_t b, int64_t total, int64_t G) {
+  return (b * total) / G;
+}
+
+template <int FORM, int NW>
+__global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                   const __grid_constant__ CUtensorMap mapW0,
+                   const __grid_constant__ CUtensorMap mapW1,
+                   const __grid_constant__ CUtensorMap mapW2, TcParams P) {
+  constexpr bool OMEGA = (NW == 1);
+  constexpr bool GRAM = (NW == 4);
+  constexpr int NWT = OMEGA ? 1 : w_tiles(NW);   // W tiles loaded per stage
+  constexpr int STAGES = stages_for(NW);
+  extern __shared__ __align__(1024) unsigned char dsm_raw[];
+  if (P.skip && *P.skip) return;
+  unsigned char* dsm = (unsigned char*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  const int L = P.L;
+  const int SB = stage_bytes(L, NW);
+  uint64_t* bars = (uint64_t*)(dsm + STAGES * SB);
+  uint64_t* full = bars;                  // TMA landed (A [+ W])
+  uint64_t* conv = bars + STAGES;         // A stage written to TMEM
+  uint64_t* genb = bars + 2 * STAGES;     // Omega tile written
+  uint64_t* done = bars + 3 * STAGES;     // MMAs of the stage finished
+  uint64_t* acc_full = bars + 4 * STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_holder = (uint32_t*)(acc_empty + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x;
+  const int64_t it0 = sk_start(blockIdx.x, P.total, G);
+  const int64_t it1 = sk_start(blockIdx.x + 1, P.total, G);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], NCONV);
+      mbar_init(&genb[s], NGEN);
+      mbar_init(&done[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, NCONV);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0 && lane == 0) {
+    prefetch_map(&mapA);
+    if (NWT >= 2) {
+      prefetch_map(&mapW0);
+      prefetch_map(&mapW1);
+    }
+    if (NWT == 3) prefetch_map(&mapW2);
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      const uint32_t bytes = A_STAGE_BYTES + (OMEGA ? 0u : (uint32_t)NWT * (uint32_t)w_tile_bytes(L));
+      int64_t last_issued = -1;
+      for (int64_t it = it0; it < it1; ++it) {
+        const int64_t li = it - it0;
+        const int s = (int)(li % STAGES);
+        const uint32_t ph = (uint32_t)((li / STAGES) & 1);
+        if (!mbar_wait(&done[s], ph ^ 1u, abort_flag, P.d_info)) break;
+        const int64_t tile = it / P.kiters, kc = it % P.kiters;
+        unsigned char* st = dsm + s * SB;
+        mbar_arrive_expect_tx(&full[s], bytes);
+        if (FORM == 0)
+          tma_load_2d(st, &mapA, &full[s], (int)(kc * BK), (int)(tile * BM));
+        else
+          tma_load_2d(st, &mapA, &full[s], (int)(tile * BM), (int)(kc * BK));
+        if (NWT >= 2) {
+          tma_load_2d(st + A_STAGE_BYTES, &mapW0, &full[s], (int)(kc * BK), 0);
+          tma_load_2d(st + A_STAGE_BYTES + w_tile_bytes(L), &mapW1, &full[s], (int)(kc * BK), 0);
+        }
+        if (NWT == 3)
+          tma_load_2d(st + A_STAGE_BYTES + 2 * w_tile_bytes(L), &mapW2, &full[s], (int)(kc * BK),
+                      0);
+        last_issued = li;
+      }
+      if (*abort_flag && last_issued >= 0) {
+        // drain: wait (bounded) for the copies this thread issued
+        const int64_t first = last_issued - STAGES + 1 > 0 ? last_issued - STAGES + 1 : 0;
+        for (int64_t li = first; li <= last_issued; ++li) {
+          const int s = (int)(li % STAGES);
+          const uint32_t ph = (uint32_t)((li / STAGES) & 1);
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[s], ph) && clock64() - t0 < WAIT_LIMIT) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------- MMA issuer -------------------------------
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, L);
+      int64_t seg = -1;
+      int64_t cur_tile = -1;
+      for (int64_t it = it0; it < it1; ++it) {
+        const int64_t li = it - it0;
+        const int s = (int)(li % STAGES);
+        const uint32_t ph = (uint32_t)((li / STAGES) & 1);
+        const int64_t tile = it / P.kiters;
+        const bool seg_start = (tile != cur_tile);
+        if (seg_start) {
+          cur_tile = tile;
+          ++seg;
+          if (seg > 0 && !mbar_wait(acc_empty, (uint32_t)((seg - 1) & 1), abort_flag, P.d_info))
+            break;
+        }
+        if (!mbar_wait(&conv[s], ph, abort_flag, P.d_info)) break;
+        if (OMEGA) {
+          if (!mbar_wait(&genb[s], ph, abort_flag, P.d_info)) break;
+        } else {
+          if (!mbar_wait(&full[s], ph, abort_flag, P.d_info)) break;
+        }
+        tc_fence_after();
+        const uint32_t wbase = smem_u32(dsm + s * SB + A_STAGE_BYTES);
+        const uint32_t a_col = tmem + TMEM_A0 + 32u * (uint32_t)s;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t bhi = sw64_desc(wbase + 32u * kk);
+          const uint32_t ahi = a_col + 8u * kk;
+          const uint32_t alo = a_col + 16u + 8u * kk;
+          const uint32_t acc0 = (seg_start && kk == 0) ? 0u : 1u;
+          mma_ts(tmem, ahi, bhi, idesc, acc0);
+          mma_ts(tmem, alo, bhi, idesc, 1u);
+#pragma unroll
+          for (int t = 1; t < NWT; ++t) {
+            const uint64_t bt = sw64_desc(wbase + (uint32_t)(t * w_tile_bytes(L)) + 32u * kk);
+            mma_ts(tmem, ahi, bt, idesc, 1u);
+            if (GRAM) mma_ts(tmem, alo, bt, idesc, 1u);
+          }
+        }
+        mma_commit(&done[s]);
+        const bool seg_end = (it + 1 == it1) || ((it + 1) / P.kiters != tile);
+        if (seg_end) mma_commit(acc_full);
+      }
+    }
+  } else if (warp >= 4 && warp < 4 + NCONV) {
+    // ------------------------ converters and epilogue -------------------------
+    const int q = warp - 4;                 // TMEM lane quadrant (= warp % 4)
+    const int r = 32 * q + lane;            // tile row handled by this thread
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    int64_t seg = -1, cur_tile = -1;
+    bool ok = true;
+    for (int64_t it = it0; it < it1 && ok; ++it) {
+      const int64_t li = it - it0;
+      const int s = (int)(li % STAGES);
+      const uint32_t ph = (uint32_t)((li / STAGES) & 1);
+      const int64_t tile = it / P.kiters;
+      if (tile != cur_tile) {
+        cur_tile = tile;
+        ++seg;
+      }
+      if (!mbar_wait(&full[s], ph, abort_flag, P.d_info)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const unsigned char* st = dsm + s * SB;
+      float x[32];
+      if (FORM == 0) {
+        // 128B-swizzled rows of 32 fp32: 16-byte chunk c of row r sits at c ^ (r & 7)
+        const unsigned char* row = st + r * 128;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(row + ((c ^ (r & 7)) << 4));
+          x[4 * c] = v.x;
+          x[4 * c + 1] = v.y;
+          x[4 * c + 2] = v.z;
+          x[4 * c + 3] = v.w;
+        }
+      } else {
+        // plain 32 x 128 fp32 tile, row = k; this thread reads column r
+        const float* t = reinterpret_cast<const float*>(st);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) x[k] = t[k * BM + r];
+      }
+      uint32_t hi[16], lo[16];
+      split_row(x, hi, lo);
+      const uint32_t a_col = tmem + TMEM_A0 + 32u * (uint32_t)s;
+      tmem_st16(lane_base + a_col, hi);
+      tmem_st16(lane_base + a_col + 16u, lo);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+      const bool seg_end = (it + 1 == it1) || ((it + 1) / P.kiters != tile);
+      if (seg_end) {
+        if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag, P.d_info)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int64_t tile0 = it0 / P.kiters;
+        float* dst = P.part + ((int64_t)blockIdx.x * P.maxseg + (tile - tile0)) * (int64_t)BM * L;
+        for (int c0 = 0; c0 < L; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(lane_base + tmem + (uint32_t)c0, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) dst[(int64_t)(c0 + c) * BM + r] = __uint_as_float(v[c]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
+      }
+    }
+  } else if (OMEGA && warp >= 8 && warp < 8 + NGEN) {
+    // ------------------------- Omega generator warps --------------------------
+    const int gt = threadIdx.x - 8 * 32;   // 0 .. 255
+    const int nq = L / 4;
+    for (int64_t it = it0; it < it1; ++it) {
+      const int64_t li = it - it0;
+      const int s = (int)(li % STAGES);
+      const uint32_t ph = (uint32_t)((li / STAGES) & 1);
+      if (!mbar_wait(&done[s], ph ^ 1u, abort_flag, P.d_info)) break;
+      const int64_t kc = it % P.kiters;
+      unsigned char* wt = dsm + s * SB + A_STAGE_BYTES;
+      for (int e = gt; e < BK * nq; e += NGEN * 32) {
+        const int kk = e % BK, qd = e / BK;
+        const int64_t krow = kc * BK + kk;
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        if (krow < P.K && 4 * qd < P.lvalid)
+          OmegaGen<float>::quad(P.seed, (uint32_t)krow, (uint32_t)qd, z);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = 4 * qd + c;
+          const float val = (j < P.lvalid) ? z[c] : 0.0f;
+          const uint32_t off = (uint32_t)j * 64u + ((((uint32_t)kk >> 3) ^ (((uint32_t)j >> 1) & 3u)) << 4) +
+                               ((uint32_t)kk & 7u) * 2u;
+          *reinterpret_cast<__nv_bfloat16*>(wt + off) = __float2bfloat16_rn(val);
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&genb[s]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// Fixed-order sum of the stream-K partial tiles into the fp32 output (ld ldo,
+// columns < ncols) and, when hi != nullptr, the transposed bf16 hi/lo split
+// (L x rows, ld ldt) used as the stored operand of a later GEMM.
+__global__ void tc_reduce_kernel(TcParams P, int G, float* __restrict__ out, int64_t ldo,
+                                 int ncols, __nv_bfloat16* __restrict__ hi,
+                                 __nv_bfloat16* __restrict__ lo, int64_t ldt) {
+  if (P.skip && *P.skip) return;
+  __shared__ float tile_s[32][33];
+  const int64_t t = blockIdx.z;            // output tile
+  const int rg = blockIdx.x;               // 32-row group inside the tile
+  const int jg = blockIdx.y;               // 32-column group
+  const int L = P.L;
+  const int64_t first = t * P.kiters, last = (t + 1) * P.kiters - 1;
+  // contributors: CTAs whose stream-K range meets [first, last]
+  int64_t blo = (first * G) / P.total;
+  while (blo > 0 && (blo * P.total) / G > first) --blo;
+  while (((blo + 1) * P.total) / G <= first) ++blo;
+  int64_t bhi = (last * G) / P.total;
+  while (bhi > 0 && (bhi * P.total) / G > last) --bhi;
+  while (((bhi + 1) * P.total) / G <= last) ++bhi;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int j = jg * 32 + jj;
+    float sum = 0.f;
+    if (j < L) {
+      for (int64_t b = blo; b <= bhi; ++b) {
+        const int64_t tile0 = ((b * P.total) / G) / P.kiters;
+        const float* src = P.part + (b * P.maxseg + (t - tile0)) * (int64_t)BM * L;
+        sum += src[(int64_t)j * BM + rg * 32 + tx];
+      }
+    }
+    tile_s[jj][tx] = sum;
+  }
+  __syncthreads();
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t i = t * BM + rg * 32 + rr;
+    const int j = jg * 32 + tx;
+    if (i < P.rows && j < ncols) out[i * ldo + j] = tile_s[tx][rr];
+  }
+  if (hi) {
+    for (int jj = ty; jj < 32; jj += 8) {
+      const int j = jg * 32 + jj;
+      const int64_t i = t * BM + rg * 32 + tx;
+      if (j < L && i < P.rows) {
+        const float v = (j < ncols) ? tile_s[jj][tx] : 0.0f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[(int64_t)j * ldt + i] = h;
+        lo[(int64_t)j * ldt + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+      }
+    }
+  }
+}
+
+// ------------------------------- host side ---------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+static bool encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem, const void* base,
+                      uint64_t inner, uint64_t outer, uint64_t pitch_elems, uint32_t box_inner,
+                      uint32_t box_outer, CUtensorMapSwizzle sw) {
+  EncodeTiledFn fn = get_encode();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch_elems * (uint64_t)elem};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  return fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 148;
+  return sms;
+}
+
+bool tc_supported(int L) { return L >= 16 && L <= 256 && L % 16 == 0; }
+
+static void sk_plan(int64_t rows, int64_t K, int G_hint, int64_t* tiles, int64_t* kiters,
+                    int64_t* total, int64_t* G, int* maxseg) {
+  *tiles = ceil_div(rows, BM);
+  *kiters = ceil_div(K, BK);
+  *total = (*tiles) * (*kiters);
+  int64_t g = G_hint;
+  if (g > *total) g = *total;
+  if (g < 1) g = 1;
+  *G = g;
+  int ms = 1;
+  for (int64_t b = 0; b < g; ++b) {
+    const int64_t s = (b * (*total)) / g, e = ((b + 1) * (*total)) / g;
+    if (e <= s) continue;
+    const int segs = (int)((e - 1) / (*kiters) - s / (*kiters) + 1);
+    if (segs > ms) ms = segs;
+  }
+  *maxseg = ms;
+}
+
+size_t tc_part_bytes(int64_t rows, int64_t K, int L) {
+  int64_t tiles, kiters, total, G;
+  int maxseg;
+  sk_plan(rows, K, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);
+  return (size_t)G * maxseg * BM * L * sizeof(float);
+}
+
+template <int FORM, int NW>
+static cudaError_t launch_form(const CUtensorMap& ma, const CUtensorMap* mw, const TcParams& P,
+                               int G, size_t smem, cudaStream_t s) {
+  auto kern = tc_gemm_kernel<FORM, NW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  // trace classes (include/rsvd.h): 0 A Omega, 1 A W, 2 A^T W, 3 Gram, 4 orth apply
+  const int cls = FORM == 1 ? (NW == 4 ? RSVD_TRACE_GRAM : RSVD_TRACE_AT_W)
+                            : (NW == 1 ? RSVD_TRACE_A_OMEGA
+                                       : (NW == 3 ? RSVD_TRACE_APPLY : RSVD_TRACE_A_W));
+  const int tr = trace_begin(cls, s);
+  kern<<<G, NW == 1 ? 512 : 256, smem, s>>>(ma, mw[0], mw[1], mw[2], P);
+  count_launch();
+  trace_end(tr, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
+  if (!tc_supported(g.L)) return cudaErrorInvalidValue;
+  if (g.form == 1 && g.omega) return cudaErrorInvalidValue;
+  int64_t tiles, kiters, total, G;
+  int maxseg;
+  sk_plan(g.rows, g.K, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);
+  TcParams P;
+  P.rows = g.rows;
+  P.K = g.K;
+  P.L = g.L;
+  P.lvalid = g.lvalid;
+  P.seed = g.seed;
+  P.tiles = tiles;
+  P.kiters = kiters;
+  P.total = total;
+  P.maxseg = maxseg;
+  P.part = g.part;
+  P.skip = g.skip;
+  P.d_info = g.d_info;
+
+  CUtensorMap ma, mw[3];
+  memset(&ma, 0, sizeof(ma));
+  memset(mw, 0, sizeof(mw));
+  bool ok;
+  if (g.form == 0)
+    ok = encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, (uint64_t)g.a_cols_total,
+                   (uint64_t)g.a_rows_total, (uint64_t)g.lda, BK, BM,
+                   CU_TENSOR_MAP_SWIZZLE_128B);
+  else
+    ok = encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, (uint64_t)g.a_cols_total,
+                   (uint64_t)g.a_rows_total, (uint64_t)g.lda, BM, BK,
+                   CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (!ok) return cudaErrorInvalidValue;
+  const int nw = g.omega ? 1 : (g.gram ? 4 : g.wterms);
+  if (nw < 1 || nw > 4 || (nw == 1 && !g.omega) || (g.gram && g.wterms != 2))
+    return cudaErrorInvalidValue;
+  const int nwt = g.omega ? 0 : w_tiles(nw);
+  const void* wp[3] = {g.Whi, g.Wlo, g.Wlo2};
+  for (int t = 0; t < nwt; ++t) {
+    if (!wp[t]) return cudaErrorInvalidValue;
+    ok = encode_2d(&mw[t], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, wp[t], (uint64_t)g.K,
+                   (uint64_t)g.L, (uint64_t)g.ldw, BK, (uint32_t)g.L, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (!ok) return cudaErrorInvalidValue;
+  }
+  for (int t = nwt; t < 3; ++t) mw[t] = (g.omega ? ma : mw[0]);
+  const size_t smem = (size_t)stages_for(nw) * stage_bytes(g.L, nw) + 1024 /*align*/ +
+                      (4 * MAXST + 2) * 8 + 16;
+  cudaError_t e;
+  if (g.form == 0 && nw == 1)
+    e = launch_form<0, 1>(ma, mw, P, (int)G, smem, s);
+  else if (g.form == 0 && nw == 2)
+    e = launch_form<0, 2>(ma, mw, P, (int)G, smem, s);
+  else if (g.form == 0 && nw == 3)
+    e = launch_form<0, 3>(ma, mw, P, (int)G, smem, s);
+  else if (g.form == 1 && nw == 2)
+    e = launch_form<1, 2>(ma, mw, P, (int)G, smem, s);
+  else if (g.form == 1 && nw == 4)
+    e = launch_form<1, 4>(ma, mw, P, (int)G, smem, s);
+  else
+    return cudaErrorInvalidValue;
+  if (e != cudaSuccess) return e;
+  // fixed-order reduction of the partial tiles
+  dim3 rgrid(BM / 32, (unsigned)ceil_div(g.L, 32), (unsigned)tiles);
+  if (tiles > 65535) return cudaErrorInvalidConfiguration;
+  const int tr = trace_begin(RSVD_TRACE_REDUCE, s);
+  tc_reduce_kernel<<<rgrid, dim3(32, 8), 0, s>>>(P, (int)G, g.out, g.ldo, g.ncols,
+                                                 (__nv_bfloat16*)g.out_hi,
+                                                 (__nv_bfloat16*)g.out_lo, g.ldt);
+  count_launch();
+  trace_end(tr, s);
+  return cudaGetLastError();
+}
+
+}  // namespace rsvd

@@ -1,0 +1,175 @@
+// Host-side launchers of the library's kernels (internal; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsvd {
+
+// ----- Philox / Omega (k_philox.cu) ----------------------------------------
+template <typename T>
+cudaError_t launch_omega(int64_t n, int l, uint64_t seed, T* Om, int64_t ldo, cudaStream_t s);
+cudaError_t launch_omega_words(int64_t n, int l, uint64_t seed, uint32_t* out, cudaStream_t s);
+
+// ----- SIMT GEMMs (k_simt.cu) ----------------------------------------------
+// C (M x N) = A (M x K) * B (K x N); B = Omega(seed) when B == nullptr, with
+// columns >= nvalid of Omega set to zero.  Row-major, leading dimensions given.
+template <typename T>
+cudaError_t launch_gemm_nn(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda,
+                           const T* B, int64_t ldb, T* C, int64_t ldc, uint64_t seed,
+                           int64_t nvalid, cudaStream_t s);
+// Partial products of C (M x N) = A^T B with A (K x M), B (K x N): split-K slab
+// z writes P[z*M*ldp + i*ldp + j]; nsplit slabs of kchunk rows.
+template <typename T>
+cudaError_t launch_gemm_tn_partial(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda,
+                                   const T* B, int64_t ldb, T* P, int64_t ldp, int nsplit,
+                                   int64_t kchunk, cudaStream_t s);
+// out[i*ldo + j] = sum_z P[z*M*ldp + i*ldp + j] (fixed order), j < ncols.
+template <typename T>
+cudaError_t launch_reduce_slabs(int64_t M, int64_t ncols, int nsplit, const T* P, int64_t ldp,
+                                T* out, int64_t ldo, cudaStream_t s);
+// Choice of split-K for the TN GEMM so the grid covers the GPU.
+void tn_split(int64_t M, int64_t N, int64_t K, int num_sms, int* nsplit, int64_t* kchunk);
+
+// ----- small dense helpers (k_misc.cu) -------------------------------------
+template <typename TI, typename TO>
+cudaError_t launch_copy2d(int64_t rows, int64_t cols, const TI* in, int64_t ldi, TO* out,
+                          int64_t ldo, cudaStream_t s);
+template <typename TI, typename TO>
+cudaError_t launch_transpose(int64_t rows, int64_t cols, const TI* in, int64_t ldi, TO* out,
+                             int64_t ldo, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fill(int64_t rows, int64_t cols, T* out, int64_t ldo, T value,
+                        cudaStream_t s);
+// X (rows x cols fp32) -> hi/lo bf16 of X^T padded to L x rows (zeros for
+// columns >= cols): the stored-operand form of the tensor-core GEMMs.
+cudaError_t launch_split_transpose(int64_t rows, int cols, int L, const float* X, int64_t ldx,
+                                   void* hi, void* lo, int64_t ldt, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cond_copy(const int* flag, int64_t count, const T* in, T* out,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale_cols(int64_t rows, int k, T* X, int64_t ldx, const double* S,
+                              cudaStream_t s);
+cudaError_t launch_copy_i32(int64_t count, const int32_t* in, int32_t* out, cudaStream_t s);
+// Sign rule: s_j = sign of the largest-|.| entry of column j of V (n x k);
+// then U(:, j) *= s_j, V(:, j) *= s_j.
+template <typename T>
+cudaError_t launch_sign_fix(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V,
+                            int64_t ldv, int* signs, cudaStream_t s);
+// Gathers for ID/CUR.
+template <typename T>
+cudaError_t launch_gather_ct(int64_t m, int k, const T* A, int64_t lda, const int32_t* J,
+                             double* W, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather_rows(int k, int64_t n, const T* A, int64_t lda, const int32_t* I,
+                               T* R, int64_t ldr, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather_rows_by_perm(int64_t count, int cols, const T* X, int64_t ldx,
+                                       const int32_t* idx, T* out, int64_t ldo,
+                                       cudaStream_t s);
+template <typename T>
+cudaError_t launch_bt_to_w64(int64_t n, int l, const T* Bt, int64_t ldbt, double* W,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_add_inplace(int64_t rows, int64_t cols, const T* X, int64_t ldx, T* Y,
+                               int64_t ldy, cudaStream_t s);
+cudaError_t launch_check_finite_d(int64_t count, const double* x, int* d_info, cudaStream_t s);
+
+// ----- Cholesky + triangular inverse (k_chol.cu) ---------------------------
+struct CholArgs {
+  int l;          // true size
+  int L;          // padded size (outputs are L x L, identity on the padding)
+  const void* G;  // l x l Gram (ld ldg)
+  int64_t ldg;
+  void* R;        // L x L upper factor (ld L), may be null
+  void* Rinv;     // L x L inverse of R (ld L), may be null
+  void* Whi;      // L x L bf16: (Rinv)^T first term (tensor-core operand), may be null
+  void* Wlo;      // L x L bf16 second term
+  void* Wlo2;     // L x L bf16 third term
+  void* scratch;  // global fallback storage when the matrix does not fit in smem
+  int* flags;     // [0] third pass needed, [1] a shift was used, [2] = 1 - [0]
+  int pass;       // 1, 2 or 3
+  int* d_info;
+};
+template <typename T>
+cudaError_t launch_chol(const CholArgs& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_trmm_upper(int L, const T* R, T* Racc, T* tmp, cudaStream_t s);
+size_t chol_scratch_bytes(int l, int elem);
+
+// ----- Jacobi SVD (k_jacobi.cu) --------------------------------------------
+template <typename T>
+cudaError_t launch_jacobi(int l, const T* M, int64_t ldm, T* Uh, int64_t lduh, double* Sh,
+                          T* Vh, int64_t ldvh, T* scratch, int max_sweeps, int* d_info,
+                          cudaStream_t s);
+size_t jacobi_scratch_bytes(int l, int elem);
+template <typename T>
+cudaError_t launch_svd_finalize(int l, const T* P, int64_t ldp, const T* Uin, int64_t ldin, T* Uh,
+                                int64_t lduh, double* Sh, T* Vh, int64_t ldvh, int* d_info,
+                                cudaStream_t s);
+
+// ----- CPQR / ID (k_cpqr.cu) -----------------------------------------------
+struct CpqrArgs {
+  int r;            // rows of the sketch
+  int64_t n;        // columns
+  int k;            // steps
+  double* W;        // n x r, column c contiguous at W + c*r (overwritten)
+  int32_t* J;       // n permutation (output)
+  int64_t* where;   // n scratch: position of each original column
+  double* gaps;     // k (may be null)
+  double* pval;     // 2 * 1024 * 2 scratch (best, second per CTA)
+  int64_t* pidx;    // 2 * 1024 scratch
+  double* nrm;      // n scratch: residual norms^2 (-1 once pivoted)
+  double* diagR;    // k: diagonal of S (the Householder betas)
+  unsigned* bar;    // 1 counter, zeroed by the launcher
+  int* d_info;
+};
+cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s);
+size_t cpqr_scratch_bytes(int64_t n);
+// Upper-triangular solve for many right-hand sides:
+//   for c < ncols: U x = rhs(:, c), out(:, c) = x; U(i, t) = Ug[i*us_i + t*us_t].
+template <typename TR, typename TO>
+cudaError_t launch_upper_solve(int kk, int64_t ncols, const double* Ug, int64_t us_i,
+                               int64_t us_t, const TR* rhs, int64_t rs_i, int64_t rs_c,
+                               TO* out, int64_t os_i, int64_t os_c, int* d_info,
+                               cudaStream_t s);
+// S11 (k x k, column-major dense) and S12 columns from the CPQR working array.
+cudaError_t launch_id_extract(int r, int64_t n, int k, const double* W, const int32_t* J,
+                              const double* diagR, double* S11, double* S12, cudaStream_t s);
+
+// ----- tcgen05 tensor-core GEMMs (k_tc.cu) ---------------------------------
+struct TcGemm {
+  int form;             // 0: Y = A W (A rows x K), 1: Z = A^T W (A K x rows)
+  int omega;            // form 0 only: W = Omega(seed) generated in-kernel
+  uint64_t seed;
+  int64_t rows;         // output rows (M): rows of A (form 0) or columns of A (form 1)
+  int64_t K;            // contraction length
+  int L;                // output columns (multiple of 16, <= 256)
+  int lvalid;           // Omega columns >= lvalid are zero
+  const float* A;       // fp32 source, row-major, 16-byte aligned, lda % 4 == 0
+  int64_t lda;          // elements
+  int64_t a_rows_total; // rows of the A tensor (form 0: rows, form 1: K)
+  int64_t a_cols_total; // cols of the A tensor (form 0: K, form 1: rows)
+  int wterms;           // stored W: 2 (hi, lo) or 3 (hi, mid, lo) bf16 terms
+  int gram;             // form 1 with W = split of A itself: adds the lo*lo product
+  const void* Whi;      // L x K bf16 (K contiguous): leading term of W^T (stored W only)
+  const void* Wlo;      // second term
+  const void* Wlo2;     // third term (wterms == 3)
+  int64_t ldw;          // elements, multiple of 8
+  float* part;          // stream-K partial tiles (workspace, tc_part_bytes)
+  float* out;           // fp32 output rows x ncols (ld ldo)
+  int64_t ldo;
+  int ncols;
+  void* out_hi;         // optional: bf16 hi/lo of out^T (L x rows, ld ldt); padding zero
+  void* out_lo;
+  int64_t ldt;
+  const int* skip;      // when non-null and *skip == 1 the launch does nothing
+  int* d_info;
+};
+size_t tc_part_bytes(int64_t rows, int64_t K, int L);
+cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s);
+bool tc_supported(int L);
+int device_sm_count();
+
+}  // namespace rsvd

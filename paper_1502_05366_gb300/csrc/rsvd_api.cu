@@ -1,0 +1,1130 @@
+// C ABI of the library (include/rsvd.h) and the host-side launch sequences.
+//
+// Every entry point validates its arguments, carves the caller's workspace
+// with a bump allocator (the same code computes the *_workspace_size values
+// by running without launching), and enqueues kernels on the caller's stream.
+// Nothing is allocated and the host never waits for the device.
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsvd {
+
+// ------------------------------------------------------------------------
+// options, workspace arena, launch context
+// ------------------------------------------------------------------------
+struct Opts {
+  int s = 1, max_sweeps = 30, precision = RSVD_PREC_TC;
+};
+
+static bool read_opts(const rsvd_opts* o, Opts* out) {
+  Opts d;
+  if (o) {
+    if (o->s < 1 || o->max_sweeps < 1 || o->max_sweeps > 1000) return false;
+    if (o->precision != RSVD_PREC_TC && o->precision != RSVD_PREC_SIMT) return false;
+    for (int i = 0; i < 13; ++i)
+      if (o->reserved[i] != 0) return false;
+    d.s = o->s;
+    d.max_sweeps = o->max_sweeps;
+    d.precision = o->precision;
+  }
+  *out = d;
+  return true;
+}
+
+struct Ctx {
+  bool dry = true;
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  cudaStream_t stream = nullptr;
+  int* d_info = nullptr;
+  cudaError_t err = cudaSuccess;
+
+  template <typename T>
+  T* take(size_t count) {
+    off = (size_t)round_up((int64_t)off, 256);
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T) + 16;
+    return p;
+  }
+  bool run(cudaError_t e) {
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    return e == cudaSuccess;
+  }
+};
+
+#define LK(...)                                      \
+  do {                                               \
+    if (!c.dry) {                                    \
+      if (!c.run(__VA_ARGS__)) return RSVD_ERR_CUDA; \
+    }                                                \
+  } while (0)
+
+static inline int padL(int l) { return (int)round_up(l, 16); }
+static inline int64_t pad8(int64_t r) { return round_up(r, 8); }
+
+// ------------------------------------------------------------------------
+// Engine: the path for one element type.  T = float uses the tensor-core GEMMs
+// (unless the SIMT option is chosen or A is not TMA-addressable); T = double
+// runs the SIMT FP64 kernels.
+// ------------------------------------------------------------------------
+template <typename T>
+struct Engine {
+  Ctx& c;
+  Opts o;
+  bool tc;
+  int sms;
+  explicit Engine(Ctx& ctx, const Opts& op, bool use_tc) : c(ctx), o(op), tc(use_tc) {
+    sms = device_sm_count();
+  }
+
+  // Split-transposed bf16 operand buffers (L x ld rows).
+  struct Split {
+    void* hi = nullptr;
+    void* lo = nullptr;
+    int64_t ld = 0;
+    void* lo2 = nullptr;   // third term (R^-1 operands only)
+  };
+  Split take_split(int L, int64_t rows) {
+    Split s;
+    s.ld = pad8(rows);
+    s.hi = c.template take<uint16_t>((size_t)L * s.ld);
+    s.lo = c.template take<uint16_t>((size_t)L * s.ld);
+    return s;
+  }
+
+  // ---------------- GEMM building blocks ----------------
+  // Y (rows x L) = A (rows x K) * W.  omega: W = Omega(seed) with lvalid columns.
+  rsvd_status gemm_n(int64_t rows, int64_t K, int L, const T* A, int64_t lda, int64_t a_rows,
+                     int64_t a_cols, bool omega, uint64_t seed, int lvalid, const Split* w,
+                     const T* Wsimt, int64_t ldws, T* out, int64_t ldo, int ncols, Split* out_split,
+                     float* part, const int* skip) {
+    if (tc) {
+      TcGemm g{};
+      g.form = 0;
+      g.omega = omega ? 1 : 0;
+      g.seed = seed;
+      g.rows = rows;
+      g.K = K;
+      g.L = L;
+      g.lvalid = lvalid;
+      g.A = (const float*)A;
+      g.lda = lda;
+      g.a_rows_total = a_rows;
+      g.a_cols_total = a_cols;
+      g.Whi = w ? w->hi : nullptr;
+      g.Wlo = w ? w->lo : nullptr;
+      g.Wlo2 = w ? w->lo2 : nullptr;
+      g.wterms = (w && w->lo2) ? 3 : 2;
+      g.ldw = w ? w->ld : 0;
+      g.part = part;
+      g.out = (float*)out;
+      g.ldo = ldo;
+      g.ncols = ncols;
+      g.out_hi = out_split ? out_split->hi : nullptr;
+      g.out_lo = out_split ? out_split->lo : nullptr;
+      g.ldt = out_split ? out_split->ld : 0;
+      g.skip = skip;
+      g.d_info = c.d_info;
+      LK(launch_tc_gemm(g, c.stream));
+    } else {
+      LK(launch_gemm_nn<T>(rows, ncols, K, A, lda, omega ? nullptr : Wsimt, ldws, out, ldo,
+                           seed, lvalid, c.stream));
+    }
+    return RSVD_OK;
+  }
+
+  // Z (rows x L) = A^T W with A (K x rows).
+  rsvd_status gemm_t(int64_t rows, int64_t K, int L, const T* A, int64_t lda, const Split* w,
+                     const T* Wsimt, int64_t ldws, T* out, int64_t ldo, int ncols,
+                     Split* out_split, float* part, T* slabs, const int* skip, bool gram = false) {
+    if (tc) {
+      TcGemm g{};
+      g.form = 1;
+      g.rows = rows;
+      g.K = K;
+      g.L = L;
+      g.lvalid = L;
+      g.A = (const float*)A;
+      g.lda = lda;
+      g.a_rows_total = K;
+      g.a_cols_total = rows;
+      g.Whi = w->hi;
+      g.Wlo = w->lo;
+      g.Wlo2 = nullptr;
+      g.wterms = 2;
+      g.gram = gram ? 1 : 0;
+      g.ldw = w->ld;
+      g.part = part;
+      g.out = (float*)out;
+      g.ldo = ldo;
+      g.ncols = ncols;
+      g.out_hi = out_split ? out_split->hi : nullptr;
+      g.out_lo = out_split ? out_split->lo : nullptr;
+      g.ldt = out_split ? out_split->ld : 0;
+      g.skip = skip;
+      g.d_info = c.d_info;
+      LK(launch_tc_gemm(g, c.stream));
+    } else {
+      int ns;
+      int64_t kc;
+      tn_split(rows, ncols, K, sms, &ns, &kc);
+      LK(launch_gemm_tn_partial<T>(rows, ncols, K, A, lda, Wsimt, ldws, slabs, ncols, ns, kc,
+                                   c.stream));
+      LK(launch_reduce_slabs<T>(rows, ncols, ns, slabs, ncols, out, ldo, c.stream));
+    }
+    return RSVD_OK;
+  }
+
+  // Scratch sizes for GEMMs of the given shapes.
+  size_t part_bytes_n(int64_t rows, int64_t K, int L) {
+    return tc ? tc_part_bytes(rows, K, L) : 0;
+  }
+  size_t slab_elems_t(int64_t rows, int64_t K, int ncols) {
+    if (tc) return 0;
+    int ns;
+    int64_t kc;
+    tn_split(rows, ncols, K, sms, &ns, &kc);
+    return (size_t)ns * rows * ncols;
+  }
+
+  // ---------------- orth: CholeskyQR with two or three passes ----------------
+  struct OrthBufs {
+    T* G;        // L x L
+    T* R;        // L x L
+    T* Rinv;     // L x L
+    T* Racc;     // L x L
+    T* tmpLL;    // L x L
+    void* Whi;   // L x L bf16, three terms of (R^-1)^T
+    void* Wlo;
+    void* Wlo2;
+    int* flags;  // 4 ints
+    T* chol_scratch;
+  };
+  OrthBufs take_orth_bufs(int L) {
+    OrthBufs b;
+    b.G = c.template take<T>((size_t)L * L);
+    b.R = c.template take<T>((size_t)L * L);
+    b.Rinv = c.template take<T>((size_t)L * L);
+    b.Racc = c.template take<T>((size_t)L * L);
+    b.tmpLL = c.template take<T>((size_t)L * L);
+    b.Whi = c.template take<uint16_t>((size_t)L * L);
+    b.Wlo = c.template take<uint16_t>((size_t)L * L);
+    b.Wlo2 = c.template take<uint16_t>((size_t)L * L);
+    b.flags = c.template take<int>(4);
+    const size_t cs = chol_scratch_bytes(L, sizeof(T));
+    b.chol_scratch = cs ? c.template take<T>(cs / sizeof(T)) : nullptr;
+    return b;
+  }
+
+  // X (rows x L, l valid columns, zero padding) -> Q in Y (rows x L).  For the
+  // tensor-core path `split` holds the hi/lo of X^T on entry and of Q^T on exit.
+  // When want_R, ob.Racc ends as R with X = Q R.
+  rsvd_status orth(int64_t rows, int l, int L, T* X, T* Y, Split* split, OrthBufs& ob,
+                   float* part, T* slabs, bool want_R) {
+    LK(cudaMemsetAsync(ob.flags, 0, 4 * sizeof(int), c.stream));
+    T* src = X;
+    T* dst = Y;
+    for (int pass = 1; pass <= 3; ++pass) {
+      const int* skip = (pass == 3) ? ob.flags + 2 : nullptr;
+      // Gram G = src^T src
+      rsvd_status st = gemm_t(L, rows, L, src, L, split, src, L, ob.G, L, L, nullptr, part, slabs,
+                              skip, true);
+      if (st != RSVD_OK) return st;
+      CholArgs a{};
+      a.l = l;
+      a.L = L;
+      a.G = ob.G;
+      a.ldg = L;
+      a.R = ob.R;
+      a.Rinv = ob.Rinv;
+      a.Whi = tc ? ob.Whi : nullptr;
+      a.Wlo = tc ? ob.Wlo : nullptr;
+      a.Wlo2 = tc ? ob.Wlo2 : nullptr;
+      a.scratch = ob.chol_scratch;
+      a.flags = ob.flags;
+      a.pass = pass;
+      a.d_info = c.d_info;
+      LK(launch_chol<T>(a, c.stream));
+      if (want_R) {
+        if (pass == 1)
+          LK(cudaMemcpyAsync(ob.Racc, ob.R, sizeof(T) * L * L, cudaMemcpyDeviceToDevice,
+                             c.stream));
+        else
+          LK(launch_trmm_upper<T>(L, ob.R, ob.Racc, ob.tmpLL, c.stream));
+      }
+      // apply: dst = src R^{-1}
+      Split w{ob.Whi, ob.Wlo, L, ob.Wlo2};
+      st = gemm_n(rows, L, L, src, L, rows, L, false, 0, L, &w, ob.Rinv, L, dst, L, L, split,
+                  part, skip);
+      if (st != RSVD_OK) return st;
+      if (pass == 3 && tc) {  // third pass skipped: Q2 carried over unchanged
+        if (!c.dry) {
+          if (!c.run(launch_cond_copy<float>(ob.flags + 2, rows * (int64_t)L, (const float*)src,
+                                             (float*)dst, c.stream)))
+            return RSVD_ERR_CUDA;
+        }
+      }
+      T* t = src;
+      src = dst;
+      dst = t;
+    }
+    // after three passes the result sits in Y (X -> Y -> X -> Y)
+    return RSVD_OK;
+  }
+
+  // ---------------- QB: range finder + power scheme + Bt ----------------
+  struct QBBufs {
+    T* Y;        // m x L
+    T* Ytmp;     // m x L
+    T* Z;        // n x L
+    T* Ztmp;     // n x L
+    Split ys, zs;
+    float* part;
+    T* slabs;
+    OrthBufs ob;
+  };
+
+  QBBufs take_qb(int64_t m, int64_t n, int L) {
+    QBBufs b;
+    b.Y = c.template take<T>((size_t)m * L);
+    b.Ytmp = c.template take<T>((size_t)m * L);
+    b.Z = c.template take<T>((size_t)n * L);
+    b.Ztmp = c.template take<T>((size_t)n * L);
+    if (tc) {
+      b.ys = take_split(L, m);
+      b.zs = take_split(L, n);
+    }
+    size_t pb = 0;
+    if (tc) {
+      pb = std::max(pb, tc_part_bytes(m, n, L));   // Y = A Omega, Y = A Z
+      pb = std::max(pb, tc_part_bytes(n, m, L));   // Z = A^T Y, Bt
+      pb = std::max(pb, tc_part_bytes(L, m, L));   // Gram of m-row X
+      pb = std::max(pb, tc_part_bytes(L, n, L));   // Gram of n-row X
+      pb = std::max(pb, tc_part_bytes(m, L, L));   // apply on m rows
+      pb = std::max(pb, tc_part_bytes(n, L, L));   // apply on n rows
+    }
+    b.part = pb ? c.template take<float>(pb / sizeof(float)) : nullptr;
+    size_t se = 0;
+    if (!tc) {
+      se = std::max(se, slab_elems_t(n, m, L));
+      se = std::max(se, slab_elems_t(L, m, L));
+      se = std::max(se, slab_elems_t(L, n, L));
+    }
+    b.slabs = se ? c.template take<T>(se) : nullptr;
+    b.ob = take_orth_bufs(L);
+    return b;
+  }
+
+  // On exit: b.Y holds Q (m x L, padded), b.Z holds Bt (n x L, padded); for
+  // the tensor-core path b.zs holds the split of Bt^T.
+  rsvd_status qb(QBBufs& b, int64_t m, int64_t n, int l, int q, uint64_t seed, const T* A,
+                 int64_t lda) {
+    const int L = padL(l);
+    rsvd_status st;
+    if (!tc) LK(launch_fill<T>(m, L, b.Y, L, T(0), c.stream));
+    // Y = A Omega (Fig. 1 step 2)
+    st = gemm_n(m, n, L, A, lda, m, n, true, seed, l, nullptr, nullptr, 0, b.Y, L, L, &b.ys,
+                b.part, nullptr);
+    if (st != RSVD_OK) return st;
+    int prod = 0;  // index of the next product with A or A^T (Alg. 5 orth test)
+    for (int j = 1; j <= q; ++j) {
+      if (prod % o.s == 0) {
+        st = orth(m, l, L, b.Y, b.Ytmp, &b.ys, b.ob, b.part, b.slabs, false);
+        if (st != RSVD_OK) return st;
+        std::swap(b.Y, b.Ytmp);
+      }
+      ++prod;
+      // Z = A^* Y (Sec. 3.2)
+      st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr);
+      if (st != RSVD_OK) return st;
+      if (prod % o.s == 0) {
+        st = orth(n, l, L, b.Z, b.Ztmp, &b.zs, b.ob, b.part, b.slabs, false);
+        if (st != RSVD_OK) return st;
+        std::swap(b.Z, b.Ztmp);
+      }
+      ++prod;
+      // Y = A Z
+      st = gemm_n(m, n, L, A, lda, m, n, false, 0, L, &b.zs, b.Z, L, b.Y, L, L, &b.ys, b.part,
+                  nullptr);
+      if (st != RSVD_OK) return st;
+    }
+    // Q = orth(Y)
+    st = orth(m, l, L, b.Y, b.Ytmp, &b.ys, b.ob, b.part, b.slabs, false);
+    if (st != RSVD_OK) return st;
+    std::swap(b.Y, b.Ytmp);
+    // Bt = A^* Q (Alg. 5)
+    st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr);
+    return st;
+  }
+
+  // ---------------- small SVD of R-hat and lift (Alg. 5 tail) ----------------
+  struct SvdBufs {
+    T* Uh;       // L x L
+    T* Vh;       // L x L
+    double* Sh;  // L
+    T* Uj;       // l x l: Jacobi's left vectors before the final sort
+    T* P;        // l x l: M^T Uj
+    double* Sj;  // l
+    T* jac_scratch;
+    T* vslabs;
+    int* signs;
+  };
+  SvdBufs take_svd(int l, int L, int k) {
+    SvdBufs s;
+    s.Uh = c.template take<T>((size_t)L * L);
+    s.Vh = c.template take<T>((size_t)L * L);
+    s.Sh = c.template take<double>((size_t)L);
+    s.Uj = c.template take<T>((size_t)l * l);
+    s.P = c.template take<T>((size_t)l * l);
+    s.Sj = c.template take<double>((size_t)l);
+    const size_t js = jacobi_scratch_bytes(l, sizeof(T));
+    s.jac_scratch = js ? c.template take<T>(js / sizeof(T)) : nullptr;
+    int ns;
+    int64_t kc;
+    tn_split(l, l, l, sms, &ns, &kc);
+    s.vslabs = c.template take<T>((size_t)ns * l * l);
+    s.signs = c.template take<int>((size_t)k + 1);
+    return s;
+  }
+
+  // M (l x l, ldm) = Uh diag(Sh) Vh^T: Jacobi for the left vectors, then
+  // P = M^T Uh, sigma_j = ||P(:, j)||, Vh = P diag(1/sigma), sorted.
+  rsvd_status small_svd(int l, const T* M, int64_t ldm, SvdBufs& s, T* Uh, int64_t lduh,
+                        double* Sh, T* Vh, int64_t ldvh) {
+    LK(launch_jacobi<T>(l, M, ldm, s.Uj, l, s.Sj, nullptr, 0, s.jac_scratch, o.max_sweeps,
+                        c.d_info, c.stream));
+    int ns;
+    int64_t kc;
+    tn_split(l, l, l, sms, &ns, &kc);
+    LK(launch_gemm_tn_partial<T>(l, l, l, M, ldm, s.Uj, l, s.vslabs, l, ns, kc, c.stream));
+    LK(launch_reduce_slabs<T>(l, l, ns, s.vslabs, l, s.P, l, c.stream));
+    LK(launch_svd_finalize<T>(l, s.P, l, s.Uj, l, Uh, lduh, Sh, Vh, ldvh, c.d_info, c.stream));
+    return RSVD_OK;
+  }
+
+  // From QB: U = Q Vh(:, :k), V = Qh Uh(:, :k), S = Sh(:k), signs fixed.
+  rsvd_status svd_from_qb(QBBufs& b, SvdBufs& s, int64_t m, int64_t n, int k, int l, T* U,
+                          int64_t ldu, double* S, T* V, int64_t ldv) {
+    const int L = padL(l);
+    // [Qh, Rh] = qr(Bt): Qh into Ztmp, Rh = Racc
+    rsvd_status st = orth(n, l, L, b.Z, b.Ztmp, &b.zs, b.ob, b.part, b.slabs, true);
+    if (st != RSVD_OK) return st;
+    T* Qh = b.Ztmp;
+    st = small_svd(l, b.ob.Racc, L, s, s.Uh, L, s.Sh, s.Vh, L);
+    if (st != RSVD_OK) return st;
+    LK(launch_gemm_nn<T>(m, k, l, b.Y, L, s.Vh, L, U, ldu, 0, k, c.stream));   // U = Q Vh
+    LK(launch_gemm_nn<T>(n, k, l, Qh, L, s.Uh, L, V, ldv, 0, k, c.stream));    // V = Qh Uh
+    LK(launch_sign_fix<T>(m, n, k, U, ldu, V, ldv, s.signs, c.stream));
+    LK(cudaMemcpyAsync(S, s.Sh, sizeof(double) * k, cudaMemcpyDeviceToDevice, c.stream));
+    return RSVD_OK;
+  }
+
+  // ---------------- ID (Sec. 3.5) and CUR (Sec. 3.6) ----------------
+  struct IdBufs {
+    double* W;       // n x r
+    int64_t* where;  // n
+    double* pval;
+    int64_t* pidx;
+    double* nrm;     // n
+    double* diagR;   // k
+    unsigned* bar;
+    double* S11;     // k x k
+    double* S12;     // (n-k) x k
+    int32_t* J;      // n (internal copy)
+    T* Tt;           // (n-k) x k
+  };
+  IdBufs take_id(int r, int64_t n, int k, bool with_T = true) {
+    IdBufs d;
+    d.W = c.template take<double>((size_t)n * r);
+    d.where = c.template take<int64_t>((size_t)n);
+    d.pval = c.template take<double>(2 * 1024 * 2);
+    d.pidx = c.template take<int64_t>(2 * 1024);
+    d.nrm = c.template take<double>((size_t)n);
+    d.diagR = c.template take<double>((size_t)k);
+    d.bar = c.template take<unsigned>(4);
+    d.J = c.template take<int32_t>((size_t)n);
+    if (with_T) {
+      d.S11 = c.template take<double>((size_t)k * k);
+      d.S12 = c.template take<double>((size_t)(n - k) * k + 1);
+      d.Tt = c.template take<T>((size_t)(n - k) * k + 1);
+    } else {
+      d.S11 = nullptr;
+      d.S12 = nullptr;
+      d.Tt = nullptr;
+    }
+    return d;
+  }
+
+  // CPQR of the r x n matrix whose column c is d.W[c*r .. c*r + r) (already
+  // filled), k steps; J into d.J; Tt ((n-k) x k) = (S11^{-1} S12)^T.
+  rsvd_status id_core(IdBufs& d, int r, int64_t n, int k, double* gaps) {
+    CpqrArgs a{};
+    a.r = r;
+    a.n = n;
+    a.k = k;
+    a.W = d.W;
+    a.J = d.J;
+    a.where = d.where;
+    a.gaps = gaps;
+    a.pval = d.pval;
+    a.pidx = d.pidx;
+    a.nrm = d.nrm;
+    a.diagR = d.diagR;
+    a.bar = d.bar;
+    a.d_info = c.d_info;
+    int grid = 0;
+    LK(launch_cpqr(a, &grid, c.stream));
+    if (!d.Tt) return RSVD_OK;   // pivots only (row ID of the CUR)
+    LK(launch_id_extract(r, n, k, d.W, d.J, d.diagR, d.S11, d.S12, c.stream));
+    // S11 column-major: U(i, t) = S11[t*k + i]; rhs(i, c) = S12[c*k + i];
+    // out Tt(c, i) = Tt[c*k + i]
+    LK(launch_upper_solve<double, T>(k, n - k, d.S11, 1, k, d.S12, 1, k, d.Tt, 1, k, c.d_info,
+                                     c.stream));
+    return RSVD_OK;
+  }
+
+  struct CurBufs {
+    IdBufs rid;       // row ID of C^T: r = k, n = m
+    T* R;             // k x n
+    T* RT;            // n x Kp
+    T* RTtmp;         // n x Kp
+    Split rts;
+    OrthBufs ob;
+    float* part;
+    T* slabs;
+    T* QRg;           // (n-k) x Kp
+    T* M1;            // k x Kp
+    T* M1b;           // k x Kp
+    T* mslabs;
+    double* RR64;     // Kp x Kp
+  };
+  CurBufs take_cur(int64_t m, int64_t n, int k) {
+    CurBufs u;
+    const int Kp = padL(k);
+    u.rid = take_id(k, m, k, false);
+    u.R = c.template take<T>((size_t)k * n);
+    u.RT = c.template take<T>((size_t)n * Kp);
+    u.RTtmp = c.template take<T>((size_t)n * Kp);
+    if (tc) u.rts = take_split(Kp, n);
+    u.ob = take_orth_bufs(Kp);
+    size_t pb = 0;
+    if (tc) {
+      pb = std::max(pb, tc_part_bytes(Kp, n, Kp));
+      pb = std::max(pb, tc_part_bytes(n, Kp, Kp));
+    }
+    u.part = pb ? c.template take<float>(pb / sizeof(float)) : nullptr;
+    const size_t se = tc ? 0 : slab_elems_t(Kp, n, Kp);
+    u.slabs = se ? c.template take<T>(se) : nullptr;
+    u.QRg = c.template take<T>((size_t)(n - k) * Kp + 1);
+    u.M1 = c.template take<T>((size_t)k * Kp);
+    u.M1b = c.template take<T>((size_t)k * Kp);
+    int ns;
+    int64_t kc;
+    tn_split(k, Kp, n - k, sms, &ns, &kc);
+    u.mslabs = c.template take<T>((size_t)ns * k * Kp);
+    u.RR64 = c.template take<double>((size_t)Kp * Kp);
+    return u;
+  }
+
+  // CUR from the column ID (J in idb.J, Tt): Jc, Ir, Ucur.
+  rsvd_status cur_from_id(CurBufs& u, IdBufs& idb, int64_t m, int64_t n, int k, const T* A,
+                          int64_t lda, int32_t* Jc, int32_t* Ir, T* Ucur, int64_t ldu,
+                          double* rgaps) {
+    const int Kp = padL(k);
+    // C^T columns (rows of C = A(:, J[:k])) in the CPQR layout
+    LK(launch_gather_ct<T>(m, k, A, lda, idb.J, u.rid.W, c.stream));
+    rsvd_status st = id_core(u.rid, k, m, k, rgaps);
+    if (st != RSVD_OK) return st;
+    if (Jc) LK(launch_copy_i32(k, idb.J, Jc, c.stream));
+    if (Ir) LK(launch_copy_i32(k, u.rid.J, Ir, c.stream));
+    // R = A(I, :), R^T (n x Kp, zero padded)
+    LK(launch_gather_rows<T>(k, n, A, lda, u.rid.J, u.R, n, c.stream));
+    LK(cudaMemsetAsync(u.RT, 0, sizeof(T) * n * Kp, c.stream));
+    LK(launch_transpose<T, T>(k, n, u.R, n, u.RT, Kp, c.stream));
+    if (tc)
+      LK(launch_split_transpose(n, Kp, Kp, (const float*)u.RT, Kp, u.rts.hi, u.rts.lo, u.rts.ld,
+                                c.stream));
+    // R^* = Q_R R_R
+    st = orth(n, k, Kp, u.RT, u.RTtmp, &u.rts, u.ob, u.part, u.slabs, true);
+    if (st != RSVD_OK) return st;
+    const T* QR = u.RTtmp;
+    // M1 = V^* Q_R = Q_R(J[:k], :) + T Q_R(J[k:], :)
+    LK(launch_gather_rows_by_perm<T>(n - k, Kp, QR, Kp, idb.J + k, u.QRg, Kp, c.stream));
+    int ns;
+    int64_t kc;
+    tn_split(k, Kp, n - k, sms, &ns, &kc);
+    LK(launch_gemm_tn_partial<T>(k, Kp, n - k, idb.Tt, k, u.QRg, Kp, u.mslabs, Kp, ns, kc,
+                                 c.stream));
+    LK(launch_reduce_slabs<T>(k, Kp, ns, u.mslabs, Kp, u.M1, Kp, c.stream));
+    LK(launch_gather_rows_by_perm<T>(k, Kp, QR, Kp, idb.J, u.M1b, Kp, c.stream));
+    LK(launch_add_inplace<T>(k, Kp, u.M1b, Kp, u.M1, Kp, c.stream));
+    // U R_R^T = M1  ->  R_R U(c, :)^T = M1(c, :)^T
+    LK(launch_copy2d<T, double>(Kp, Kp, u.ob.Racc, Kp, u.RR64, Kp, c.stream));
+    LK(launch_upper_solve<T, T>(k, k, u.RR64, Kp, 1, u.M1, 1, Kp, Ucur, 1, ldu, c.d_info,
+                                c.stream));
+    return RSVD_OK;
+  }
+};
+
+// ------------------------------------------------------------------------
+// argument checks
+// ------------------------------------------------------------------------
+static bool base_args_ok(int64_t m, int64_t n, int k, int p, int q, int dtype) {
+  if (dtype != RSVD_F32 && dtype != RSVD_F64) return false;
+  if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 64) return false;
+  const int64_t l = (int64_t)k + p;
+  if (l > m || l > n || l > 1024) return false;
+  if (m > 0x7fffffffLL || n > 0x7fffffffLL) return false;
+  return true;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Tensor-core path usable: FP32, requested, width fits, A TMA-addressable.
+static bool want_tc(int dtype, const Opts& o, int l, const void* A, int64_t lda) {
+  if (dtype != RSVD_F32 || o.precision != RSVD_PREC_TC) return false;
+  if (!tc_supported(padL(l))) return false;
+  if (A && !aligned16(A)) return false;
+  if (lda % 4 != 0) return false;
+  return true;
+}
+
+static void reset_info(Ctx& c) {
+  if (c.d_info && !c.dry) c.run(cudaMemsetAsync(c.d_info, 0, sizeof(int), c.stream));
+}
+
+enum Want { W_Q = 1, W_SVD = 2, W_ID = 4, W_CUR = 8 };
+
+template <typename T>
+static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n, int k, int p,
+                           int q, uint64_t seed, const T* A, int64_t lda, int want, T* Qo,
+                           int64_t ldq, T* Bto, int64_t ldbt, T* U, int64_t ldu, double* S, T* V,
+                           int64_t ldv, int32_t* J, T* Tout, int64_t ldt, int32_t* Jc,
+                           int32_t* Ir, T* Ucur, int64_t lducur) {
+  Engine<T> e(c, o, tc);
+  const int l = k + p, L = padL(l);
+  auto qbb = e.take_qb(m, n, L);
+  typename Engine<T>::SvdBufs sb{};
+  if (want & W_SVD) sb = e.take_svd(l, L, k);
+  typename Engine<T>::IdBufs idb{};
+  if (want & (W_ID | W_CUR)) idb = e.take_id(l, n, k);
+  typename Engine<T>::CurBufs cb{};
+  if (want & W_CUR) cb = e.take_cur(m, n, k);
+  if (c.dry) return RSVD_OK;
+  if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
+
+  reset_info(c);
+  rsvd_status st = e.qb(qbb, m, n, l, q, seed, A, lda);
+  if (st != RSVD_OK) return st;
+  if (want & W_Q) {
+    if (Qo) LK(launch_copy2d<T, T>(m, l, qbb.Y, L, Qo, ldq, c.stream));
+    if (Bto) LK(launch_copy2d<T, T>(n, l, qbb.Z, L, Bto, ldbt, c.stream));
+  }
+  if (want & (W_ID | W_CUR)) {
+    // B = Bt^T: column j of B is row j of Bt (before the SVD overwrites nothing of Bt)
+    LK(launch_copy2d<T, double>(n, l, qbb.Z, L, idb.W, l, c.stream));
+    st = e.id_core(idb, l, n, k, nullptr);
+    if (st != RSVD_OK) return st;
+    if (J) LK(launch_copy_i32(n, idb.J, J, c.stream));
+    if (Tout) LK(launch_transpose<T, T>(n - k, k, idb.Tt, k, Tout, ldt, c.stream));
+  }
+  if (want & W_SVD) {
+    st = e.svd_from_qb(qbb, sb, m, n, k, l, U, ldu, S, V, ldv);
+    if (st != RSVD_OK) return st;
+  }
+  if (want & W_CUR) {
+    st = e.cur_from_id(cb, idb, m, n, k, A, lda, Jc, Ir, Ucur, lducur, nullptr);
+    if (st != RSVD_OK) return st;
+  }
+  return RSVD_OK;
+}
+
+template <typename T>
+static size_t size_all(const Opts& o, bool tc, int64_t m, int64_t n, int k, int p, int want) {
+  Ctx c;
+  c.dry = true;
+  run_all<T>(c, o, tc, m, n, k, p, 0, 0, nullptr, 0, want, nullptr, 0, nullptr, 0, nullptr, 0,
+             nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr, 0);
+  return c.off + 256;
+}
+
+static size_t ws_query(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                       const rsvd_opts* opts, int want) {
+  Opts o;
+  if (!read_opts(opts, &o) || !base_args_ok(m, n, k, p, q, dtype)) return 0;
+  const bool tc = want_tc(dtype, o, k + p, nullptr, 0);
+  if (dtype == RSVD_F64) return size_all<double>(o, false, m, n, k, p, want);
+  // Both variants may be chosen at call time (alignment of A): report the max.
+  size_t s1 = size_all<float>(o, false, m, n, k, p, want);
+  size_t s2 = tc ? size_all<float>(o, true, m, n, k, p, want) : 0;
+  return s1 > s2 ? s1 : s2;
+}
+
+static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                            const void* A, int64_t lda, int want, void* Qo, int64_t ldq,
+                            void* Bto, int64_t ldbt, void* U, int64_t ldu, double* S, void* V,
+                            int64_t ldv, int32_t* J, void* Tout, int64_t ldt, int32_t* Jc,
+                            int32_t* Ir, void* Ucur, int64_t lducur, void* work,
+                            size_t work_bytes, int* d_info, void* stream,
+                            const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o)) return RSVD_ERR_INVALID_ARG;
+  if (!base_args_ok(m, n, k, p, q, dtype)) {
+    if (dtype == RSVD_BF16) return RSVD_ERR_UNSUPPORTED;
+    return RSVD_ERR_INVALID_ARG;
+  }
+  if (!A || lda < n) return RSVD_ERR_INVALID_ARG;
+  const int l = k + p;
+  if ((want & W_Q) && ((Qo && ldq < l) || (Bto && ldbt < l) || (!Qo && !Bto)))
+    return RSVD_ERR_INVALID_ARG;
+  if ((want & W_SVD) && (!U || !S || !V || ldu < k || ldv < k)) return RSVD_ERR_INVALID_ARG;
+  if ((want & W_ID) && (k >= n) ) return RSVD_ERR_INVALID_ARG;
+  if (want & W_ID) {
+    if (!J && !Tout) return RSVD_ERR_INVALID_ARG;
+    if (Tout && ldt < n - k) return RSVD_ERR_INVALID_ARG;
+  }
+  if ((want & W_CUR) && (!Jc || !Ir || !Ucur || lducur < k || k >= n || k >= m))
+    return RSVD_ERR_INVALID_ARG;
+  if ((want & (W_ID | W_CUR)) && k > 2048) return RSVD_ERR_UNSUPPORTED;
+  if (!work && work_bytes) return RSVD_ERR_INVALID_ARG;
+  if (work && !aligned16(work)) return RSVD_ERR_INVALID_ARG;
+  Ctx c;
+  c.dry = false;
+  c.base = (char*)work;
+  c.cap = work_bytes;
+  c.stream = (cudaStream_t)stream;
+  c.d_info = d_info;
+  rsvd_status st;
+  if (dtype == RSVD_F64) {
+    // workspace check first (dry pass with the same carving)
+    Ctx d;
+    run_all<double>(d, o, false, m, n, k, p, q, seed, nullptr, lda, want, nullptr, 0, nullptr, 0,
+                    nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr,
+                    nullptr, 0);
+    if (d.off > work_bytes) return RSVD_ERR_WORKSPACE;
+    st = run_all<double>(c, o, false, m, n, k, p, q, seed, (const double*)A, lda, want,
+                         (double*)Qo, ldq, (double*)Bto, ldbt, (double*)U, ldu, S, (double*)V,
+                         ldv, J, (double*)Tout, ldt, Jc, Ir, (double*)Ucur, lducur);
+  } else {
+    const bool tc = want_tc(dtype, o, l, A, lda);
+    Ctx d;
+    run_all<float>(d, o, tc, m, n, k, p, q, seed, nullptr, lda, want, nullptr, 0, nullptr, 0,
+                   nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr,
+                   nullptr, 0);
+    if (d.off > work_bytes) return RSVD_ERR_WORKSPACE;
+    st = run_all<float>(c, o, tc, m, n, k, p, q, seed, (const float*)A, lda, want, (float*)Qo,
+                        ldq, (float*)Bto, ldbt, (float*)U, ldu, S, (float*)V, ldv, J,
+                        (float*)Tout, ldt, Jc, Ir, (float*)Ucur, lducur);
+  }
+  if (st == RSVD_OK && c.err != cudaSuccess) st = RSVD_ERR_CUDA;
+  return st;
+}
+
+}  // namespace rsvd
+
+using namespace rsvd;
+
+extern "C" {
+
+void rsvd_opts_default(rsvd_opts* opts) {
+  if (!opts) return;
+  std::memset(opts, 0, sizeof(*opts));
+  opts->s = 1;
+  opts->max_sweeps = 30;
+  opts->precision = RSVD_PREC_TC;
+}
+
+const char* rsvd_status_string(int status) {
+  switch (status) {
+    case RSVD_OK: return "RSVD_OK";
+    case RSVD_ERR_INVALID_ARG: return "RSVD_ERR_INVALID_ARG";
+    case RSVD_ERR_WORKSPACE: return "RSVD_ERR_WORKSPACE";
+    case RSVD_ERR_CUDA: return "RSVD_ERR_CUDA";
+    case RSVD_ERR_UNSUPPORTED: return "RSVD_ERR_UNSUPPORTED";
+    case RSVD_ERR_NOT_SPD: return "RSVD_ERR_NOT_SPD";
+    case RSVD_ERR_NO_CONVERGENCE: return "RSVD_ERR_NO_CONVERGENCE";
+    case RSVD_ERR_NUMERIC: return "RSVD_ERR_NUMERIC";
+    case RSVD_ERR_TIMEOUT: return "RSVD_ERR_TIMEOUT";
+    default: return "RSVD_ERR_UNKNOWN";
+  }
+}
+
+int rsvd_version(void) { return 100; }
+
+size_t rsvd_qb_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                              const rsvd_opts* opts) {
+  return ws_query(m, n, k, p, q, dtype, opts, W_Q);
+}
+size_t rsvd_svd_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                               const rsvd_opts* opts) {
+  return ws_query(m, n, k, p, q, dtype, opts, W_SVD);
+}
+size_t rsvd_id_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                              const rsvd_opts* opts) {
+  if (k >= n) return 0;
+  return ws_query(m, n, k, p, q, dtype, opts, W_ID);
+}
+size_t rsvd_cur_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                               const rsvd_opts* opts) {
+  if (k >= n || k >= m) return 0;
+  return ws_query(m, n, k, p, q, dtype, opts, W_ID | W_CUR);
+}
+size_t rsvd_svd_id_cur_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                                      const rsvd_opts* opts) {
+  if (k >= n || k >= m) return 0;
+  return ws_query(m, n, k, p, q, dtype, opts, W_SVD | W_ID | W_CUR);
+}
+
+rsvd_status rsvd_qb(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                    const void* A, int64_t lda, void* Q, int64_t ldq, void* Bt, int64_t ldbt,
+                    void* work, size_t work_bytes, int* d_info, void* stream,
+                    const rsvd_opts* opts) {
+  return dispatch(m, n, k, p, q, seed, dtype, A, lda, W_Q, Q, ldq, Bt, ldbt, nullptr, 0, nullptr,
+                  nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr, 0, work,
+                  work_bytes, d_info, stream, opts);
+}
+
+rsvd_status rsvd_svd(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                     const void* A, int64_t lda, void* U, int64_t ldu, double* S, void* V,
+                     int64_t ldv, void* work, size_t work_bytes, int* d_info, void* stream,
+                     const rsvd_opts* opts) {
+  return dispatch(m, n, k, p, q, seed, dtype, A, lda, W_SVD, nullptr, 0, nullptr, 0, U, ldu, S, V,
+                  ldv, nullptr, nullptr, 0, nullptr, nullptr, nullptr, 0, work, work_bytes,
+                  d_info, stream, opts);
+}
+
+rsvd_status rsvd_id(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                    const void* A, int64_t lda, int32_t* J, void* T, int64_t ldt, void* work,
+                    size_t work_bytes, int* d_info, void* stream, const rsvd_opts* opts) {
+  return dispatch(m, n, k, p, q, seed, dtype, A, lda, W_ID, nullptr, 0, nullptr, 0, nullptr, 0,
+                  nullptr, nullptr, 0, J, T, ldt, nullptr, nullptr, nullptr, 0, work, work_bytes,
+                  d_info, stream, opts);
+}
+
+rsvd_status rsvd_cur(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                     const void* A, int64_t lda, int32_t* Jc, int32_t* Ir, void* U, int64_t ldu,
+                     void* work, size_t work_bytes, int* d_info, void* stream,
+                     const rsvd_opts* opts) {
+  return dispatch(m, n, k, p, q, seed, dtype, A, lda, W_ID | W_CUR, nullptr, 0, nullptr, 0,
+                  nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, 0, Jc, Ir, U, ldu, work,
+                  work_bytes, d_info, stream, opts);
+}
+
+rsvd_status rsvd_svd_id_cur(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                            const void* A, int64_t lda, void* U, int64_t ldu, double* S, void* V,
+                            int64_t ldv, int32_t* J, void* T, int64_t ldt, int32_t* Jc,
+                            int32_t* Ir, void* Ucur, int64_t lducur, void* work,
+                            size_t work_bytes, int* d_info, void* stream,
+                            const rsvd_opts* opts) {
+  int want = 0;
+  if (U || S || V) want |= W_SVD;
+  if (J || T) want |= W_ID;
+  if (Jc || Ir || Ucur) want |= W_ID | W_CUR;
+  if (!want) return RSVD_ERR_INVALID_ARG;
+  return dispatch(m, n, k, p, q, seed, dtype, A, lda, want, nullptr, 0, nullptr, 0, U, ldu, S, V,
+                  ldv, J, T, ldt, Jc, Ir, Ucur, lducur, work, work_bytes, d_info, stream, opts);
+}
+
+}  // extern "C"
+
+// ==========================================================================
+// Step-level entry points
+// ==========================================================================
+namespace rsvd {
+
+static bool dtype_ok(int dtype) { return dtype == RSVD_F32 || dtype == RSVD_F64; }
+
+template <typename T>
+static rsvd_status sample_impl(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n, int l,
+                               uint64_t seed, const T* A, int64_t lda, T* Y, int64_t ldy) {
+  Engine<T> e(c, o, tc);
+  const int L = padL(l);
+  float* part = tc ? c.template take<float>(tc_part_bytes(m, n, L) / sizeof(float)) : nullptr;
+  if (c.dry) return RSVD_OK;
+  if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
+  return e.gemm_n(m, n, L, A, lda, m, n, true, seed, l, nullptr, nullptr, 0, Y, ldy, l, nullptr,
+                  part, nullptr);
+}
+
+template <typename T>
+static rsvd_status apply_impl(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n, int l,
+                              int trans, const T* A, int64_t lda, const T* X, int64_t ldx, T* Y,
+                              int64_t ldy) {
+  Engine<T> e(c, o, tc);
+  const int L = padL(l);
+  const int64_t K = trans ? m : n;
+  const int64_t rows = trans ? n : m;
+  typename Engine<T>::Split w{};
+  float* part = nullptr;
+  T* slabs = nullptr;
+  if (tc) {
+    w = e.take_split(L, K);
+    part = c.template take<float>(tc_part_bytes(rows, K, L) / sizeof(float));
+  } else if (trans) {
+    slabs = c.template take<T>(e.slab_elems_t(rows, K, l));
+  }
+  if (c.dry) return RSVD_OK;
+  if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
+  if (tc) LK(launch_split_transpose(K, l, L, (const float*)X, ldx, w.hi, w.lo, w.ld, c.stream));
+  if (!trans)
+    return e.gemm_n(rows, K, L, A, lda, m, n, false, 0, L, &w, X, ldx, Y, ldy, l, nullptr, part,
+                    nullptr);
+  return e.gemm_t(rows, K, L, A, lda, &w, X, ldx, Y, ldy, l, nullptr, part, slabs, nullptr);
+}
+
+template <typename T>
+static rsvd_status orth_impl(Ctx& c, const Opts& o, bool tc, int64_t rows, int l, const T* X,
+                             int64_t ldx, T* Q, int64_t ldq, T* R, int64_t ldr) {
+  Engine<T> e(c, o, tc);
+  const int L = padL(l);
+  T* Xb = c.template take<T>((size_t)rows * L);
+  T* Yb = c.template take<T>((size_t)rows * L);
+  typename Engine<T>::Split sp{};
+  float* part = nullptr;
+  T* slabs = nullptr;
+  if (tc) {
+    sp = e.take_split(L, rows);
+    size_t pb = std::max(tc_part_bytes(L, rows, L), tc_part_bytes(rows, L, L));
+    part = c.template take<float>(pb / sizeof(float));
+  } else {
+    slabs = c.template take<T>(e.slab_elems_t(L, rows, L));
+  }
+  auto ob = e.take_orth_bufs(L);
+  if (c.dry) return RSVD_OK;
+  if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
+  LK(cudaMemsetAsync(Xb, 0, sizeof(T) * rows * L, c.stream));
+  LK(launch_copy2d<T, T>(rows, l, X, ldx, Xb, L, c.stream));
+  if (tc) LK(launch_split_transpose(rows, L, L, (const float*)Xb, L, sp.hi, sp.lo, sp.ld, c.stream));
+  rsvd_status st = e.orth(rows, l, L, Xb, Yb, &sp, ob, part, slabs, R != nullptr);
+  if (st != RSVD_OK) return st;
+  LK(launch_copy2d<T, T>(rows, l, Yb, L, Q, ldq, c.stream));
+  if (R) LK(launch_copy2d<T, T>(l, l, ob.Racc, L, R, ldr, c.stream));
+  return RSVD_OK;
+}
+
+template <typename T>
+static rsvd_status small_svd_impl(Ctx& c, const Opts& o, int l, const T* M, int64_t ldm, T* Uh,
+                                  int64_t lduh, double* Sh, T* Vh, int64_t ldvh) {
+  Engine<T> e(c, o, false);
+  auto sb = e.take_svd(l, padL(l), 1);
+  if (c.dry) return RSVD_OK;
+  if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
+  return e.small_svd(l, M, ldm, sb, Uh, lduh, Sh, Vh, ldvh);
+}
+
+static rsvd_status cpqr_impl(Ctx& c, int r, int64_t n, int k, const double* M, int64_t ldm,
+                             int32_t* J, double* T, int64_t ldt, double* gaps) {
+  Opts o;
+  Engine<double> e(c, o, false);
+  auto idb = e.take_id(r, n, k, true);
+  if (c.dry) return RSVD_OK;
+  if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
+  LK(launch_transpose<double, double>(r, n, M, ldm, idb.W, r, c.stream));
+  rsvd_status st = e.id_core(idb, r, n, k, gaps);
+  if (st != RSVD_OK) return st;
+  LK(launch_copy_i32(n, idb.J, J, c.stream));
+  if (T && n > k) LK(launch_transpose<double, double>(n - k, k, idb.Tt, k, T, ldt, c.stream));
+  return RSVD_OK;
+}
+
+static Ctx make_ctx(void* work, size_t bytes, int* d_info, void* stream) {
+  Ctx c;
+  c.dry = false;
+  c.base = (char*)work;
+  c.cap = bytes;
+  c.d_info = d_info;
+  c.stream = (cudaStream_t)stream;
+  return c;
+}
+
+static rsvd_status finish(Ctx& c, rsvd_status st) {
+  if (st == RSVD_OK && c.err != cudaSuccess) return RSVD_ERR_CUDA;
+  return st;
+}
+
+}  // namespace rsvd
+
+extern "C" {
+
+rsvd_status rsvd_omega(int64_t n, int l, uint64_t seed, int dtype, void* Omega, int64_t ldo,
+                       void* stream) {
+  if (!dtype_ok(dtype) || n < 1 || l < 1 || !Omega || ldo < l) return RSVD_ERR_INVALID_ARG;
+  if (n > 0xffffffffLL) return RSVD_ERR_INVALID_ARG;
+  cudaError_t e = (dtype == RSVD_F64)
+                      ? launch_omega<double>(n, l, seed, (double*)Omega, ldo, (cudaStream_t)stream)
+                      : launch_omega<float>(n, l, seed, (float*)Omega, ldo, (cudaStream_t)stream);
+  return e == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+}
+
+rsvd_status rsvd_omega_words(int64_t n, int l, uint64_t seed, uint32_t* out, void* stream) {
+  if (n < 1 || l < 1 || !out || ((uintptr_t)out & 15u)) return RSVD_ERR_INVALID_ARG;
+  if (n > 0xffffffffLL) return RSVD_ERR_INVALID_ARG;
+  return launch_omega_words(n, l, seed, out, (cudaStream_t)stream) == cudaSuccess ? RSVD_OK
+                                                                                 : RSVD_ERR_CUDA;
+}
+
+static bool sizes_ok(int64_t m, int64_t n, int l) {
+  return m >= 1 && n >= 1 && l >= 1 && l <= 1024 && m <= 0x7fffffffLL && n <= 0x7fffffffLL;
+}
+
+size_t rsvd_sample_workspace_size(int64_t m, int64_t n, int l, int dtype, const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(m, n, l)) return 0;
+  Ctx c;
+  const bool tc = want_tc(dtype, o, l, nullptr, 0);
+  if (dtype == RSVD_F64)
+    sample_impl<double>(c, o, false, m, n, l, 0, nullptr, n, nullptr, l);
+  else
+    sample_impl<float>(c, o, tc, m, n, l, 0, nullptr, n, nullptr, l);
+  return c.off + 256;
+}
+
+rsvd_status rsvd_sample(int64_t m, int64_t n, int l, uint64_t seed, int dtype, const void* A,
+                        int64_t lda, void* Y, int64_t ldy, void* work, size_t work_bytes,
+                        void* stream, const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(m, n, l)) return RSVD_ERR_INVALID_ARG;
+  if (!A || !Y || lda < n || ldy < l) return RSVD_ERR_INVALID_ARG;
+  if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
+  Ctx c = make_ctx(work, work_bytes, nullptr, stream);
+  rsvd_status st;
+  if (dtype == RSVD_F64) {
+    st = sample_impl<double>(c, o, false, m, n, l, seed, (const double*)A, lda, (double*)Y, ldy);
+  } else {
+    const bool tc = want_tc(dtype, o, l, A, lda);
+    st = sample_impl<float>(c, o, tc, m, n, l, seed, (const float*)A, lda, (float*)Y, ldy);
+  }
+  return finish(c, st);
+}
+
+size_t rsvd_apply_workspace_size(int64_t m, int64_t n, int l, int dtype, const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(m, n, l)) return 0;
+  size_t best = 0;
+  for (int trans = 0; trans < 2; ++trans) {
+    Ctx c;
+    const bool tc = want_tc(dtype, o, l, nullptr, 0);
+    if (dtype == RSVD_F64)
+      apply_impl<double>(c, o, false, m, n, l, trans, nullptr, n, nullptr, l, nullptr, l);
+    else {
+      apply_impl<float>(c, o, tc, m, n, l, trans, nullptr, n, nullptr, l, nullptr, l);
+      Ctx c2;
+      apply_impl<float>(c2, o, false, m, n, l, trans, nullptr, n, nullptr, l, nullptr, l);
+      best = std::max(best, c2.off);
+    }
+    best = std::max(best, c.off);
+  }
+  return best + 256;
+}
+
+rsvd_status rsvd_apply(int64_t m, int64_t n, int l, int trans, int dtype, const void* A,
+                       int64_t lda, const void* X, int64_t ldx, void* Y, int64_t ldy, void* work,
+                       size_t work_bytes, void* stream, const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(m, n, l)) return RSVD_ERR_INVALID_ARG;
+  if (trans != 0 && trans != 1) return RSVD_ERR_INVALID_ARG;
+  if (!A || !X || !Y || lda < n || ldx < l || ldy < l) return RSVD_ERR_INVALID_ARG;
+  if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
+  Ctx c = make_ctx(work, work_bytes, nullptr, stream);
+  rsvd_status st;
+  if (dtype == RSVD_F64) {
+    st = apply_impl<double>(c, o, false, m, n, l, trans, (const double*)A, lda, (const double*)X,
+                            ldx, (double*)Y, ldy);
+  } else {
+    const bool tc = want_tc(dtype, o, l, A, lda);
+    st = apply_impl<float>(c, o, tc, m, n, l, trans, (const float*)A, lda, (const float*)X, ldx,
+                           (float*)Y, ldy);
+  }
+  return finish(c, st);
+}
+
+size_t rsvd_orth_workspace_size(int64_t rows, int l, int dtype, const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(rows, l, l) || rows < l) return 0;
+  Ctx c, c2;
+  if (dtype == RSVD_F64) {
+    orth_impl<double>(c, o, false, rows, l, nullptr, l, nullptr, l, nullptr, l);
+  } else {
+    const bool tc = want_tc(dtype, o, l, nullptr, 0);
+    orth_impl<float>(c, o, tc, rows, l, nullptr, l, nullptr, l, nullptr, l);
+    orth_impl<float>(c2, o, false, rows, l, nullptr, l, nullptr, l, nullptr, l);
+  }
+  return std::max(c.off, c2.off) + 256;
+}
+
+rsvd_status rsvd_orth(int64_t rows, int l, int dtype, const void* X, int64_t ldx, void* Q,
+                      int64_t ldq, void* R, int64_t ldr, void* work, size_t work_bytes,
+                      int* d_info, void* stream, const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(rows, l, l) || rows < l)
+    return RSVD_ERR_INVALID_ARG;
+  if (!X || !Q || ldx < l || ldq < l || (R && ldr < l)) return RSVD_ERR_INVALID_ARG;
+  if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
+  Ctx c = make_ctx(work, work_bytes, d_info, stream);
+  reset_info(c);
+  rsvd_status st;
+  if (dtype == RSVD_F64) {
+    st = orth_impl<double>(c, o, false, rows, l, (const double*)X, ldx, (double*)Q, ldq,
+                           (double*)R, ldr);
+  } else {
+    const bool tc = want_tc(dtype, o, l, nullptr, 0);
+    st = orth_impl<float>(c, o, tc, rows, l, (const float*)X, ldx, (float*)Q, ldq, (float*)R,
+                          ldr);
+  }
+  return finish(c, st);
+}
+
+size_t rsvd_small_svd_workspace_size(int l, int dtype, const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !dtype_ok(dtype) || l < 1 || l > 1024) return 0;
+  Ctx c;
+  if (dtype == RSVD_F64)
+    small_svd_impl<double>(c, o, l, nullptr, l, nullptr, l, nullptr, nullptr, l);
+  else
+    small_svd_impl<float>(c, o, l, nullptr, l, nullptr, l, nullptr, nullptr, l);
+  return c.off + 256;
+}
+
+rsvd_status rsvd_small_svd(int l, int dtype, const void* M, int64_t ldm, void* Uh, int64_t lduh,
+                           double* Sh, void* Vh, int64_t ldvh, void* work, size_t work_bytes,
+                           int* d_info, void* stream, const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !dtype_ok(dtype) || l < 1 || l > 1024) return RSVD_ERR_INVALID_ARG;
+  if (!M || !Uh || !Sh || !Vh || ldm < l || lduh < l || ldvh < l) return RSVD_ERR_INVALID_ARG;
+  if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
+  Ctx c = make_ctx(work, work_bytes, d_info, stream);
+  reset_info(c);
+  rsvd_status st;
+  if (dtype == RSVD_F64)
+    st = small_svd_impl<double>(c, o, l, (const double*)M, ldm, (double*)Uh, lduh, Sh,
+                                (double*)Vh, ldvh);
+  else
+    st = small_svd_impl<float>(c, o, l, (const float*)M, ldm, (float*)Uh, lduh, Sh, (float*)Vh,
+                               ldvh);
+  return finish(c, st);
+}
+
+size_t rsvd_cpqr_workspace_size(int r, int64_t n, int k) {
+  if (r < 1 || n < 1 || k < 1 || k > r || k > n || r > 8192 || k > 2048 || n > 0x7fffffffLL)
+    return 0;
+  Ctx c;
+  cpqr_impl(c, r, n, k, nullptr, n, nullptr, nullptr, 0, nullptr);
+  return c.off + 256;
+}
+
+rsvd_status rsvd_cpqr_id(int r, int64_t n, int k, const double* M, int64_t ldm, int32_t* J,
+                         double* T, int64_t ldt, double* gaps, void* work, size_t work_bytes,
+                         int* d_info, void* stream) {
+  if (r < 1 || n < 1 || k < 1 || k > r || k > n || r > 8192 || k > 2048 || n > 0x7fffffffLL)
+    return RSVD_ERR_INVALID_ARG;
+  if (!M || !J || ldm < n || (T && n > k && ldt < n - k)) return RSVD_ERR_INVALID_ARG;
+  if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
+  Ctx c = make_ctx(work, work_bytes, d_info, stream);
+  reset_info(c);
+  return finish(c, cpqr_impl(c, r, n, k, M, ldm, J, T, ldt, gaps));
+}
+
+}  // extern "C"

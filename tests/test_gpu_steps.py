@@ -1,0 +1,217 @@
+"""GPU parity of each step of the path against the FP64 oracle (through the C ABI).
+
+Tolerances (derived in the design doc): the FP32 tensor-core path splits each fp32
+operand into two bf16 terms (16 significant bits, unit roundoff 2^-16 per
+term product) with fp32 accumulation, so a product entry carries a relative
+error of order 2^-16 / sqrt(terms) ~ 1e-5 in the worst case and ~1e-6 in the
+Frobenius mean; the SIMT FP32 path is plain fp32 (~1e-6); FP64 is ~1e-13.
+"""
+import numpy as np
+import pytest
+
+from oracle import philox, rsvd as orc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+rs = pytest.importorskip("paper_1502_05366_gb300")
+
+DEV = "cuda:0"
+SIMT = None
+
+
+def _simt():
+    return rs.make_opts(precision=rs.PREC_SIMT)
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _dev(x, dtype):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV, dtype)
+
+
+# ---------------------------------------------------------------------------
+# Philox / Omega: integer words bit-exact, Gaussians within rounding
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,l,seed", [(1000, 60, 0x5EED + 1), (777, 13, 3), (1, 1, 0),
+                                      (4096, 224, (1 << 40) + 5)])
+def test_omega_words_bit_exact(n, l, seed):
+    w = rs.omega_words(n, l, seed, device=DEV).cpu().numpy().view(np.uint32)
+    ref = philox.omega_words(n, l, seed)
+    assert np.array_equal(w, ref)
+
+
+def test_omega_f64_matches():
+    n, l, seed = 2000, 61, 99
+    g = rs.omega(n, l, seed, torch.float64, DEV).cpu().numpy()
+    ref = philox.omega(n, l, seed, "f64")
+    assert np.max(np.abs(g - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_omega_f32_bf16_rounding():
+    n, l, seed = 20000, 220, 0x5EED + 2
+    g = rs.omega(n, l, seed, torch.float32, DEV).cpu().numpy().astype(np.float64)
+    ref = philox.omega(n, l, seed, "bf16")
+    bits = g.astype(np.float32).view(np.uint32)
+    assert np.all(bits & np.uint32(0xFFFF) == 0)          # bf16-exact entries
+    diff = g != ref
+    frac = diff.mean()
+    # fp32 libm vs CUDA math differ by a few ulps; a bf16 rounding flip needs the
+    # fp32 value within those ulps of a rounding boundary: rare, one bf16 ulp each
+    assert frac < 2e-4, frac
+    if diff.any():
+        assert np.max(np.abs(g[diff] - ref[diff]) / np.abs(ref[diff])) <= 2.0 ** -7
+
+
+# ---------------------------------------------------------------------------
+# sample Y = A Omega and the power half steps
+# ---------------------------------------------------------------------------
+SHAPES = [(300, 200, 24), (1000, 777, 60), (517, 1290, 17), (129, 33, 16), (2048, 4096, 220)]
+
+
+@pytest.mark.parametrize("m,n,l", SHAPES)
+@pytest.mark.parametrize("mode", ["tc", "simt", "f64"])
+def test_sample(m, n, l, mode):
+    rng = np.random.default_rng(m + n + l)
+    A = rng.standard_normal((m, n))
+    seed = 1234 + l
+    if mode == "f64":
+        Y = rs.sample(_dev(A, torch.float64), l, seed).cpu().numpy()
+        ref = A @ philox.omega(n, l, seed, "f64")
+        assert _rel(Y, ref) <= 1e-13
+    else:
+        A32 = A.astype(np.float32)
+        opts = _simt() if mode == "simt" else None
+        Y = rs.sample(_dev(A32, torch.float32), l, seed, opts).cpu().numpy()
+        # GEMM arithmetic against the kernels' own Omega (same device function) ...
+        Om_gpu = rs.omega(n, l, seed, torch.float32, DEV).double().cpu().numpy()
+        ref = A32.astype(np.float64) @ Om_gpu
+        tol = 2e-5 if mode == "tc" else 2e-6
+        assert _rel(Y, ref) <= tol, _rel(Y, ref)
+        # ... and against the oracle's Omega, which differs by rare bf16 flips
+        ref_o = A32.astype(np.float64) @ philox.omega(n, l, seed, "bf16")
+        assert _rel(Y, ref_o) <= 1e-4, _rel(Y, ref_o)
+
+
+@pytest.mark.parametrize("m,n,l", SHAPES)
+@pytest.mark.parametrize("trans", [0, 1])
+@pytest.mark.parametrize("mode", ["tc", "simt", "f64"])
+def test_apply(m, n, l, trans, mode):
+    rng = np.random.default_rng(7 * m + n + l + trans)
+    A = rng.standard_normal((m, n))
+    X = rng.standard_normal((m if trans else n, l))
+    ref = (A.T @ X) if trans else (A @ X)
+    if mode == "f64":
+        Y = rs.apply(_dev(A, torch.float64), _dev(X, torch.float64), trans).cpu().numpy()
+        assert _rel(Y, ref) <= 1e-13
+    else:
+        opts = _simt() if mode == "simt" else None
+        A32, X32 = A.astype(np.float32), X.astype(np.float32)
+        ref = (A32.astype(np.float64).T @ X32) if trans else (A32.astype(np.float64) @ X32)
+        Y = rs.apply(_dev(A32, torch.float32), _dev(X32, torch.float32), trans, opts).cpu().numpy()
+        tol = 3e-5 if mode == "tc" else 2e-6
+        assert _rel(Y, ref) <= tol, _rel(Y, ref)
+
+
+# ---------------------------------------------------------------------------
+# orth (CholeskyQR2/3) against the Householder Q of the oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("rows,l", [(500, 40), (3000, 220), (129, 17), (64, 64), (20000, 96)])
+@pytest.mark.parametrize("mode", ["tc", "simt", "f64"])
+@pytest.mark.parametrize("cond", [1e1, 1e3, 1e6])
+def test_orth(rows, l, mode, cond):
+    rng = np.random.default_rng(rows + l)
+    G, _ = np.linalg.qr(rng.standard_normal((rows, l)))
+    H, _ = np.linalg.qr(rng.standard_normal((l, l)))
+    X = (G * np.logspace(0, -np.log10(cond), l)) @ H
+    if mode == "f64":
+        Q, R = rs.orth(_dev(X, torch.float64))
+        Qn, Rn = Q.cpu().numpy(), R.cpu().numpy()
+        Qo, Ro = orc.qr_pos(X)
+        assert np.linalg.norm(Qn.T @ Qn - np.eye(l)) <= 1e-12
+        assert _rel(Qn @ Rn, X) <= 1e-13
+        assert np.max(np.abs(Qn - Qo)) <= 1e-10 * cond
+    else:
+        X32 = X.astype(np.float32)
+        opts = _simt() if mode == "simt" else None
+        Q, R = rs.orth(_dev(X32, torch.float32), opts)
+        Qn, Rn = Q.double().cpu().numpy(), R.double().cpu().numpy()
+        Qo, Ro = orc.qr_pos(X32.astype(np.float64))
+        orth_err = np.linalg.norm(Qn.T @ Qn - np.eye(l), 2)
+        res = _rel(Qn @ Rn, X32)
+        # fp32 CholeskyQR3 reaches O(u) orthogonality for kappa well below 1/u;
+        # kappa = 1e6 is within 20x of 1/u = 1.7e7 and gets a looser bar
+        tol = 1e-5 if cond < 1e6 else 1e-4
+        assert orth_err <= tol, (orth_err, res)
+        assert res <= 3e-5, (orth_err, res)
+        assert np.all(np.diag(Rn) > 0)
+        assert np.allclose(np.tril(Rn, -1), 0)
+        # Q is unique (diag R > 0); its columns agree with Householder's
+        assert np.max(np.abs(Qn - Qo)) <= 5e-4 * max(1.0, cond / 1e3)
+
+
+# ---------------------------------------------------------------------------
+# small SVD (one-sided Jacobi)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("l", [1, 2, 17, 60, 224])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_small_svd(l, dtype):
+    rng = np.random.default_rng(l)
+    # upper-triangular core with a prescribed spectrum (as R-hat of Alg. 5 is)
+    G1, _ = np.linalg.qr(rng.standard_normal((l, l)))
+    G2, _ = np.linalg.qr(rng.standard_normal((l, l)))
+    M = np.linalg.qr((G1 * np.logspace(0, -3, l)) @ G2.T)[1]
+    Mt = M.astype(np.float32).astype(np.float64) if dtype == torch.float32 else M
+    Uh, Sh, Vh = rs.small_svd(_dev(Mt, dtype))
+    Uh, Sh, Vh = Uh.double().cpu().numpy(), Sh.cpu().numpy(), Vh.double().cpu().numpy()
+    s_ref = np.linalg.svd(Mt, compute_uv=False)
+    tol = 2e-6 if dtype == torch.float32 else 1e-13
+    assert np.max(np.abs(Sh - s_ref) / s_ref) <= tol * 10
+    assert np.all(np.diff(Sh) <= 0)
+    assert np.linalg.norm(Uh.T @ Uh - np.eye(l)) <= tol * 100
+    assert _rel((Uh * Sh) @ Vh.T, Mt) <= tol * 50
+
+
+def test_small_svd_closed_forms():
+    M = np.diag([0.5, -3.0, 2.0, 1e-3])
+    Uh, Sh, Vh = rs.small_svd(_dev(M, torch.float64))
+    assert np.allclose(Sh.cpu().numpy(), [3.0, 2.0, 0.5, 1e-3], rtol=1e-15)
+    a, b, d = 3.0, 4.0, 2.0
+    M = np.array([[a, b], [0.0, d]])
+    s = a * a + b * b + d * d
+    s1 = np.sqrt((s + np.sqrt(s * s - 4 * (a * d) ** 2)) / 2)
+    s2 = np.sqrt((s - np.sqrt(s * s - 4 * (a * d) ** 2)) / 2)
+    _, Sh, _ = rs.small_svd(_dev(M, torch.float64))
+    assert np.allclose(Sh.cpu().numpy(), [s1, s2], rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# CPQR / ID of an explicit matrix: pivots bit-exact, T close
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("r,n,k", [(20, 50, 10), (60, 1000, 50), (220, 5000, 200), (8, 9, 8),
+                                   (33, 4097, 1)])
+def test_cpqr_id(r, n, k):
+    rng = np.random.default_rng(r * n + k)
+    M = rng.standard_normal((r, n)) * np.logspace(0, -4, n)[rng.permutation(n)]
+    J, T, gaps = rs.cpqr_id(_dev(M, torch.float64), k)
+    J, T, gaps = J.cpu().numpy(), T.cpu().numpy(), gaps.cpu().numpy()
+    Jo, To, go = orc.id_from_matrix(M, k)
+    assert np.array_equal(J[:k], Jo[:k])
+    assert np.array_equal(J, Jo)
+    assert np.allclose(gaps[go < np.inf], go[go < np.inf], rtol=1e-9, atol=1e-12)
+    if n > k:
+        assert np.max(np.abs(T - To)) <= 1e-9 * max(1.0, np.max(np.abs(To)))
+
+
+def test_cpqr_golden_worked_example():
+    import os
+    M = np.array([[3, 0, 1, 0], [4, 0, 0, 2]], dtype=np.float64)
+    J, T, _ = rs.cpqr_id(_dev(M, torch.float64), 2)
+    assert list(J.cpu().numpy()) == [0, 3, 2, 1]
+    assert np.allclose(T.cpu().numpy(), [[1 / 3, 0], [-2 / 3, 0]], atol=1e-14)
+    assert os.path.exists(os.path.join(os.path.dirname(__file__), "golden",
+                                       "cpqr_worked_example.txt"))
