@@ -239,6 +239,24 @@ rsvd_status rsvd_cpqr_id(int r, int64_t n, int k, const double* M, int64_t ldm,
                          int32_t* J, double* T, int64_t ldt, double* gaps, void* work,
                          size_t work_bytes, int* d_info, void* stream);
 
+/* -------------------------------------------------------------------------
+ * rsvd_small_svd_noalloc - rsvd_small_svd without a caller workspace.
+ * The paper has no counterpart: this is an interface for callers that cannot
+ * allocate device memory or pass a workspace (cudaMalloc/cudaFree synchronise
+ * the device, and some host frameworks own the whole device-memory budget).
+ * Same arguments and results as rsvd_small_svd minus work/work_bytes.  Its
+ * scratch is one static device array of RSVD_NOALLOC_SCRATCH_BYTES per GPU
+ * (held until the process exits), shared by all calls: calls that overlap on
+ * the GPU race and must be serialised by the caller.  The first call on a
+ * device looks up the array's address (make it before any stream capture).
+ * Sizes whose scratch need exceeds the array (l above 512 in FP64, about 720
+ * in FP32) return RSVD_ERR_WORKSPACE; nothing is allocated.
+ * ------------------------------------------------------------------------- */
+#define RSVD_NOALLOC_SCRATCH_BYTES (16u << 20)
+rsvd_status rsvd_small_svd_noalloc(int l, int dtype, const void* M, int64_t ldm, void* Uh,
+                                   int64_t lduh, double* Sh, void* Vh, int64_t ldvh,
+                                   int* d_info, void* stream, const rsvd_opts* opts);
+
 /* =========================================================================
  * Tracing aids (host only; not part of the paper's method).
  * ========================================================================= */

@@ -84,6 +84,8 @@ _SIGS = {
     "rsvd_small_svd": (_c_int, [_c_int, _c_int, _vp, _c_i64, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
                                 _c_size, _vp, _vp, _OPTP]),
     "rsvd_cpqr_workspace_size": (_c_size, [_c_int, _c_i64, _c_int]),
+    "rsvd_small_svd_noalloc": (_c_int, [_c_int, _c_int, _vp, _c_i64, _vp, _c_i64, _vp, _vp,
+                                        _c_i64, _vp, _vp, _OPTP]),
     "rsvd_trace_enable": (_c_int, [_c_int]),
     "rsvd_trace_read": (_c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_i64), _c_int]),
     "rsvd_kernel_launch_count": (_c_i64, []),
