@@ -270,7 +270,11 @@ enum {
   RSVD_TRACE_APPLY = 4,   /* X R^-1 of CholeskyQR                                    */
   RSVD_TRACE_REDUCE = 5,  /* fixed-order sum of the stream-K partial tiles           */
   RSVD_TRACE_CPQR = 6,    /* column-pivoted QR of ID / CUR                           */
-  RSVD_TRACE_CLASSES = 7
+  RSVD_TRACE_JACOBI = 7,  /* one-sided Jacobi SVD of the l x l core                  */
+  RSVD_TRACE_CHOL = 8,    /* Cholesky factor and inverse of CholeskyQR               */
+  RSVD_TRACE_SOLVE = 9,   /* triangular solves of ID / CUR                           */
+  RSVD_TRACE_SIMT = 10,   /* SIMT GEMMs (lift, CUR products, FP64 path)              */
+  RSVD_TRACE_CLASSES = 11
 };
 
 /* Turns on (1) or off (0) CUDA-event timing of the classes above.  While on,

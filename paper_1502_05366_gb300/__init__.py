@@ -114,7 +114,8 @@ def exported_symbols():
     return sorted(_SIGS)
 
 
-TRACE_CLASSES = ["a_omega", "a_w", "at_w", "gram", "orth_apply", "reduce", "cpqr"]
+TRACE_CLASSES = ["a_omega", "a_w", "at_w", "gram", "orth_apply", "reduce", "cpqr", "jacobi",
+                 "chol", "solve", "simt_gemm"]
 
 
 def trace_enable(on=True):

@@ -47,10 +47,10 @@ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32
                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;   // one wide multiply each
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
     const uint32_t n0 = hi1 ^ c1 ^ k0;
     const uint32_t n2 = hi0 ^ c3 ^ k1;
     c0 = n0;
@@ -79,17 +79,40 @@ __device__ __forceinline__ double word_to_uniform_d(uint32_t x) {
 }
 
 // Box-Muller (Box & Muller 1958) on the four words: (x0,x1) -> z0, z1 and
-// (x2,x3) -> z2, z3.  Single precision with CUDA's logf / sqrtf / sincospif.
+// (x2,x3) -> z2, z3.  Single precision with the hardware approximations
+// __log2f and __sincosf (the values feed bf16 Omega entries, 8 significant
+// bits): r = sqrt(-2 ln u0) (minus2log_f); the angle 2 pi u1 is taken as
+// 2 pi (u1 - 1/2) in [-pi, pi), where __sincosf is accurate, and the sign of
+// sin and cos flipped back (cos(x + pi) = -cos x, sin(x + pi) = -sin x).
+// -2 ln u for u in (0, 1): the Taylor series of ln(1 - v), v = 1 - u (exact in
+// fp32 for these u), when v <= 1/8 (truncation below 2^-24 relative), else
+// -2 ln 2 log2 u with the hardware log2 (whose absolute error would dominate
+// near u = 1).
+__device__ __forceinline__ float minus2log_f(float u) {
+  const float v = 1.0f - u;
+  if (v <= 0.125f) {
+    float p = 1.0f / 7.0f;
+    p = fmaf(p, v, 1.0f / 6.0f);
+    p = fmaf(p, v, 0.2f);
+    p = fmaf(p, v, 0.25f);
+    p = fmaf(p, v, 1.0f / 3.0f);
+    p = fmaf(p, v, 0.5f);
+    p = fmaf(p, v, 1.0f);
+    return 2.0f * v * p;
+  }
+  return -1.3862943611198906f * __log2f(u);
+}
+
 __device__ __forceinline__ void gauss4_f(const Words4& w, float z[4]) {
-  const float r0 = sqrtf(-2.0f * logf(word_to_uniform_f(w.x0)));
-  const float r1 = sqrtf(-2.0f * logf(word_to_uniform_f(w.x2)));
+  const float r0 = sqrtf(minus2log_f(word_to_uniform_f(w.x0)));
+  const float r1 = sqrtf(minus2log_f(word_to_uniform_f(w.x2)));
   float s0, c0, s1, c1;
-  sincospif(2.0f * word_to_uniform_f(w.x1), &s0, &c0);
-  sincospif(2.0f * word_to_uniform_f(w.x3), &s1, &c1);
-  z[0] = r0 * c0;
-  z[1] = r0 * s0;
-  z[2] = r1 * c1;
-  z[3] = r1 * s1;
+  __sincosf(6.283185307179586f * (word_to_uniform_f(w.x1) - 0.5f), &s0, &c0);
+  __sincosf(6.283185307179586f * (word_to_uniform_f(w.x3) - 0.5f), &s1, &c1);
+  z[0] = -r0 * c0;
+  z[1] = -r0 * s0;
+  z[2] = -r1 * c1;
+  z[3] = -r1 * s1;
 }
 
 __device__ __forceinline__ void gauss4_d(const Words4& w, double z[4]) {

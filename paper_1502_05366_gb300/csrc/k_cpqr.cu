@@ -17,7 +17,7 @@
 namespace rsvd {
 
 namespace {
-constexpr int PT = 256;
+constexpr int PT = 1024;
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;
 }
 
@@ -108,10 +108,17 @@ __device__ Top2 block_top2(Top2 v) {
   return r;
 }
 
+// W is the r x n sketch in FP64, ROW-major (element (i, c) at W[i*n + c]), so a
+// warp's 32 threads, one column each, touch 32 consecutive doubles of a row.
+// Residual norms are downdated, nu_c^2 <- nu_c^2 - W(j, c)^2 after step j (the
+// reflector keeps ||W(j:, c)||), and recomputed exactly from the column when
+// the downdated value falls below sqrt(eps) of its last exact value (the
+// LAPACK dgeqp3 safeguard); the pivot relative error stays below ~1e-8.
 __global__ void __launch_bounds__(PT) cpqr_kernel(CpqrArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   double* v = (double*)dsm;  // Householder vector, r entries
   __shared__ double s_tau, s_beta;
+  __shared__ double s_part[PT];
   const int r = a.r;
   const int64_t n = a.n;
   const int G = gridDim.x;
@@ -121,15 +128,19 @@ __global__ void __launch_bounds__(PT) cpqr_kernel(CpqrArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = PT / 32;
   double* W = a.W;
   double* __restrict__ nrm = a.nrm;
+  double* __restrict__ nref = a.nrm + n;     // norm^2 at the last exact computation
   double* __restrict__ diagR = a.diagR;
+  const double tol3z = 1.4901161193847656e-08;   // sqrt(eps_fp64)
 
   // exact initial norms of the own columns
-  for (int64_t c = c0 + warp; c < c1; c += nwarp) {
-    const double* col = W + c * r;
+  for (int64_t c = c0 + tid; c < c1; c += PT) {
     double s = 0.0;
-    for (int i = lane; i < r; i += 32) s = fma(col[i], col[i], s);
-    s = warp_sum(s);
-    if (lane == 0) nrm[c] = s;
+    for (int i = 0; i < r; ++i) {
+      const double x = W[(int64_t)i * n + c];
+      s = fma(x, x, s);
+    }
+    nrm[c] = s;
+    nref[c] = s;
   }
   if (blockIdx.x == 0)
     for (int64_t c = tid; c < n; c += PT) {
@@ -165,11 +176,10 @@ __global__ void __launch_bounds__(PT) cpqr_kernel(CpqrArgs a) {
       return;
     }
     // Householder vector of the pivot column, rows j..r-1 (read-only this step)
-    const double* colp = W + p * r;
     const int len = r - j;
     double part = 0.0;
     for (int i = tid; i < len; i += PT) {
-      const double x = __ldcg(colp + j + i);
+      const double x = __ldcg(W + (int64_t)(j + i) * n + p);
       v[i] = x;
       part = fma(x, x, part);
     }
@@ -194,20 +204,51 @@ __global__ void __launch_bounds__(PT) cpqr_kernel(CpqrArgs a) {
     }
     __syncthreads();
     const double tau = s_tau;
-    for (int64_t c = c0 + warp; c < c1; c += nwarp) {
-      if (c == p || nrm[c] < 0.0) continue;
-      double* col = W + c * r + j;
-      double w = 0.0;
-      for (int i = lane; i < len; i += 32) w = fma(v[i], col[i], w);
-      w = warp_sum(w) * tau;
-      double s = 0.0;
-      for (int i = lane; i < len; i += 32) {
-        const double y = col[i] - w * v[i];
-        col[i] = y;
-        if (i > 0) s = fma(y, y, s);
+    // TPC threads per column, each on a chunk of the len active rows; the
+    // partial dot products meet in shared memory.
+    const int cw = PT / a.tpc;                 // columns per pass
+    const int h = tid / cw, cc = tid - h * cw;
+    const int clen = (len + a.tpc - 1) / a.tpc;
+    const int i0 = h * clen, i1 = min(len, i0 + clen);
+    for (int64_t cb = c0; cb < c1; cb += cw) {
+      const int64_t c = cb + cc;
+      const bool act = c < c1 && c != p && nrm[c] >= 0.0;
+      double* col = W + (int64_t)j * n + c;
+      if (act) {
+        double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+        int i = i0;
+        for (; i + 4 <= i1; i += 4) {
+          w0 = fma(v[i], col[(int64_t)i * n], w0);
+          w1 = fma(v[i + 1], col[(int64_t)(i + 1) * n], w1);
+          w2 = fma(v[i + 2], col[(int64_t)(i + 2) * n], w2);
+          w3 = fma(v[i + 3], col[(int64_t)(i + 3) * n], w3);
+        }
+        for (; i < i1; ++i) w0 = fma(v[i], col[(int64_t)i * n], w0);
+        s_part[h * cw + cc] = (w0 + w1) + (w2 + w3);
       }
-      s = warp_sum(s);
-      if (lane == 0) nrm[c] = s;
+      __syncthreads();
+      if (act) {
+        double w = 0.0;
+        for (int t = 0; t < a.tpc; ++t) w += s_part[t * cw + cc];
+        w *= tau;
+#pragma unroll 4
+        for (int i = i0; i < i1; ++i) col[(int64_t)i * n] -= w * v[i];
+      }
+      __syncthreads();
+      if (act && h == 0) {
+        const double top = col[0];
+        const double nc = nrm[c];
+        double nn = nc - top * top;
+        if (!(nn > tol3z * nref[c]) && j + 1 < r) {   // cancellation: recompute exactly
+          nn = 0.0;
+          for (int i = 1; i < len; ++i) {
+            const double x = col[(int64_t)i * n];
+            nn = fma(x, x, nn);
+          }
+          nref[c] = nn;
+        }
+        nrm[c] = nn > 0.0 ? nn : 0.0;
+      }
     }
     if (p >= c0 && p < c1 && tid == 0) nrm[p] = -1.0;
     if (blockIdx.x == 0 && tid == 0) {
@@ -236,6 +277,8 @@ cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const size_t dyn = (size_t)a.r * sizeof(double);
+  e = cudaFuncSetAttribute(cpqr_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel, PT, dyn);
   if (e != cudaSuccess) return e;
@@ -246,9 +289,14 @@ cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   if (G > 1024) G = 1024;
   if (G < 1) G = 1;
   *grid_out = (int)G;
+  // threads per column: the largest power of two that keeps one pass per step
+  const int64_t per = ceil_div(a.n, G);
+  int tpc = 1;
+  while (tpc < 8 && (int64_t)(PT / (tpc * 2)) >= per) tpc *= 2;
   e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   CpqrArgs b = a;
+  b.tpc = tpc;
   void* args[] = {(void*)&b};
   count_launch();
   const int tr = trace_begin(RSVD_TRACE_CPQR, s);
@@ -259,7 +307,8 @@ cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
 }
 
 // S11 (k x k, column-major, upper triangular incl. beta on the diagonal) and
-// S12 (column c' = position k + c', k entries each) in pivot order.
+// S12 (k x (n-k), row-major; column c' = position k + c') in pivot order, from
+// the row-major working array W (r x n).
 __global__ void id_extract_kernel(int r, int64_t n, int k, const double* __restrict__ W,
                                   const int32_t* __restrict__ J, const double* __restrict__ diagR,
                                   double* __restrict__ S11, double* __restrict__ S12) {
@@ -271,12 +320,12 @@ __global__ void id_extract_kernel(int r, int64_t n, int k, const double* __restr
     const int64_t c = J[pos];
     if (pos < k) {
       double v;
-      if (i < pos) v = W[c * r + i];
+      if (i < pos) v = W[(int64_t)i * n + c];
       else if (i == pos) v = diagR[pos];
       else v = 0.0;
       S11[pos * k + i] = v;
     } else {
-      S12[(pos - k) * k + i] = W[c * r + i];
+      S12[(int64_t)i * (n - k) + (pos - k)] = W[(int64_t)i * n + c];
     }
   }
 }
@@ -292,35 +341,39 @@ cudaError_t launch_id_extract(int r, int64_t n, int k, const double* W, const in
   return cudaGetLastError();
 }
 
-// One warp per right-hand side; the running right-hand side sits in shared
-// memory.  Column-oriented back substitution:
-//   for i = kk-1 .. 0: x_i = s_i / U(i,i); s(0:i) -= x_i U(0:i, i).
+// One thread per right-hand side; the running right-hand side sits in shared
+// memory (sv[i * blockDim + thread]).  Column-oriented back substitution:
+//   for i = kk-1 .. 0: x_i = s_i / U(i,i); s(0:i) -= x_i U(0:i, i),
+// with U read by all threads at the same address (broadcast).
 template <typename TR, typename TO>
 __global__ void upper_solve_kernel(int kk, int64_t ncols, const double* __restrict__ Ug,
                                    int64_t us_i, int64_t us_t, const TR* __restrict__ rhs,
                                    int64_t rs_i, int64_t rs_c, TO* __restrict__ out,
                                    int64_t os_i, int64_t os_c, int* d_info) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  double* sv = (double*)dsm + (size_t)warp * kk;
-  for (int64_t c = (int64_t)blockIdx.x * nw + warp; c < ncols; c += (int64_t)gridDim.x * nw) {
-    for (int i = lane; i < kk; i += 32) sv[i] = (double)rhs[i * rs_i + c * rs_c];
-    __syncwarp();
+  double* sv = (double*)dsm;
+  const int t = threadIdx.x, bd = blockDim.x;
+  for (int64_t cb = (int64_t)blockIdx.x * bd; cb < ncols; cb += (int64_t)gridDim.x * bd) {
+    const int64_t c = cb + t;
+    const bool act = c < ncols;
+    if (act)
+      for (int i = 0; i < kk; ++i) sv[i * bd + t] = (double)rhs[i * rs_i + c * rs_c];
     for (int i = kk - 1; i >= 0; --i) {
       const double d = Ug[i * us_i + i * us_t];
-      double xi = sv[i] / d;
       if (!(d != 0.0)) {
-        xi = 0.0;
-        if (lane == 0) set_info(d_info, RSVD_ERR_NUMERIC);
+        if (act) sv[i * bd + t] = 0.0;
+        if (t == 0) set_info(d_info, RSVD_ERR_NUMERIC);
+        continue;
       }
-      __syncwarp();
-      if (lane == 0) sv[i] = xi;
-      for (int t = lane; t < i; t += 32) sv[t] -= xi * Ug[t * us_i + i * us_t];
-      __syncwarp();
+      if (act) {
+        const double xi = sv[i * bd + t] / d;
+        sv[i * bd + t] = xi;
+        const double* ucol = Ug + i * us_t;
+        for (int q = 0; q < i; ++q) sv[q * bd + t] = fma(-xi, ucol[q * us_i], sv[q * bd + t]);
+      }
     }
-    for (int i = lane; i < kk; i += 32) out[i * os_i + c * os_c] = (TO)sv[i];
-    __syncwarp();
+    if (act)
+      for (int i = 0; i < kk; ++i) out[i * os_i + c * os_c] = (TO)sv[i * bd + t];
   }
 }
 
@@ -329,18 +382,27 @@ cudaError_t launch_upper_solve(int kk, int64_t ncols, const double* Ug, int64_t 
                                int64_t us_t, const TR* rhs, int64_t rs_i, int64_t rs_c, TO* out,
                                int64_t os_i, int64_t os_c, int* d_info, cudaStream_t s) {
   if (kk <= 0 || ncols <= 0) return cudaSuccess;
-  if (kk > 2048) return cudaErrorInvalidValue;
-  const int warps = 8;
-  const size_t dyn = (size_t)warps * kk * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(upper_solve_kernel<TR, TO>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(warps * 2048 * sizeof(double)));
-  if (e != cudaSuccess) return e;
-  int64_t blocks = ceil_div(ncols, warps);
-  if (blocks > 4096) blocks = 4096;
-  upper_solve_kernel<TR, TO><<<(unsigned)blocks, warps * 32, dyn, s>>>(
+  if (kk > UPPER_SOLVE_MAX_K) return cudaErrorInvalidValue;
+  // threads per block: as many as fit 8*kk bytes each in 220 KB of shared
+  // memory (multiples of 32, at most 128), and no more blocks than columns need
+  int bd = (int)((220 * 1024) / ((size_t)kk * sizeof(double)));
+  bd = bd > 128 ? 128 : (bd / 32) * 32;
+  if (bd < 32) return cudaErrorInvalidValue;
+  const int sms = device_sm_count();
+  while (bd > 32 && ceil_div(ncols, bd) < sms) bd -= 32;
+  const size_t dyn = (size_t)bd * kk * sizeof(double);
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(upper_solve_kernel<TR, TO>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  int64_t blocks = ceil_div(ncols, bd);
+  if (blocks > 65535) blocks = 65535;
+  const int tr_ = trace_begin(RSVD_TRACE_SOLVE, s);
+  upper_solve_kernel<TR, TO><<<(unsigned)blocks, bd, dyn, s>>>(
       kk, ncols, Ug, us_i, us_t, rhs, rs_i, rs_c, out, os_i, os_c, d_info);
   count_launch();
+  trace_end(tr_, s);
   return cudaGetLastError();
 }
 

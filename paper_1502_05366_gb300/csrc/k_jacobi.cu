@@ -39,17 +39,55 @@ __device__ __forceinline__ void rr_pair(int r, int p, int N, int* a, int* b) {
   }
 }
 
+// Error-free transformations (Knuth TwoSum; TwoProduct through fma) for the
+// compensated dot product Dot2 of Ogita, Rump & Oishi (SIAM J. Sci. Comput.
+// 2005): the result is as accurate as if computed in twice the working
+// precision, so pairs are judged orthogonal on their stored values and not on
+// rounding noise of the dot product.
 template <typename T>
-__global__ void __launch_bounds__(JT) jacobi_kernel(int l, const T* __restrict__ M, int64_t ldm,
-                                                    T* __restrict__ Uh, int64_t lduh,
-                                                    double* __restrict__ Sh, T* scratch,
-                                                    int max_sweeps, int* d_info) {
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+  s = a + b;
+  const T z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
+// Warp-level reduction of one (p, s) compensated pair (TwoSum on the leading
+// parts, errors accumulated).
+template <typename T>
+__device__ __forceinline__ void warp_sum2(T& p, T& s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T op = __shfl_xor_sync(0xffffffffu, p, o);
+    const T os = __shfl_xor_sync(0xffffffffu, s, o);
+    T q;
+    two_sum(p, op, p, q);
+    s += os + q;
+  }
+}
+
+// 1024 threads for fp32; 512 for fp64.
+template <typename T>
+__host__ __device__ constexpr int jthreads() { return sizeof(T) == 8 ? 512 : 1024; }
+
+// One group of 8 lanes per column pair, so a round's l/2 pairs run at once;
+// each lane strides over the rows with step 8.  The dot products are plain;
+// when a pair's cosine is within a factor 64 of the threshold, gamma is
+// recomputed with Dot2 so convergence is judged on accurate values.
+template <typename T>
+__global__ void __launch_bounds__(jthreads<T>()) jacobi_kernel(int l, const T* __restrict__ M,
+                                                              int64_t ldm, T* __restrict__ Uh,
+                                                              int64_t lduh,
+                                                              double* __restrict__ Sh, T* scratch,
+                                                              int max_sweeps, int* d_info) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double s_sig[1024];
   __shared__ int s_rot;
   T* X = scratch ? scratch : (T*)dsm;  // column-major: X[j*l + i]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = JT / 32;
-  for (int t = tid; t < l * l; t += JT) {
+  constexpr int NT = jthreads<T>();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = NT / 32;
+  const int g = tid >> 3, gl = tid & 7, ngroups = NT / 8;
+  const unsigned gmask = 0xffu << (lane & ~7);
+  for (int t = tid; t < l * l; t += NT) {
     const int j = t / l, i = t - j * l;
     X[t] = M[(int64_t)i * ldm + j];
   }
@@ -61,34 +99,58 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(int l, const T* __restrict__
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int r = 0; r < N - 1; ++r) {
-      for (int p = warp; p < N / 2; p += nwarp) {
+      for (int p = g; p < N / 2; p += ngroups) {
         int a, b;
         rr_pair(r, p, N, &a, &b);
-        if (a >= l || b >= l) continue;
+        if (a >= l || b >= l) continue;          // uniform within the group
         T* xa = X + (int64_t)a * l;
         T* xb = X + (int64_t)b * l;
         T al = T(0), be = T(0), ga = T(0);
-        for (int i = lane; i < l; i += 32) {
+        for (int i = gl; i < l; i += 8) {
           const T u = xa[i], v = xb[i];
           al = fma(u, u, al);
           be = fma(v, v, be);
           ga = fma(u, v, ga);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(gmask, al, o, 8);
+          be += __shfl_xor_sync(gmask, be, o, 8);
+          ga += __shfl_xor_sync(gmask, ga, o, 8);
+        }
         if (!(al > T(0)) || !(be > T(0))) continue;
-        if (!(abs(ga) > tol * sqrt(al) * sqrt(be))) continue;
+        const T scale = sqrt(al) * sqrt(be);
+        if (abs(ga) < T(64) * tol * scale) {     // near the threshold: Dot2
+          T gp = T(0), gs = T(0);
+          for (int i = gl; i < l; i += 8) {
+            const T u = xa[i], v = xb[i];
+            const T h = u * v;
+            const T hr = fma(u, v, -h);
+            T e;
+            two_sum(gp, h, gp, e);
+            gs += e + hr;
+          }
+#pragma unroll
+          for (int o = 4; o > 0; o >>= 1) {
+            const T op = __shfl_xor_sync(gmask, gp, o, 8);
+            const T os = __shfl_xor_sync(gmask, gs, o, 8);
+            T e;
+            two_sum(gp, op, gp, e);
+            gs += os + e;
+          }
+          ga = gp + gs;
+        }
+        if (!(abs(ga) > tol * scale)) continue;
         const T zeta = (be - al) / (T(2) * ga);
         const T t = (zeta >= T(0) ? T(1) : T(-1)) / (abs(zeta) + sqrt(T(1) + zeta * zeta));
         const T c = T(1) / sqrt(T(1) + t * t);
-        const T s = c * t;
-        for (int i = lane; i < l; i += 32) {
+        const T sn = c * t;
+        for (int i = gl; i < l; i += 8) {
           const T u = xa[i], v = xb[i];
-          xa[i] = c * u - s * v;
-          xb[i] = s * u + c * v;
+          xa[i] = c * u - sn * v;
+          xb[i] = sn * u + c * v;
         }
-        if (lane == 0) atomicAdd(&s_rot, 1);
+        if (gl == 0) atomicAdd(&s_rot, 1);
       }
       __syncthreads();
     }
@@ -171,8 +233,10 @@ cudaError_t launch_svd_finalize(int l, const T* P, int64_t ldp, const T* Uin, in
                                 int64_t lduh, double* Sh, T* Vh, int64_t ldvh, int* d_info,
                                 cudaStream_t s) {
   if (l > 1024) return cudaErrorInvalidValue;
+  const int tr_ = trace_begin(RSVD_TRACE_JACOBI, s);
   svd_finalize_kernel<T><<<1, 1024, 0, s>>>(l, P, ldp, Uin, ldin, Uh, lduh, Sh, Vh, ldvh, d_info);
   count_launch();
+  trace_end(tr_, s);
   return cudaGetLastError();
 }
 template cudaError_t launch_svd_finalize<float>(int, const float*, int64_t, const float*, int64_t,
@@ -203,8 +267,11 @@ cudaError_t launch_jacobi(int l, const T* M, int64_t ldm, T* Uh, int64_t lduh, d
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }
-  jacobi_kernel<T><<<1, JT, dyn, s>>>(l, M, ldm, Uh, lduh, Sh, scr, max_sweeps, d_info);
+  const int tr_ = trace_begin(RSVD_TRACE_JACOBI, s);
+  jacobi_kernel<T><<<1, jthreads<T>(), dyn, s>>>(l, M, ldm, Uh, lduh, Sh, scr, max_sweeps,
+                                                  d_info);
   count_launch();
+  trace_end(tr_, s);
   return cudaGetLastError();
 }
 

@@ -182,15 +182,15 @@ cudaError_t launch_sign_fix(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V
   return cudaGetLastError();
 }
 
-// W (m x k doubles, row r contiguous) = C^T columns: W[r*k + i] = A[r, J[i]].
+// W (k x m doubles, row-major) = C^T with C = A(:, J[0:k]): W[i*m + r] = A[r, J[i]].
 template <typename T>
 __global__ void gather_ct_kernel(int64_t m, int k, const T* __restrict__ A, int64_t lda,
                                  const int32_t* __restrict__ J, double* __restrict__ W) {
   const int64_t total = m * k;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t / k;
-    const int i = (int)(t - r * k);
+    const int i = (int)(t / m);
+    const int64_t r = t - (int64_t)i * m;
     W[t] = (double)A[r * lda + J[i]];
   }
 }

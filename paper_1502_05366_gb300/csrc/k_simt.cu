@@ -169,11 +169,13 @@ cudaError_t launch_gemm_nn(int64_t M, int64_t N, int64_t K, const T* A, int64_t 
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(N, BN), (unsigned)ceil_div(M, BM));
   if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  const int tr_ = trace_begin(RSVD_TRACE_SIMT, s);
   if (B == nullptr)
     gemm_nn_kernel<T, true><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, seed, nvalid);
   else
     gemm_nn_kernel<T, false><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, seed, nvalid);
   count_launch();
+  trace_end(tr_, s);
   return cudaGetLastError();
 }
 
@@ -198,8 +200,10 @@ cudaError_t launch_gemm_tn_partial(int64_t M, int64_t N, int64_t K, const T* A, 
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(N, BN), (unsigned)ceil_div(M, BM), (unsigned)nsplit);
   if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
+  const int tr_ = trace_begin(RSVD_TRACE_SIMT, s);
   gemm_tn_kernel<T><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, P, ldp, kchunk);
   count_launch();
+  trace_end(tr_, s);
   return cudaGetLastError();
 }
 

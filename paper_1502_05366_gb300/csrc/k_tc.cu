@@ -69,6 +69,14 @@ struct TcParams {
   int64_t tiles, kiters, total;
   int maxseg;
   float* part;
+  // final outputs: tiles covered by one CTA are written by its epilogue,
+  // tiles split between CTAs by tc_reduce_kernel
+  float* out;
+  int64_t ldo;
+  int ncols;
+  __nv_bfloat16* out_hi;
+  __nv_bfloat16* out_lo;
+  int64_t ldt;
   const int* skip;
   int* d_info;
 };
@@ -285,12 +293,12 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
     if (lane == 0) {
       const uint32_t bytes = A_STAGE_BYTES + (OMEGA ? 0u : (uint32_t)NWT * (uint32_t)w_tile_bytes(L));
       int64_t last_issued = -1;
+      int64_t tile = it0 / P.kiters, kc = it0 - tile * P.kiters;
+      int s = 0;
+      uint32_t ph = 0;
       for (int64_t it = it0; it < it1; ++it) {
         const int64_t li = it - it0;
-        const int s = (int)(li % STAGES);
-        const uint32_t ph = (uint32_t)((li / STAGES) & 1);
         if (!mbar_wait(&done[s], ph ^ 1u, abort_flag, P.d_info)) break;
-        const int64_t tile = it / P.kiters, kc = it % P.kiters;
         unsigned char* st = dsm + s * SB;
         mbar_arrive_expect_tx(&full[s], bytes);
         if (FORM == 0)
@@ -305,15 +313,23 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
           tma_load_2d(st + A_STAGE_BYTES + 2 * w_tile_bytes(L), &mapW2, &full[s], (int)(kc * BK),
                       0);
         last_issued = li;
+        if (++kc == P.kiters) {
+          kc = 0;
+          ++tile;
+        }
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
       if (*abort_flag && last_issued >= 0) {
         // drain: wait (bounded) for the copies this thread issued
         const int64_t first = last_issued - STAGES + 1 > 0 ? last_issued - STAGES + 1 : 0;
         for (int64_t li = first; li <= last_issued; ++li) {
-          const int s = (int)(li % STAGES);
-          const uint32_t ph = (uint32_t)((li / STAGES) & 1);
+          const int sd = (int)(li % STAGES);
+          const uint32_t pd = (uint32_t)((li / STAGES) & 1);
           const long long t0 = clock64();
-          while (!mbar_try_wait(&full[s], ph) && clock64() - t0 < WAIT_LIMIT) {
+          while (!mbar_try_wait(&full[sd], pd) && clock64() - t0 < WAIT_LIMIT) {
           }
         }
       }
@@ -323,15 +339,12 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
     if (lane == 0) {
       const uint32_t idesc = make_idesc(BM, L);
       int64_t seg = -1;
-      int64_t cur_tile = -1;
+      int64_t kc = it0 % P.kiters;
+      int s = 0;
+      uint32_t ph = 0;
       for (int64_t it = it0; it < it1; ++it) {
-        const int64_t li = it - it0;
-        const int s = (int)(li % STAGES);
-        const uint32_t ph = (uint32_t)((li / STAGES) & 1);
-        const int64_t tile = it / P.kiters;
-        const bool seg_start = (tile != cur_tile);
+        const bool seg_start = (it == it0) || (kc == 0);
         if (seg_start) {
-          cur_tile = tile;
           ++seg;
           if (seg > 0 && !mbar_wait(acc_empty, (uint32_t)((seg - 1) & 1), abort_flag, P.d_info))
             break;
@@ -361,8 +374,13 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
           }
         }
         mma_commit(&done[s]);
-        const bool seg_end = (it + 1 == it1) || ((it + 1) / P.kiters != tile);
+        const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
         if (seg_end) mma_commit(acc_full);
+        if (++kc == P.kiters) kc = 0;
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
     }
   } else if (warp >= 4 && warp < 4 + NCONV) {
@@ -370,16 +388,17 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
     const int q = warp - 4;                 // TMEM lane quadrant (= warp % 4)
     const int r = 32 * q + lane;            // tile row handled by this thread
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    int64_t seg = -1, cur_tile = -1;
+    int64_t seg = -1;
+    int64_t tile = it0 / P.kiters, kc = it0 - tile * P.kiters;
+    const int64_t tile0 = tile;
+    bool whole = false;                     // current segment started at k-chunk 0
+    int s = 0;
+    uint32_t ph = 0;
     bool ok = true;
     for (int64_t it = it0; it < it1 && ok; ++it) {
-      const int64_t li = it - it0;
-      const int s = (int)(li % STAGES);
-      const uint32_t ph = (uint32_t)((li / STAGES) & 1);
-      const int64_t tile = it / P.kiters;
-      if (tile != cur_tile) {
-        cur_tile = tile;
+      if (it == it0 || kc == 0) {
         ++seg;
+        whole = (kc == 0);
       }
       if (!mbar_wait(&full[s], ph, abort_flag, P.d_info)) {
         ok = false;
@@ -414,37 +433,76 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&conv[s]);
-      const bool seg_end = (it + 1 == it1) || ((it + 1) / P.kiters != tile);
+      const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
       if (seg_end) {
         if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag, P.d_info)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const int64_t tile0 = it0 / P.kiters;
-        float* dst = P.part + ((int64_t)blockIdx.x * P.maxseg + (tile - tile0)) * (int64_t)BM * L;
-        for (int c0 = 0; c0 < L; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld16(lane_base + tmem + (uint32_t)c0, v);
-          tmem_wait_ld();
+        if (whole && kc + 1 == P.kiters) {
+          // this CTA holds the whole tile: final rows (+ transposed bf16 split)
+          const int64_t gr = tile * BM + r;
+          for (int c0 = 0; c0 < L; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(lane_base + tmem + (uint32_t)c0, v);
+            tmem_wait_ld();
+            if (gr < P.rows) {
+              float* orow = P.out + gr * P.ldo + c0;
+              const bool vec = (c0 + 16 <= P.ncols) && ((reinterpret_cast<uintptr_t>(orow) & 15u) == 0);
+              if (vec) {
 #pragma unroll
-          for (int c = 0; c < 16; ++c) dst[(int64_t)(c0 + c) * BM + r] = __uint_as_float(v[c]);
+                for (int c = 0; c < 16; c += 4)
+                  *reinterpret_cast<float4*>(orow + c) =
+                      make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]),
+                                  __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
+              }
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                const int col = c0 + c;
+                const float val = __uint_as_float(v[c]);
+                if (!vec && col < P.ncols) orow[c] = val;
+                if (P.out_hi) {
+                  const float w = col < P.ncols ? val : 0.0f;
+                  const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                  P.out_hi[(int64_t)col * P.ldt + gr] = h;
+                  P.out_lo[(int64_t)col * P.ldt + gr] = __float2bfloat16_rn(w - __bfloat162float(h));
+                }
+              }
+            }
+          }
+        } else {
+          float* dst = P.part + ((int64_t)blockIdx.x * P.maxseg + (tile - tile0)) * (int64_t)BM * L;
+          for (int c0 = 0; c0 < L; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(lane_base + tmem + (uint32_t)c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) dst[(int64_t)(c0 + c) * BM + r] = __uint_as_float(v[c]);
+          }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty);
+      }
+      if (++kc == P.kiters) {
+        kc = 0;
+        ++tile;
+      }
+      if (++s == STAGES) {
+        s = 0;
+        ph ^= 1u;
       }
     }
   } else if (OMEGA && warp >= 8 && warp < 8 + NGEN) {
     // ------------------------- Omega generator warps --------------------------
     const int gt = threadIdx.x - 8 * 32;   // 0 .. 255
     const int nq = L / 4;
+    int64_t kc = it0 % P.kiters;
+    int s = 0;
+    uint32_t ph = 0;
     for (int64_t it = it0; it < it1; ++it) {
-      const int64_t li = it - it0;
-      const int s = (int)(li % STAGES);
-      const uint32_t ph = (uint32_t)((li / STAGES) & 1);
       if (!mbar_wait(&done[s], ph ^ 1u, abort_flag, P.d_info)) break;
-      const int64_t kc = it % P.kiters;
       unsigned char* wt = dsm + s * SB + A_STAGE_BYTES;
       for (int e = gt; e < BK * nq; e += NGEN * 32) {
         const int kk = e % BK, qd = e / BK;
@@ -464,6 +522,11 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&genb[s]);
+      if (++kc == P.kiters) kc = 0;
+      if (++s == STAGES) {
+        s = 0;
+        ph ^= 1u;
+      }
     }
   }
 
@@ -477,54 +540,66 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
   }
 }
 
-// Fixed-order sum of the stream-K partial tiles into the fp32 output (ld ldo,
-// columns < ncols) and, when hi != nullptr, the transposed bf16 hi/lo split
-// (L x rows, ld ldt) used as the stored operand of a later GEMM.
-__global__ void tc_reduce_kernel(TcParams P, int G, float* __restrict__ out, int64_t ldo,
-                                 int ncols, __nv_bfloat16* __restrict__ hi,
-                                 __nv_bfloat16* __restrict__ lo, int64_t ldt) {
+// Fixed-order sum of the stream-K partials of the tiles split between CTAs.
+// Block (sub, z): boundary b = z + 1 (start of CTA b); the tile containing it
+// is handled by the first boundary inside it; the block sums one 32 x 32
+// sub-tile over the contributing CTAs in increasing order and writes the fp32
+// output and, when requested, the transposed bf16 split (padding zero).
+__global__ void tc_reduce_kernel(TcParams P, int G) {
   if (P.skip && *P.skip) return;
   __shared__ float tile_s[32][33];
-  const int64_t t = blockIdx.z;            // output tile
-  const int rg = blockIdx.x;               // 32-row group inside the tile
-  const int jg = blockIdx.y;               // 32-column group
+  __shared__ int64_t s_base[1024];
+  const int64_t b = (int64_t)blockIdx.y + 1;
+  const int64_t sb = (b * P.total) / G;
+  const int64_t t = sb / P.kiters;
+  if (sb == t * P.kiters) return;                           // boundary at a tile start
+  const int64_t sprev = ((b - 1) * P.total) / G;
+  if (b - 1 >= 1 && sprev > t * P.kiters) return;          // not the first boundary in t
+  const int64_t last = (t + 1) * P.kiters - 1;
+  const int64_t blo = b - 1;
   const int L = P.L;
-  const int64_t first = t * P.kiters, last = (t + 1) * P.kiters - 1;
-  // contributors: CTAs whose stream-K range meets [first, last]
-  int64_t blo = (first * G) / P.total;
-  while (blo > 0 && (blo * P.total) / G > first) --blo;
-  while (((blo + 1) * P.total) / G <= first) ++blo;
-  int64_t bhi = (last * G) / P.total;
-  while (bhi > 0 && (bhi * P.total) / G > last) --bhi;
-  while (((bhi + 1) * P.total) / G <= last) ++bhi;
+  const int tid = threadIdx.x + threadIdx.y * 32;
+  // contributors blo .. bhi: CTA c contributes iff start(c) <= last
+  int nctr;
+  __shared__ int s_n;
+  if (tid == 0) {
+    int64_t c = b;
+    while (c < G && (c * P.total) / G <= last) ++c;
+    s_n = (int)(c - blo);
+  }
+  __syncthreads();
+  nctr = s_n;
+  if (nctr > 1024) nctr = 1024;
+  for (int i = tid; i < nctr; i += 256) {
+    const int64_t c = blo + i;
+    const int64_t tile0 = ((c * P.total) / G) / P.kiters;
+    s_base[i] = (c * P.maxseg + (t - tile0)) * (int64_t)BM * L;
+  }
+  __syncthreads();
+  const int rg = blockIdx.x % (BM / 32), jg = blockIdx.x / (BM / 32);
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   for (int jj = ty; jj < 32; jj += 8) {
     const int j = jg * 32 + jj;
     float sum = 0.f;
-    if (j < L) {
-      for (int64_t b = blo; b <= bhi; ++b) {
-        const int64_t tile0 = ((b * P.total) / G) / P.kiters;
-        const float* src = P.part + (b * P.maxseg + (t - tile0)) * (int64_t)BM * L;
-        sum += src[(int64_t)j * BM + rg * 32 + tx];
-      }
-    }
+    if (j < L)
+      for (int i = 0; i < nctr; ++i) sum += P.part[s_base[i] + (int64_t)j * BM + rg * 32 + tx];
     tile_s[jj][tx] = sum;
   }
   __syncthreads();
   for (int rr = ty; rr < 32; rr += 8) {
     const int64_t i = t * BM + rg * 32 + rr;
     const int j = jg * 32 + tx;
-    if (i < P.rows && j < ncols) out[i * ldo + j] = tile_s[tx][rr];
+    if (i < P.rows && j < P.ncols) P.out[i * P.ldo + j] = tile_s[tx][rr];
   }
-  if (hi) {
+  if (P.out_hi) {
     for (int jj = ty; jj < 32; jj += 8) {
       const int j = jg * 32 + jj;
       const int64_t i = t * BM + rg * 32 + tx;
       if (j < L && i < P.rows) {
-        const float v = (j < ncols) ? tile_s[jj][tx] : 0.0f;
+        const float v = (j < P.ncols) ? tile_s[jj][tx] : 0.0f;
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi[(int64_t)j * ldt + i] = h;
-        lo[(int64_t)j * ldt + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+        P.out_hi[(int64_t)j * P.ldt + i] = h;
+        P.out_lo[(int64_t)j * P.ldt + i] = __float2bfloat16_rn(v - __bfloat162float(h));
       }
     }
   }
@@ -635,6 +710,12 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   P.total = total;
   P.maxseg = maxseg;
   P.part = g.part;
+  P.out = g.out;
+  P.ldo = g.ldo;
+  P.ncols = g.ncols;
+  P.out_hi = (__nv_bfloat16*)g.out_hi;
+  P.out_lo = (__nv_bfloat16*)g.out_lo;
+  P.ldt = g.ldt;
   P.skip = g.skip;
   P.d_info = g.d_info;
 
@@ -679,15 +760,14 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   else
     return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
-  // fixed-order reduction of the partial tiles
-  dim3 rgrid(BM / 32, (unsigned)ceil_div(g.L, 32), (unsigned)tiles);
-  if (tiles > 65535) return cudaErrorInvalidConfiguration;
-  const int tr = trace_begin(RSVD_TRACE_REDUCE, s);
-  tc_reduce_kernel<<<rgrid, dim3(32, 8), 0, s>>>(P, (int)G, g.out, g.ldo, g.ncols,
-                                                 (__nv_bfloat16*)g.out_hi,
-                                                 (__nv_bfloat16*)g.out_lo, g.ldt);
-  count_launch();
-  trace_end(tr, s);
+  // fixed-order reduction of the tiles split between CTAs
+  if (G > 1) {
+    dim3 rgrid((unsigned)((BM / 32) * ceil_div(g.L, 32)), (unsigned)(G - 1));
+    const int tr = trace_begin(RSVD_TRACE_REDUCE, s);
+    tc_reduce_kernel<<<rgrid, dim3(32, 8), 0, s>>>(P, (int)G);
+    count_launch();
+    trace_end(tr, s);
+  }
   return cudaGetLastError();
 }
 

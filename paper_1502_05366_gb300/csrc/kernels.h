@@ -58,6 +58,7 @@ template <typename T>
 cudaError_t launch_sign_fix(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V,
                             int64_t ldv, int* signs, cudaStream_t s);
 // Gathers for ID/CUR.
+// W (k x m doubles, row-major) = C^T with C = A(:, J[0:k]): W[i*m + r] = A[r, J[i]].
 template <typename T>
 cudaError_t launch_gather_ct(int64_t m, int k, const T* A, int64_t lda, const int32_t* J,
                              double* W, cudaStream_t s);
@@ -88,8 +89,10 @@ struct CholArgs {
   void* Wlo;      // L x L bf16 second term
   void* Wlo2;     // L x L bf16 third term
   void* scratch;  // global fallback storage when the matrix does not fit in smem
-  int* flags;     // [0] third pass needed, [1] a shift was used, [2] = 1 - [0]
+  int* flags;     // [0] third pass needed, [1] a shift was used, [2] skip pass 3,
+                  // [3] skip pass 2 (conditional second pass)
   int pass;       // 1, 2 or 3
+  int skip_idx;   // when >= 0 and flags[skip_idx] == 1: write R = I and return
   int* d_info;
 };
 template <typename T>
@@ -114,19 +117,23 @@ struct CpqrArgs {
   int r;            // rows of the sketch
   int64_t n;        // columns
   int k;            // steps
-  double* W;        // n x r, column c contiguous at W + c*r (overwritten)
+  double* W;        // r x n row-major, element (i, c) at W[i*n + c] (overwritten)
   int32_t* J;       // n permutation (output)
   int64_t* where;   // n scratch: position of each original column
   double* gaps;     // k (may be null)
   double* pval;     // 2 * 1024 * 2 scratch (best, second per CTA)
   int64_t* pidx;    // 2 * 1024 scratch
-  double* nrm;      // n scratch: residual norms^2 (-1 once pivoted)
+  double* nrm;      // 2n scratch: residual norms^2 (-1 once pivoted), last exact norms^2
   double* diagR;    // k: diagonal of S (the Householder betas)
   unsigned* bar;    // 1 counter, zeroed by the launcher
   int* d_info;
+  int tpc;          // threads per column (set by the launcher)
 };
 cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s);
 size_t cpqr_scratch_bytes(int64_t n);
+// Largest triangle the many-right-hand-side solve handles (one 32-thread block
+// of kk doubles each in 220 KB of shared memory).
+constexpr int UPPER_SOLVE_MAX_K = 880;
 // Upper-triangular solve for many right-hand sides:
 //   for c < ncols: U x = rhs(:, c), out(:, c) = x; U(i, t) = Ug[i*us_i + t*us_t].
 template <typename TR, typename TO>

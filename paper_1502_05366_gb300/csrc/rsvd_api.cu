@@ -222,13 +222,19 @@ struct Engine {
   // X (rows x L, l valid columns, zero padding) -> Q in Y (rows x L).  For the
   // tensor-core path `split` holds the hi/lo of X^T on entry and of Q^T on exit.
   // When want_R, ob.Racc ends as R with X = Q R.
+  // full = true: CholeskyQR2 plus the conditional third pass (orthonormal Q).
+  // full = false (inside the power scheme, where any well-conditioned basis of
+  // range(X) gives the same subspace): one pass, and the second and third
+  // passes only when the first one needed a shift (numerically rank-deficient
+  // X), decided on the device.
   rsvd_status orth(int64_t rows, int l, int L, T* X, T* Y, Split* split, OrthBufs& ob,
-                   float* part, T* slabs, bool want_R) {
+                   float* part, T* slabs, bool want_R, bool full = true) {
     LK(cudaMemsetAsync(ob.flags, 0, 4 * sizeof(int), c.stream));
     T* src = X;
     T* dst = Y;
     for (int pass = 1; pass <= 3; ++pass) {
-      const int* skip = (pass == 3) ? ob.flags + 2 : nullptr;
+      const int skip_idx = (pass == 3) ? 2 : ((pass == 2 && !full) ? 3 : -1);
+      const int* skip = skip_idx >= 0 ? ob.flags + skip_idx : nullptr;
       // Gram G = src^T src
       rsvd_status st = gemm_t(L, rows, L, src, L, split, src, L, ob.G, L, L, nullptr, part, slabs,
                               skip, true);
@@ -246,6 +252,7 @@ struct Engine {
       a.scratch = ob.chol_scratch;
       a.flags = ob.flags;
       a.pass = pass;
+      a.skip_idx = skip_idx;
       a.d_info = c.d_info;
       LK(launch_chol<T>(a, c.stream));
       if (want_R) {
@@ -260,9 +267,9 @@ struct Engine {
       st = gemm_n(rows, L, L, src, L, rows, L, false, 0, L, &w, ob.Rinv, L, dst, L, L, split,
                   part, skip);
       if (st != RSVD_OK) return st;
-      if (pass == 3 && tc) {  // third pass skipped: Q2 carried over unchanged
+      if (skip && tc) {  // pass skipped: the previous Q carried over unchanged
         if (!c.dry) {
-          if (!c.run(launch_cond_copy<float>(ob.flags + 2, rows * (int64_t)L, (const float*)src,
+          if (!c.run(launch_cond_copy<float>(skip, rows * (int64_t)L, (const float*)src,
                                              (float*)dst, c.stream)))
             return RSVD_ERR_CUDA;
         }
@@ -271,7 +278,7 @@ struct Engine {
       src = dst;
       dst = t;
     }
-    // after three passes the result sits in Y (X -> Y -> X -> Y)
+    // three passes (run or carried over) leave the result in Y (X -> Y -> X -> Y)
     return RSVD_OK;
   }
 
@@ -332,7 +339,7 @@ struct Engine {
     int prod = 0;  // index of the next product with A or A^T (Alg. 5 orth test)
     for (int j = 1; j <= q; ++j) {
       if (prod % o.s == 0) {
-        st = orth(m, l, L, b.Y, b.Ytmp, &b.ys, b.ob, b.part, b.slabs, false);
+        st = orth(m, l, L, b.Y, b.Ytmp, &b.ys, b.ob, b.part, b.slabs, false, false);
         if (st != RSVD_OK) return st;
         std::swap(b.Y, b.Ytmp);
       }
@@ -341,7 +348,7 @@ struct Engine {
       st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr);
       if (st != RSVD_OK) return st;
       if (prod % o.s == 0) {
-        st = orth(n, l, L, b.Z, b.Ztmp, &b.zs, b.ob, b.part, b.slabs, false);
+        st = orth(n, l, L, b.Z, b.Ztmp, &b.zs, b.ob, b.part, b.slabs, false, false);
         if (st != RSVD_OK) return st;
         std::swap(b.Z, b.Ztmp);
       }
@@ -424,7 +431,7 @@ struct Engine {
 
   // ---------------- ID (Sec. 3.5) and CUR (Sec. 3.6) ----------------
   struct IdBufs {
-    double* W;       // n x r
+    double* W;       // r x n row-major
     int64_t* where;  // n
     double* pval;
     int64_t* pidx;
@@ -432,7 +439,7 @@ struct Engine {
     double* diagR;   // k
     unsigned* bar;
     double* S11;     // k x k
-    double* S12;     // (n-k) x k
+    double* S12;     // k x (n-k) row-major
     int32_t* J;      // n (internal copy)
     T* Tt;           // (n-k) x k
   };
@@ -442,7 +449,7 @@ struct Engine {
     d.where = c.template take<int64_t>((size_t)n);
     d.pval = c.template take<double>(2 * 1024 * 2);
     d.pidx = c.template take<int64_t>(2 * 1024);
-    d.nrm = c.template take<double>((size_t)n);
+    d.nrm = c.template take<double>((size_t)2 * n);
     d.diagR = c.template take<double>((size_t)k);
     d.bar = c.template take<unsigned>(4);
     d.J = c.template take<int32_t>((size_t)n);
@@ -458,8 +465,8 @@ struct Engine {
     return d;
   }
 
-  // CPQR of the r x n matrix whose column c is d.W[c*r .. c*r + r) (already
-  // filled), k steps; J into d.J; Tt ((n-k) x k) = (S11^{-1} S12)^T.
+  // CPQR of the r x n row-major matrix in d.W (already filled), k steps; J
+  // into d.J; Tt ((n-k) x k) = (S11^{-1} S12)^T.
   rsvd_status id_core(IdBufs& d, int r, int64_t n, int k, double* gaps) {
     CpqrArgs a{};
     a.r = r;
@@ -479,10 +486,10 @@ struct Engine {
     LK(launch_cpqr(a, &grid, c.stream));
     if (!d.Tt) return RSVD_OK;   // pivots only (row ID of the CUR)
     LK(launch_id_extract(r, n, k, d.W, d.J, d.diagR, d.S11, d.S12, c.stream));
-    // S11 column-major: U(i, t) = S11[t*k + i]; rhs(i, c) = S12[c*k + i];
+    // S11 column-major: U(i, t) = S11[t*k + i]; rhs(i, c) = S12[i*(n-k) + c];
     // out Tt(c, i) = Tt[c*k + i]
-    LK(launch_upper_solve<double, T>(k, n - k, d.S11, 1, k, d.S12, 1, k, d.Tt, 1, k, c.d_info,
-                                     c.stream));
+    LK(launch_upper_solve<double, T>(k, n - k, d.S11, 1, k, d.S12, n - k, 1, d.Tt, 1, k,
+                                     c.d_info, c.stream));
     return RSVD_OK;
   }
 
@@ -624,8 +631,8 @@ static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n,
     if (Bto) LK(launch_copy2d<T, T>(n, l, qbb.Z, L, Bto, ldbt, c.stream));
   }
   if (want & (W_ID | W_CUR)) {
-    // B = Bt^T: column j of B is row j of Bt (before the SVD overwrites nothing of Bt)
-    LK(launch_copy2d<T, double>(n, l, qbb.Z, L, idb.W, l, c.stream));
+    // B = Bt^T (l x n, row-major FP64), taken before the SVD reuses Bt's buffer
+    LK(launch_transpose<T, double>(n, l, qbb.Z, L, idb.W, n, c.stream));
     st = e.id_core(idb, l, n, k, nullptr);
     if (st != RSVD_OK) return st;
     if (J) LK(launch_copy_i32(n, idb.J, J, c.stream));
@@ -688,7 +695,7 @@ static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t 
   }
   if ((want & W_CUR) && (!Jc || !Ir || !Ucur || lducur < k || k >= n || k >= m))
     return RSVD_ERR_INVALID_ARG;
-  if ((want & (W_ID | W_CUR)) && k > 2048) return RSVD_ERR_UNSUPPORTED;
+  if ((want & (W_ID | W_CUR)) && k > UPPER_SOLVE_MAX_K) return RSVD_ERR_UNSUPPORTED;
   if (!work && work_bytes) return RSVD_ERR_INVALID_ARG;
   if (work && !aligned16(work)) return RSVD_ERR_INVALID_ARG;
   Ctx c;
@@ -922,7 +929,7 @@ static rsvd_status cpqr_impl(Ctx& c, int r, int64_t n, int k, const double* M, i
   auto idb = e.take_id(r, n, k, true);
   if (c.dry) return RSVD_OK;
   if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
-  LK(launch_transpose<double, double>(r, n, M, ldm, idb.W, r, c.stream));
+  LK(launch_copy2d<double, double>(r, n, M, ldm, idb.W, n, c.stream));
   rsvd_status st = e.id_core(idb, r, n, k, gaps);
   if (st != RSVD_OK) return st;
   LK(launch_copy_i32(n, idb.J, J, c.stream));
@@ -1108,7 +1115,8 @@ rsvd_status rsvd_small_svd(int l, int dtype, const void* M, int64_t ldm, void* U
 }
 
 size_t rsvd_cpqr_workspace_size(int r, int64_t n, int k) {
-  if (r < 1 || n < 1 || k < 1 || k > r || k > n || r > 8192 || k > 2048 || n > 0x7fffffffLL)
+  if (r < 1 || n < 1 || k < 1 || k > r || k > n || r > 8192 || k > UPPER_SOLVE_MAX_K ||
+      n > 0x7fffffffLL)
     return 0;
   Ctx c;
   cpqr_impl(c, r, n, k, nullptr, n, nullptr, nullptr, 0, nullptr);
@@ -1118,8 +1126,9 @@ size_t rsvd_cpqr_workspace_size(int r, int64_t n, int k) {
 rsvd_status rsvd_cpqr_id(int r, int64_t n, int k, const double* M, int64_t ldm, int32_t* J,
                          double* T, int64_t ldt, double* gaps, void* work, size_t work_bytes,
                          int* d_info, void* stream) {
-  if (r < 1 || n < 1 || k < 1 || k > r || k > n || r > 8192 || k > 2048 || n > 0x7fffffffLL)
+  if (r < 1 || n < 1 || k < 1 || k > r || k > n || r > 8192 || n > 0x7fffffffLL)
     return RSVD_ERR_INVALID_ARG;
+  if (k > UPPER_SOLVE_MAX_K) return RSVD_ERR_UNSUPPORTED;
   if (!M || !J || ldm < n || (T && n > k && ldt < n - k)) return RSVD_ERR_INVALID_ARG;
   if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
   Ctx c = make_ctx(work, work_bytes, d_info, stream);

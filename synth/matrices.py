@@ -86,24 +86,26 @@ def low_rank_np(m, n, rank, seed=0, dtype="float64"):
 
 def make_matrix_torch(m, n, sigma, noise=0.0, seed=0, dtype="float32", device="cuda",
                       chunk_rows=8192):
-    """The same recipe generated with torch on a device (large workloads).
+    """The same recipe with the large products on a device (large workloads).
 
-    Uses torch's own seeded generator on ``device``; the values differ from
-    ``make_matrix_np`` for the same seed.  Returns a contiguous row-major tensor.
+    The Gaussian factors are drawn and orthonormalised (LAPACK QR) on the host
+    with numpy; A = U diag(sigma) V^T and the noise are formed on ``device``
+    with torch's seeded generator.  Values differ from ``make_matrix_np`` for
+    the same seed.  Returns a contiguous row-major tensor.
     """
     import torch
+    sigma = np.asarray(sigma, dtype=np.float64)
+    r = sigma.size
+    rng = np.random.default_rng(seed)
+    cdtype = torch.float64 if dtype == "float64" else torch.float32
+    U = torch.from_numpy(_orthonormal_np(rng, m, r) * sigma[None, :]).to(device, cdtype)
+    V = torch.from_numpy(_orthonormal_np(rng, n, r)).to(device, cdtype)
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
-    cdtype = torch.float64 if dtype == "float64" else torch.float32
-    sig = torch.as_tensor(np.asarray(sigma), dtype=cdtype, device=device)
-    r = sig.numel()
     prev_tf32 = torch.backends.cuda.matmul.allow_tf32 if str(device).startswith("cuda") else None
     if prev_tf32 is not None:
         torch.backends.cuda.matmul.allow_tf32 = False
     try:
-        U = torch.linalg.qr(torch.randn(m, r, generator=g, device=device, dtype=cdtype))[0]
-        V = torch.linalg.qr(torch.randn(n, r, generator=g, device=device, dtype=cdtype))[0]
-        U.mul_(sig[None, :])
         tdtype = {"float32": torch.float32, "bfloat16": torch.bfloat16,
                   "float64": torch.float64}[dtype]
         A = torch.empty(m, n, dtype=tdtype, device=device)

@@ -127,8 +127,8 @@ def test_exact_rank_recovery(dtype, q):
     Q, Bt = rs.qb(_dev(A, tdt), 10, 4, q, 11)
     Qn, Btn = Q.double().cpu().numpy(), Bt.double().cpu().numpy()
     err = np.linalg.norm(A - Qn @ Btn.T) / np.linalg.norm(A)
-    # FP32 tensor-core products carry 16-bit splits: noise ~2^-17 per entry
-    assert err <= (1e-12 if dtype == "float64" else 3e-5), err
+    # FP32 tensor-core products carry 16-bit splits: noise ~2^-17 per product
+    assert err <= (1e-12 if dtype == "float64" else 5e-5), err
     assert np.linalg.norm(Qn.T @ Qn - np.eye(14)) <= (1e-12 if dtype == "float64" else 5e-5)
 
 
