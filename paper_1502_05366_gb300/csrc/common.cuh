@@ -71,8 +71,11 @@ __device__ __forceinline__ Words4 omega_words(uint64_t seed, uint32_t row, uint3
 }
 
 // u = (2*(x >> 9) + 1) * 2^-24: odd multiples of 2^-24 in (0, 1), exact in fp32.
+// In single precision it is formed without an integer conversion: the float
+// with exponent 0 and mantissa x >> 9 is 1 + (x >> 9) 2^-23, and subtracting
+// 1 - 2^-24 leaves (2 (x >> 9) + 1) 2^-24, exactly representable, so exact.
 __device__ __forceinline__ float word_to_uniform_f(uint32_t x) {
-  return (float)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f;
+  return __uint_as_float(0x3f800000u | (x >> 9)) - 0x1.fffffep-1f;
 }
 __device__ __forceinline__ double word_to_uniform_d(uint32_t x) {
   return (double)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8;

@@ -283,7 +283,9 @@ cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel, PT, dyn);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  int64_t G = sms;
+  // one SM is left to a single-CTA kernel running beside the CPQR on another
+  // stream (the Jacobi SVD of the combined SVD + ID/CUR call)
+  int64_t G = sms > 1 ? sms - 1 : 1;
   const int64_t byn = ceil_div(a.n, 32);
   if (G > byn) G = byn;
   if (G > 1024) G = 1024;

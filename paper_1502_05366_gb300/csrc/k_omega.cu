@@ -1,0 +1,418 @@
+// Sketch Y = A Omega (Sec. 3.1, Fig. 1 step 2) on the tcgen05 tensor cores,
+// with Omega generated inside the kernel from its Philox counter stream and
+// never stored.
+//
+// Generating Omega is the cost of this GEMM: every 128-row M-tile needs the
+// whole n x l Omega, i.e. l/128 Gaussians per entry of A.  Here one stream-K
+// unit is a pair of M-tiles (256 rows of A) that share every generated Omega
+// stage, which halves the Gaussians per entry of A.  The two fp32 accumulators
+// (up to 256 columns each) take all 512 TMEM columns, so the bf16 hi/lo split
+// of A is staged in shared memory and both MMA operands come from shared-
+// memory descriptors.  Arithmetic as in k_tc.cu: a0 w0 + a1 w0 with
+// x ~ a0 + a1 (16 significant bits) and Omega bf16-exact.
+//
+// Roles (640 threads, one CTA per SM, persistent stream-K over the flattened
+// (unit, k-chunk) space):
+//   warp 0       TMA producer: fp32 A block (256 rows x 32) into a 3-stage ring
+//   warp 1       MMA issuer (one thread) and TMEM owner
+//   warps 4-11   converters: fp32 rows -> bf16 hi/lo rows (64-byte swizzled,
+//                K-major) in a 2-stage operand ring; then the epilogue of
+//                their TMEM lane quadrant of their tile
+//   warps 12-19  generators: the bf16 Omega tile (same layout) in the operand
+//                ring; one thread makes 8 K-consecutive quads and stores each
+//                of its 4 columns as one 16-byte chunk
+// Every wait is bounded (about 1 s of clock); on expiry the kernel records
+// RSVD_ERR_TIMEOUT, all roles leave, the producer drains its copies in flight
+// and TMEM is freed.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace rsvd {
+
+using namespace tc;
+
+namespace {
+constexpr int OBM = 128;                      // rows of one M-tile (MMA M)
+constexpr int OUNIT = 2 * OBM;                // rows of one stream-K unit
+constexpr int OBK = 32;                       // K per stage
+constexpr int F_ST = 3;                       // fp32 A stages
+constexpr int B_ST = 2;                       // bf16 operand stages
+constexpr int F_BYTES = OUNIT * OBK * 4;      // 32 KB
+constexpr int AT_BYTES = OBM * OBK * 2;       // 8 KB: one tile, hi or lo
+constexpr int NCONV = 8;                      // warps 4..11
+constexpr int NGEN = 8;                       // warps 12..19
+constexpr int OTHREADS = 32 * (12 + NGEN);    // 640
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC_STRIDE = 256;          // TMEM column of the second accumulator
+
+__host__ __device__ constexpr int w_bytes(int L) { return L * OBK * 2; }
+__host__ __device__ constexpr int b_stage_bytes(int L) { return 4 * AT_BYTES + w_bytes(L); }
+size_t omega_smem(int L) { return 1024 + (size_t)F_ST * F_BYTES + (size_t)B_ST * b_stage_bytes(L) + 256; }
+
+// Byte offset of the 16-byte chunk c (0..3) of row r in a K-major tile of
+// 64-byte rows with the 64-byte swizzle (8-row groups of 512 bytes).
+__device__ __forceinline__ uint32_t sw64_off(uint32_t r, uint32_t c) {
+  return r * 64u + ((c ^ ((r >> 1) & 3u)) << 4);
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+// D[tmem] (+)= A[smem desc] * B[smem desc], kind::f16 (bf16 in, fp32 accumulate).
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+}  // namespace
+
+__global__ void __launch_bounds__(OTHREADS, 1)
+    tc_omega_kernel(const __grid_constant__ CUtensorMap mapA, TcParams P) {
+  extern __shared__ __align__(1024) unsigned char dsm_raw[];
+  if (P.skip && *P.skip) return;
+  unsigned char* dsm = (unsigned char*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  const int L = P.L;
+  const int BSB = b_stage_bytes(L);
+  unsigned char* fring = dsm;
+  unsigned char* bring = dsm + F_ST * F_BYTES;
+  uint64_t* bars = (uint64_t*)(bring + B_ST * BSB);
+  uint64_t* ffull = bars;                 // fp32 block landed (TMA bytes)
+  uint64_t* fempty = bars + F_ST;         // fp32 block read by the converters
+  uint64_t* aready = bars + 2 * F_ST;     // bf16 A tiles written
+  uint64_t* wready = aready + B_ST;       // Omega tile written
+  uint64_t* bdone = wready + B_ST;        // MMAs of the operand stage finished
+  uint64_t* acc_full = bdone + B_ST;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_holder = (uint32_t*)(acc_empty + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x;
+  const int64_t it0 = (blockIdx.x * P.total) / G;
+  const int64_t it1 = ((blockIdx.x + 1) * P.total) / G;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < F_ST; ++s) {
+      mbar_init(&ffull[s], 1);
+      mbar_init(&fempty[s], NCONV);
+    }
+    for (int s = 0; s < B_ST; ++s) {
+      mbar_init(&aready[s], NCONV);
+      mbar_init(&wready[s], NGEN);
+      mbar_init(&bdone[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, NCONV);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0 && lane == 0) prefetch_map(&mapA);
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      int64_t last_issued = -1;
+      int64_t unit = it0 / P.kiters, kc = it0 - unit * P.kiters;
+      int fs = 0;
+      uint32_t fph = 0;
+      for (int64_t it = it0; it < it1; ++it) {
+        if (!mbar_wait(&fempty[fs], fph ^ 1u, abort_flag, P.d_info)) break;
+        mbar_arrive_expect_tx(&ffull[fs], (uint32_t)F_BYTES);
+        tma_load_2d(fring + fs * F_BYTES, &mapA, &ffull[fs], (int)(kc * OBK), (int)(unit * OUNIT));
+        last_issued = it - it0;
+        if (++kc == P.kiters) {
+          kc = 0;
+          ++unit;
+        }
+        if (++fs == F_ST) {
+          fs = 0;
+          fph ^= 1u;
+        }
+      }
+      if (*abort_flag && last_issued >= 0) {
+        const int64_t first = last_issued - F_ST + 1 > 0 ? last_issued - F_ST + 1 : 0;
+        for (int64_t li = first; li <= last_issued; ++li) {
+          const int sd = (int)(li % F_ST);
+          const uint32_t pd = (uint32_t)((li / F_ST) & 1);
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&ffull[sd], pd) && clock64() - t0 < WAIT_LIMIT) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------- MMA issuer -------------------------------
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(OBM, L);
+      int64_t seg = -1;
+      int64_t kc = it0 % P.kiters;
+      int bs = 0;
+      uint32_t bph = 0;
+      for (int64_t it = it0; it < it1; ++it) {
+        const bool seg_start = (it == it0) || (kc == 0);
+        if (seg_start) {
+          ++seg;
+          if (seg > 0 && !mbar_wait(acc_empty, (uint32_t)((seg - 1) & 1), abort_flag, P.d_info))
+            break;
+        }
+        if (!mbar_wait(&aready[bs], bph, abort_flag, P.d_info)) break;
+        if (!mbar_wait(&wready[bs], bph, abort_flag, P.d_info)) break;
+        tc_fence_after();
+        const uint32_t base = smem_u32(bring + bs * BSB);
+#pragma unroll
+        for (int kk = 0; kk < OBK / 16; ++kk) {
+          const uint64_t bw = sw64_desc(base + 4u * AT_BYTES + 32u * kk);
+          const uint32_t acc0 = (seg_start && kk == 0) ? 0u : 1u;
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const uint32_t d = tmem + ACC_STRIDE * (uint32_t)t;
+            mma_ss(d, sw64_desc(base + (uint32_t)(2 * t) * AT_BYTES + 32u * kk), bw, idesc, acc0);
+            mma_ss(d, sw64_desc(base + (uint32_t)(2 * t + 1) * AT_BYTES + 32u * kk), bw, idesc, 1u);
+          }
+        }
+        mma_commit(&bdone[bs]);
+        const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
+        if (seg_end) mma_commit(acc_full);
+        if (++kc == P.kiters) kc = 0;
+        if (++bs == B_ST) {
+          bs = 0;
+          bph ^= 1u;
+        }
+      }
+    }
+  } else if (warp >= 4 && warp < 4 + NCONV) {
+    // ------------------------ converters and epilogue -------------------------
+    const int t = (warp - 4) >> 2;          // M-tile of the unit
+    const int q = warp & 3;                 // TMEM lane quadrant (= warp % 4)
+    const int r = 32 * q + lane;            // row within the tile
+    const int rr = t * OBM + r;             // row within the fp32 block
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const uint32_t acc = tmem + ACC_STRIDE * (uint32_t)t;
+    int64_t seg = -1;
+    int64_t unit = it0 / P.kiters, kc = it0 - unit * P.kiters;
+    const int64_t unit0 = unit;
+    bool whole = false;
+    int fs = 0, bs = 0;
+    uint32_t fph = 0, bph = 0;
+    for (int64_t it = it0; it < it1; ++it) {
+      if (it == it0 || kc == 0) {
+        ++seg;
+        whole = (kc == 0);
+      }
+      if (!mbar_wait(&ffull[fs], fph, abort_flag, P.d_info)) break;
+      // 128B-swizzled rows of 32 fp32: 16-byte chunk c of row rr sits at c ^ (rr & 7)
+      float x[32];
+      const unsigned char* row = fring + fs * F_BYTES + rr * 128;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(row + ((c ^ (rr & 7)) << 4));
+        x[4 * c] = v.x;
+        x[4 * c + 1] = v.y;
+        x[4 * c + 2] = v.z;
+        x[4 * c + 3] = v.w;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&fempty[fs]);
+      uint32_t hi[16], lo[16];
+      split_row(x, hi, lo);
+      if (!mbar_wait(&bdone[bs], bph ^ 1u, abort_flag, P.d_info)) break;
+      const uint32_t ab = smem_u32(bring + bs * BSB + 2 * t * AT_BYTES);
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const uint32_t o = sw64_off((uint32_t)r, (uint32_t)cc);
+        st_shared_v4(ab + o, hi[4 * cc], hi[4 * cc + 1], hi[4 * cc + 2], hi[4 * cc + 3]);
+        st_shared_v4(ab + AT_BYTES + o, lo[4 * cc], lo[4 * cc + 1], lo[4 * cc + 2],
+                     lo[4 * cc + 3]);
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&aready[bs]);
+      const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
+      if (seg_end) {
+        if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag, P.d_info)) break;
+        tc_fence_after();
+        if (whole && kc + 1 == P.kiters) {
+          // this CTA holds the whole unit: final rows (+ transposed bf16 split)
+          const int64_t gr = unit * OUNIT + rr;
+          for (int c0 = 0; c0 < L; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(lane_base + acc + (uint32_t)c0, v);
+            tmem_wait_ld();
+            if (gr < P.rows) {
+              float* orow = P.out + gr * P.ldo + c0;
+              const bool vec =
+                  (c0 + 16 <= P.ncols) && ((reinterpret_cast<uintptr_t>(orow) & 15u) == 0);
+              if (vec) {
+#pragma unroll
+                for (int c = 0; c < 16; c += 4)
+                  *reinterpret_cast<float4*>(orow + c) =
+                      make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]),
+                                  __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
+              }
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                const int col = c0 + c;
+                const float val = __uint_as_float(v[c]);
+                if (!vec && col < P.ncols) orow[c] = val;
+                if (P.out_hi) {
+                  const float w = col < P.ncols ? val : 0.0f;
+                  const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                  P.out_hi[(int64_t)col * P.ldt + gr] = h;
+                  P.out_lo[(int64_t)col * P.ldt + gr] =
+                      __float2bfloat16_rn(w - __bfloat162float(h));
+                }
+              }
+            }
+          }
+        } else {
+          float* dst =
+              P.part + ((int64_t)blockIdx.x * P.maxseg + (unit - unit0)) * (int64_t)OUNIT * L;
+          for (int c0 = 0; c0 < L; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(lane_base + acc + (uint32_t)c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              dst[(int64_t)(c0 + c) * OUNIT + rr] = __uint_as_float(v[c]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
+      }
+      if (++kc == P.kiters) {
+        kc = 0;
+        ++unit;
+      }
+      if (++fs == F_ST) {
+        fs = 0;
+        fph ^= 1u;
+      }
+      if (++bs == B_ST) {
+        bs = 0;
+        bph ^= 1u;
+      }
+    }
+  } else if (warp >= 12 && warp < 12 + NGEN) {
+    // ------------------------- Omega generator warps --------------------------
+    const int gt = threadIdx.x - 12 * 32;   // 0 .. 32 NGEN - 1
+    const int nunits = L;                   // (L / 4 quads) x (4 chunks of 8 K-rows)
+    int64_t kc = it0 % P.kiters;
+    int bs = 0;
+    uint32_t bph = 0;
+    for (int64_t it = it0; it < it1; ++it) {
+      if (!mbar_wait(&bdone[bs], bph ^ 1u, abort_flag, P.d_info)) break;
+      const uint32_t wb = smem_u32(bring + bs * BSB + 4 * AT_BYTES);
+      for (int u = gt; u < nunits; u += NGEN * 32) {
+        const int kk8 = u & 3, qd = u >> 2;
+        uint32_t pk[4][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) pk[c][w] = 0u;
+        if (4 * qd < P.lvalid) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int64_t krow = kc * OBK + kk8 * 8 + e;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            if (krow < P.K) OmegaGen<float>::quad(P.seed, (uint32_t)krow, (uint32_t)qd, z);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              // z is bf16-exact: its upper 16 bits are the bf16 encoding
+              const uint32_t b = (4 * qd + c < P.lvalid) ? (__float_as_uint(z[c]) >> 16) : 0u;
+              pk[c][e >> 1] |= b << (16 * (e & 1));
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t o = sw64_off((uint32_t)(4 * qd + c), (uint32_t)kk8);
+          st_shared_v4(wb + o, pk[c][0], pk[c][1], pk[c][2], pk[c][3]);
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&wready[bs]);
+      if (++kc == P.kiters) kc = 0;
+      if (++bs == B_ST) {
+        bs = 0;
+        bph ^= 1u;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+cudaError_t launch_tc_omega(const TcGemm& g, cudaStream_t s) {
+  if (!tc_supported(g.L) || g.form != 0 || !g.omega) return cudaErrorInvalidValue;
+  int64_t tiles, kiters, total, G;
+  int maxseg;
+  sk_plan(g.rows, g.K, OUNIT, OBK, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);
+  TcParams P;
+  P.rows = g.rows;
+  P.K = g.K;
+  P.bm = OUNIT;
+  P.L = g.L;
+  P.lvalid = g.lvalid;
+  P.seed = g.seed;
+  P.tiles = tiles;
+  P.kiters = kiters;
+  P.total = total;
+  P.maxseg = maxseg;
+  P.part = g.part;
+  P.out = g.out;
+  P.ldo = g.ldo;
+  P.ncols = g.ncols;
+  P.out_hi = (__nv_bfloat16*)g.out_hi;
+  P.out_lo = (__nv_bfloat16*)g.out_lo;
+  P.ldt = g.ldt;
+  P.skip = g.skip;
+  P.d_info = g.d_info;
+  CUtensorMap ma;
+  memset(&ma, 0, sizeof(ma));
+  if (!encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, (uint64_t)g.a_cols_total,
+                 (uint64_t)g.a_rows_total, (uint64_t)g.lda, OBK, OUNIT,
+                 CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorInvalidValue;
+  const size_t smem = omega_smem(g.L);
+  cudaError_t e = cudaFuncSetAttribute(tc_omega_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tr = trace_begin(RSVD_TRACE_A_OMEGA, s);
+  tc_omega_kernel<<<(unsigned)G, OTHREADS, smem, s>>>(ma, P);
+  count_launch();
+  trace_end(tr, s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_tc_reduce(P, (int)G, s);
+}
+
+}  // namespace rsvd

@@ -38,8 +38,11 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_ptx.cuh"
 
 namespace rsvd {
+
+using namespace tc;
 
 namespace {
 constexpr int BM = 128;             // output rows per tile (MMA M)
@@ -50,7 +53,6 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TMEM_A0 = 256;   // first TMEM column of the A stages
 constexpr int NCONV = 4;            // converter / epilogue warps (4..7)
 constexpr int NGEN = 8;             // Omega generator warps (8..15)
-constexpr long long WAIT_LIMIT = 2000000000LL;   // cycles
 
 __host__ __device__ constexpr int w_tile_bytes(int L) { return L * BK * 2; }
 __host__ __device__ constexpr int stages_for(int nw) { return nw == 3 ? 3 : 4; }
@@ -62,164 +64,6 @@ __host__ __device__ constexpr int stage_bytes(int L, int nw) {
 }
 }  // namespace
 
-struct TcParams {
-  int64_t rows, K;
-  int L, lvalid;
-  uint64_t seed;
-  int64_t tiles, kiters, total;
-  int maxseg;
-  float* part;
-  // final outputs: tiles covered by one CTA are written by its epilogue,
-  // tiles split between CTAs by tc_reduce_kernel
-  float* out;
-  int64_t ldo;
-  int ncols;
-  __nv_bfloat16* out_hi;
-  __nv_bfloat16* out_lo;
-  int64_t ldt;
-  const int* skip;
-  int* d_info;
-};
-
-// ------------------------------- PTX helpers --------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false when the CTA aborted or the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* d_info) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_LIMIT) {
-      *abort_flag = 1;
-      set_info(d_info, RSVD_ERR_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, "
-      "%10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-      "r"(v[15])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-// D[tmem] (+)= A[tmem] * B[smem desc], kind::f16 (bf16 inputs, fp32 accumulate).
-__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
-                                       uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups of
-// 512 bytes (SBO), version 1 (bit 46), layout code 4 in bits 61-63.
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512u >> 4) << 32;        // stride byte offset
-  d |= (uint64_t)1u << 46;                 // descriptor version
-  d |= (uint64_t)4u << 61;                 // SWIZZLE_64B
-  return d;
-}
-// Instruction descriptor: D f32, A bf16, B bf16, both K-major, N and M.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_elem), "f"(lo_elem));
-  return r;
-}
-
-// 32 fp32 values of one A row -> 16 hi words and 16 lo words (2 bf16 each).
-__device__ __forceinline__ void split_row(const float (&x)[32], uint32_t (&hi)[16],
-                                          uint32_t (&lo)[16]) {
-#pragma unroll
-  for (int e = 0; e < 16; ++e) {
-    const float a = x[2 * e], b = x[2 * e + 1];
-    const uint32_t h = pack_bf16x2(a, b);
-    const float ha = __uint_as_float(h << 16), hb = __uint_as_float(h & 0xFFFF0000u);
-    hi[e] = h;
-    lo[e] = pack_bf16x2(a - ha, b - hb);
-  }
-}
 
 // Stream-K bounds of CTA b.
 __device__ __forceinline__ int64_t sk_start(int64_t b, int64_t total, int64_t G) {
@@ -573,28 +417,28 @@ __global__ void tc_reduce_kernel(TcParams P, int G) {
   for (int i = tid; i < nctr; i += 256) {
     const int64_t c = blo + i;
     const int64_t tile0 = ((c * P.total) / G) / P.kiters;
-    s_base[i] = (c * P.maxseg + (t - tile0)) * (int64_t)BM * L;
+    s_base[i] = (c * P.maxseg + (t - tile0)) * (int64_t)P.bm * L;
   }
   __syncthreads();
-  const int rg = blockIdx.x % (BM / 32), jg = blockIdx.x / (BM / 32);
+  const int rg = blockIdx.x % (P.bm / 32), jg = blockIdx.x / (P.bm / 32);
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   for (int jj = ty; jj < 32; jj += 8) {
     const int j = jg * 32 + jj;
     float sum = 0.f;
     if (j < L)
-      for (int i = 0; i < nctr; ++i) sum += P.part[s_base[i] + (int64_t)j * BM + rg * 32 + tx];
+      for (int i = 0; i < nctr; ++i) sum += P.part[s_base[i] + (int64_t)j * P.bm + rg * 32 + tx];
     tile_s[jj][tx] = sum;
   }
   __syncthreads();
   for (int rr = ty; rr < 32; rr += 8) {
-    const int64_t i = t * BM + rg * 32 + rr;
+    const int64_t i = t * P.bm + rg * 32 + rr;
     const int j = jg * 32 + tx;
     if (i < P.rows && j < P.ncols) P.out[i * P.ldo + j] = tile_s[tx][rr];
   }
   if (P.out_hi) {
     for (int jj = ty; jj < 32; jj += 8) {
       const int j = jg * 32 + jj;
-      const int64_t i = t * BM + rg * 32 + tx;
+      const int64_t i = t * P.bm + rg * 32 + tx;
       if (j < L && i < P.rows) {
         const float v = (j < P.ncols) ? tile_s[jj][tx] : 0.0f;
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -625,7 +469,7 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-static bool encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem, const void* base,
+bool encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem, const void* base,
                       uint64_t inner, uint64_t outer, uint64_t pitch_elems, uint32_t box_inner,
                       uint32_t box_outer, CUtensorMapSwizzle sw) {
   EncodeTiledFn fn = get_encode();
@@ -649,10 +493,10 @@ int device_sm_count() {
 
 bool tc_supported(int L) { return L >= 16 && L <= 256 && L % 16 == 0; }
 
-static void sk_plan(int64_t rows, int64_t K, int G_hint, int64_t* tiles, int64_t* kiters,
-                    int64_t* total, int64_t* G, int* maxseg) {
-  *tiles = ceil_div(rows, BM);
-  *kiters = ceil_div(K, BK);
+void sk_plan(int64_t rows, int64_t K, int bm, int bk, int G_hint, int64_t* tiles, int64_t* kiters,
+             int64_t* total, int64_t* G, int* maxseg) {
+  *tiles = ceil_div(rows, bm);
+  *kiters = ceil_div(K, bk);
   *total = (*tiles) * (*kiters);
   int64_t g = G_hint;
   if (g > *total) g = *total;
@@ -668,11 +512,28 @@ static void sk_plan(int64_t rows, int64_t K, int G_hint, int64_t* tiles, int64_t
   *maxseg = ms;
 }
 
+// Partial-tile buffer of one GEMM: the larger of the one-tile (128-row) plan
+// and the two-tile (256-row) plan of the Omega kernel.
 size_t tc_part_bytes(int64_t rows, int64_t K, int L) {
-  int64_t tiles, kiters, total, G;
-  int maxseg;
-  sk_plan(rows, K, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);
-  return (size_t)G * maxseg * BM * L * sizeof(float);
+  size_t best = 0;
+  for (int bm = 128; bm <= 256; bm *= 2) {
+    int64_t tiles, kiters, total, G;
+    int maxseg;
+    sk_plan(rows, K, bm, BK, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);
+    const size_t b = (size_t)G * maxseg * bm * L * sizeof(float);
+    if (b > best) best = b;
+  }
+  return best;
+}
+
+cudaError_t launch_tc_reduce(const TcParams& P, int G, cudaStream_t s) {
+  if (G <= 1) return cudaSuccess;
+  dim3 rgrid((unsigned)((P.bm / 32) * ceil_div(P.L, 32)), (unsigned)(G - 1));
+  const int tr = trace_begin(RSVD_TRACE_REDUCE, s);
+  tc_reduce_kernel<<<rgrid, dim3(32, 8), 0, s>>>(P, G);
+  count_launch();
+  trace_end(tr, s);
+  return cudaGetLastError();
 }
 
 template <int FORM, int NW>
@@ -696,12 +557,14 @@ static cudaError_t launch_form(const CUtensorMap& ma, const CUtensorMap* mw, con
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   if (!tc_supported(g.L)) return cudaErrorInvalidValue;
   if (g.form == 1 && g.omega) return cudaErrorInvalidValue;
+  if (g.form == 0 && g.omega) return launch_tc_omega(g, s);
   int64_t tiles, kiters, total, G;
   int maxseg;
-  sk_plan(g.rows, g.K, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);
+  sk_plan(g.rows, g.K, BM, BK, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);
   TcParams P;
   P.rows = g.rows;
   P.K = g.K;
+  P.bm = BM;
   P.L = g.L;
   P.lvalid = g.lvalid;
   P.seed = g.seed;
@@ -747,9 +610,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   const size_t smem = (size_t)stages_for(nw) * stage_bytes(g.L, nw) + 1024 /*align*/ +
                       (4 * MAXST + 2) * 8 + 16;
   cudaError_t e;
-  if (g.form == 0 && nw == 1)
-    e = launch_form<0, 1>(ma, mw, P, (int)G, smem, s);
-  else if (g.form == 0 && nw == 2)
+  if (g.form == 0 && nw == 2)
     e = launch_form<0, 2>(ma, mw, P, (int)G, smem, s);
   else if (g.form == 0 && nw == 3)
     e = launch_form<0, 3>(ma, mw, P, (int)G, smem, s);
@@ -761,13 +622,8 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
     return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
   // fixed-order reduction of the tiles split between CTAs
-  if (G > 1) {
-    dim3 rgrid((unsigned)((BM / 32) * ceil_div(g.L, 32)), (unsigned)(G - 1));
-    const int tr = trace_begin(RSVD_TRACE_REDUCE, s);
-    tc_reduce_kernel<<<rgrid, dim3(32, 8), 0, s>>>(P, (int)G);
-    count_launch();
-    trace_end(tr, s);
-  }
+  e = launch_tc_reduce(P, (int)G, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

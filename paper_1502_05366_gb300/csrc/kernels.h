@@ -176,6 +176,9 @@ struct TcGemm {
 };
 size_t tc_part_bytes(int64_t rows, int64_t K, int L);
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s);
+// Y = A Omega with two M-tiles per CTA sharing each generated Omega stage
+// (k_omega.cu); called by launch_tc_gemm for form 0 with omega set.
+cudaError_t launch_tc_omega(const TcGemm& g, cudaStream_t s);
 bool tc_supported(int L);
 int device_sm_count();
 

@@ -3,8 +3,12 @@
 // Every entry point validates its arguments, carves the caller's workspace
 // with a bump allocator (the same code computes the *_workspace_size values
 // by running without launching), and enqueues kernels on the caller's stream.
-// Nothing is allocated and the host never waits for the device.
+// No device memory is allocated and the host never waits for the device.  The
+// combined SVD + ID/CUR call forks one kernel (the single-CTA Jacobi SVD) onto
+// an auxiliary stream and joins it back with events; that stream and its two
+// events are created once per device on first use.
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -401,8 +405,18 @@ struct Engine {
   // P = M^T Uh, sigma_j = ||P(:, j)||, Vh = P diag(1/sigma), sorted.
   rsvd_status small_svd(int l, const T* M, int64_t ldm, SvdBufs& s, T* Uh, int64_t lduh,
                         double* Sh, T* Vh, int64_t ldvh) {
+    rsvd_status st = small_svd_jacobi(l, M, ldm, s, c.stream);
+    if (st != RSVD_OK) return st;
+    return small_svd_finish(l, M, ldm, s, Uh, lduh, Sh, Vh, ldvh);
+  }
+  // The Jacobi sweeps alone (one CTA), on stream js.
+  rsvd_status small_svd_jacobi(int l, const T* M, int64_t ldm, SvdBufs& s, cudaStream_t js) {
     LK(launch_jacobi<T>(l, M, ldm, s.Uj, l, s.Sj, nullptr, 0, s.jac_scratch, o.max_sweeps,
-                        c.d_info, c.stream));
+                        c.d_info, js));
+    return RSVD_OK;
+  }
+  rsvd_status small_svd_finish(int l, const T* M, int64_t ldm, SvdBufs& s, T* Uh, int64_t lduh,
+                               double* Sh, T* Vh, int64_t ldvh) {
     int ns;
     int64_t kc;
     tn_split(l, l, l, sms, &ns, &kc);
@@ -415,12 +429,23 @@ struct Engine {
   // From QB: U = Q Vh(:, :k), V = Qh Uh(:, :k), S = Sh(:k), signs fixed.
   rsvd_status svd_from_qb(QBBufs& b, SvdBufs& s, int64_t m, int64_t n, int k, int l, T* U,
                           int64_t ldu, double* S, T* V, int64_t ldv) {
-    const int L = padL(l);
-    // [Qh, Rh] = qr(Bt): Qh into Ztmp, Rh = Racc
-    rsvd_status st = orth(n, l, L, b.Z, b.Ztmp, &b.zs, b.ob, b.part, b.slabs, true);
+    rsvd_status st = svd_prep(b, s, n, l);
     if (st != RSVD_OK) return st;
+    st = small_svd_jacobi(l, b.ob.Racc, padL(l), s, c.stream);
+    if (st != RSVD_OK) return st;
+    return svd_finish(b, s, m, n, k, l, U, ldu, S, V, ldv);
+  }
+  // [Qh, Rh] = qr(Bt): Qh into Ztmp, Rh = Racc (overwrites Bt).
+  rsvd_status svd_prep(QBBufs& b, SvdBufs& s, int64_t n, int l) {
+    (void)s;
+    return orth(n, l, padL(l), b.Z, b.Ztmp, &b.zs, b.ob, b.part, b.slabs, true);
+  }
+  // After the Jacobi sweeps on Rh: its right vectors and sigma, then the lifts.
+  rsvd_status svd_finish(QBBufs& b, SvdBufs& s, int64_t m, int64_t n, int k, int l, T* U,
+                         int64_t ldu, double* S, T* V, int64_t ldv) {
+    const int L = padL(l);
     T* Qh = b.Ztmp;
-    st = small_svd(l, b.ob.Racc, L, s, s.Uh, L, s.Sh, s.Vh, L);
+    rsvd_status st = small_svd_finish(l, b.ob.Racc, L, s, s.Uh, L, s.Sh, s.Vh, L);
     if (st != RSVD_OK) return st;
     LK(launch_gemm_nn<T>(m, k, l, b.Y, L, s.Vh, L, U, ldu, 0, k, c.stream));   // U = Q Vh
     LK(launch_gemm_nn<T>(n, k, l, Qh, L, s.Uh, L, V, ldv, 0, k, c.stream));    // V = Qh Uh
@@ -605,6 +630,38 @@ static void reset_info(Ctx& c) {
 
 enum Want { W_Q = 1, W_SVD = 2, W_ID = 4, W_CUR = 8 };
 
+// Auxiliary stream and fork/join events of one device (created on first use,
+// kept for the life of the process).  The host-side enqueue of a forked call
+// holds the device's mutex so that concurrent callers do not interleave their
+// records of the shared events.
+struct SideStream {
+  std::mutex mu;
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static SideStream* side_stream() {
+  static SideStream g_side[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  SideStream* ss = &g_side[dev];
+  std::lock_guard<std::mutex> lk(ss->mu);
+  if (!ss->s) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+      if (a) cudaEventDestroy(a);
+      cudaStreamDestroy(st);
+      return nullptr;
+    }
+    ss->fork = a;
+    ss->join = b;
+    ss->s = st;
+  }
+  return ss;
+}
+
 template <typename T>
 static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n, int k, int p,
                            int q, uint64_t seed, const T* A, int64_t lda, int want, T* Qo,
@@ -630,20 +687,48 @@ static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n,
     if (Qo) LK(launch_copy2d<T, T>(m, l, qbb.Y, L, Qo, ldq, c.stream));
     if (Bto) LK(launch_copy2d<T, T>(n, l, qbb.Z, L, Bto, ldbt, c.stream));
   }
-  if (want & (W_ID | W_CUR)) {
+  const bool idcur = (want & (W_ID | W_CUR)) != 0;
+  if (idcur) {
     // B = Bt^T (l x n, row-major FP64), taken before the SVD reuses Bt's buffer
     LK(launch_transpose<T, double>(n, l, qbb.Z, L, idb.W, n, c.stream));
+  }
+  // With the ID/CUR requested too, the single-CTA Jacobi sweeps of the SVD run
+  // on the auxiliary stream, beside the CPQR and solves (which leave one SM
+  // free); the SVD is finished on the caller's stream after the join.  The
+  // two branches share no buffer: the Jacobi reads Rh and writes the SVD
+  // buffers only.
+  SideStream* ss = nullptr;
+  std::unique_lock<std::mutex> side_lock;
+  if (want & W_SVD) {
+    st = e.svd_prep(qbb, sb, n, l);
+    if (st != RSVD_OK) return st;
+    if (idcur) {
+      ss = side_stream();
+      if (!ss) return RSVD_ERR_CUDA;
+      side_lock = std::unique_lock<std::mutex>(ss->mu);
+      LK(cudaEventRecord(ss->fork, c.stream));
+      LK(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+      st = e.small_svd_jacobi(l, qbb.ob.Racc, L, sb, ss->s);
+      if (st != RSVD_OK) return st;
+      LK(cudaEventRecord(ss->join, ss->s));
+    } else {
+      st = e.small_svd_jacobi(l, qbb.ob.Racc, L, sb, c.stream);
+      if (st != RSVD_OK) return st;
+    }
+  }
+  if (idcur) {
     st = e.id_core(idb, l, n, k, nullptr);
     if (st != RSVD_OK) return st;
     if (J) LK(launch_copy_i32(n, idb.J, J, c.stream));
     if (Tout) LK(launch_transpose<T, T>(n - k, k, idb.Tt, k, Tout, ldt, c.stream));
   }
-  if (want & W_SVD) {
-    st = e.svd_from_qb(qbb, sb, m, n, k, l, U, ldu, S, V, ldv);
-    if (st != RSVD_OK) return st;
-  }
   if (want & W_CUR) {
     st = e.cur_from_id(cb, idb, m, n, k, A, lda, Jc, Ir, Ucur, lducur, nullptr);
+    if (st != RSVD_OK) return st;
+  }
+  if (want & W_SVD) {
+    if (ss) LK(cudaStreamWaitEvent(c.stream, ss->join, 0));
+    st = e.svd_finish(qbb, sb, m, n, k, l, U, ldu, S, V, ldv);
     if (st != RSVD_OK) return st;
   }
   return RSVD_OK;
