@@ -54,6 +54,90 @@ def a_pass_bytes(m, n, elem=4):
     return float(m) * n * elem
 
 
+# Algorithmic work of one launch of each kernel class at the bench workload:
+# HBM bytes for the passes over A (one read of the m x n fp32 matrix), FP64
+# flops for the pivoted QR and the triangular solves.
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_SM = 4   # 2 DFMA per clock per SM (1.25 TFLOP/s at 2070 MHz, 152 SMs)
+
+
+def cpqr_flops(r, n, k):
+    """Householder k-step CPQR of an r x n matrix: per step j the dot products and
+    the rank-1 update of the (r - j) x (n - j - 1) trailing block, 2 flops each."""
+    return float(sum(4.0 * (r - j) * (n - j - 1) for j in range(k)))
+
+
+def solve_flops(k, ncols):
+    """Upper-triangular solve with k x k factor for ncols right-hand sides."""
+    return float(k) * k * ncols
+
+
+def load_traffic():
+    """dram bytes per launch measured by ncu, from profiles/traffic.txt
+    (lines: class workload bytes_per_launch)."""
+    out = {}
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if os.path.exists(p):
+        with open(p) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 3 and not line.startswith("#"):
+                    out[(parts[0], parts[1])] = float(parts[2])
+    return out
+
+
+def class_roofline(cls, trace, cfg, peaks, peak_kind, sm_mhz):
+    ms_total, launches = trace[cls]
+    if launches <= 0 or ms_total <= 0:
+        return None
+    avg_ms = ms_total / launches
+    m, n, k, p = cfg["m"], cfg["n"], cfg["k"], cfg["p"]
+    l = k + p
+    traffic = load_traffic().get((cls, cfg["name"]))
+    base = {"kernel_class": cls, "avg_launch_ms": avg_ms, "launches": launches,
+            "traffic": traffic}
+    if cls in ("a_omega", "a_w", "at_w"):
+        achieved = a_pass_bytes(m, n) / (avg_ms * 1e-3) / 1e9
+        base.update({"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "peak_source": peak_kind + " STREAM-style copy",
+                     "work_per_launch": "m n 4 bytes (one read of A)"})
+        return base
+    mhz = sm_mhz or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = SM_COUNT * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+    # two launches per step in both classes; flops averaged over the pair
+    if cls == "cpqr":
+        flops = cpqr_flops(l, n, k) + cpqr_flops(k, m, k)    # ID of B, row ID of C^T
+    elif cls == "solve":
+        flops = solve_flops(k, n - k) + solve_flops(k, k)      # T = S11^-1 S12, U_cur
+    else:
+        return dict(base, bound=None, note="no work model for this class")
+    achieved = (flops / 2.0) / (avg_ms * 1e-3) / 1e12
+    base.update({"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                 "frac": achieved / fp64_peak,
+                 "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x %.0f MHz (measured SM clock)" % mhz,
+                 "work_per_launch": "FP64 flops of the launch (both launches averaged)"})
+    return base
+
+
+def sketch_roofline(trace, cfg, peaks, peak_kind):
+    """The 2q+2 passes over A (a1-a7) against HBM: one read of A per pass."""
+    m, n, q = cfg["m"], cfg["n"], cfg["q"]
+    cls = [c for c in ("a_omega", "a_w", "at_w") if c in trace]
+    ms = sum(trace[c][0] for c in cls)
+    nl = sum(trace[c][1] for c in cls)
+    if nl <= 0 or ms <= 0:
+        return None
+    achieved = nl * a_pass_bytes(m, n) / (ms * 1e-3) / 1e9
+    t = load_traffic()
+    return {"kernels": "tc_omega_kernel (A Omega), tc_gemm_kernel (A W, A^T W)",
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "passes_timed": nl,
+            "per_class_ms": {c: trace[c][0] / trace[c][1] for c in cls},
+            "traffic": {c: t.get((c, cfg["name"])) for c in cls},
+            "peak_source": peak_kind + " STREAM-style copy"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -268,20 +352,15 @@ def main():
 
     # ---------------- roofline of the dominant kernel class ----------------
     peaks, peak_kind = load_peaks()
-    apass = {c: trace[c] for c in ("a_omega", "a_w", "at_w")}
+    sm_mhz = None
+    if clk and clk.get("sm_mhz"):
+        sm_mhz = float(clk["sm_mhz"])
     dom = max(trace, key=lambda c: trace[c][0])
-    roof = None
-    if dom in apass and trace[dom][1] > 0:
-        avg_ms = trace[dom][0] / trace[dom][1]
-        achieved = a_pass_bytes(m, n) / (avg_ms * 1e-3) / 1e9
-        roof = {"kernel": "tc_gemm_kernel (%s)" % dom, "bound": "hbm",
-                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": peak_kind + " (STREAM-style copy)",
-                "avg_launch_ms": avg_ms, "launches": trace[dom][1]}
+    roof = class_roofline(dom, trace, cfg, peaks, peak_kind, sm_mhz)
+    roof_sketch = sketch_roofline(trace, cfg, peaks, peak_kind)
     breakdown = {c: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                  for c, v in trace.items()}
-    pass_ms = sum(v[0] for c, v in trace.items() if c in apass) / args.steps
+    pass_ms = sum(v[0] for c, v in trace.items() if c in ("a_omega", "a_w", "at_w")) / args.steps
     qb_flops = 2.0 * m * n * (k + p) * (2 * q + 2)
 
     # ---------------- end to end: host A in, host outputs out ----------------
@@ -326,6 +405,7 @@ def main():
                           "a_pass_tflops": qb_flops / (pass_ms * 1e-3) / 1e12 if pass_ms else None,
                           "a_passes_per_step": 2 * q + 2},
             "roofline": roof,
+            "roofline_sketch": roof_sketch,
             "kernels": breakdown,
             "clocks": clk,
             "e2e": e2e,

@@ -239,6 +239,17 @@ rsvd_status rsvd_cpqr_id(int r, int64_t n, int k, const double* M, int64_t ldm,
                          int32_t* J, double* T, int64_t ldt, double* gaps, void* work,
                          size_t work_bytes, int* d_info, void* stream);
 
+size_t rsvd_cpqr_f32_workspace_size(int r, int64_t n, int k);
+/* rsvd_cpqr_id for an FP32 matrix M (r x n floats, ldm >= n), in the
+ * arithmetic of the FP32 rsvd_id / rsvd_cur path: the entries are carried as
+ * double-float pairs (about 48 significant bits; dot products compensated),
+ * residual norms, reflector scalars and the triangular solve in FP64.
+ * Out: J n int32; T k x (n-k) float (ldt >= n-k); gaps as rsvd_cpqr_id.
+ * Errors as rsvd_cpqr_id. */
+rsvd_status rsvd_cpqr_id_f32(int r, int64_t n, int k, const float* M, int64_t ldm,
+                             int32_t* J, float* T, int64_t ldt, double* gaps, void* work,
+                             size_t work_bytes, int* d_info, void* stream);
+
 /* -------------------------------------------------------------------------
  * rsvd_small_svd_noalloc - rsvd_small_svd without a caller workspace.
  * The paper has no counterpart: this is an interface for callers that cannot

@@ -91,6 +91,9 @@ _SIGS = {
     "rsvd_kernel_launch_count": (_c_i64, []),
     "rsvd_cpqr_id": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp, _vp,
                               _c_size, _vp, _vp]),
+    "rsvd_cpqr_f32_workspace_size": (_c_size, [_c_int, _c_i64, _c_int]),
+    "rsvd_cpqr_id_f32": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
+                                  _vp, _c_size, _vp, _vp]),
 }
 
 
@@ -427,23 +430,31 @@ def small_svd(M, opts=None, check=True):
 
 
 def cpqr_id(M, k, check=True):
-    """Column ID of an explicit float64 CUDA matrix M (r x n): (J, T, gaps)."""
+    """Column ID of an explicit CUDA matrix M (r x n): (J, T, gaps).
+
+    float64 M: FP64 arithmetic (rsvd_cpqr_id); float32 M: the double-float
+    arithmetic of the FP32 path (rsvd_cpqr_id_f32), T in float32."""
     torch = _torch()
     _check_matrix(M, "M")
-    if M.dtype != torch.float64:
-        raise TypeError("cpqr_id takes float64")
+    if M.dtype == torch.float64:
+        size_fn, fn, name = lib().rsvd_cpqr_workspace_size, lib().rsvd_cpqr_id, "rsvd_cpqr_id"
+    elif M.dtype == torch.float32:
+        size_fn, fn, name = (lib().rsvd_cpqr_f32_workspace_size, lib().rsvd_cpqr_id_f32,
+                             "rsvd_cpqr_id_f32")
+    else:
+        raise TypeError("cpqr_id takes float64 or float32")
     r, n = M.shape
     J = torch.empty(n, dtype=torch.int32, device=M.device)
-    T = torch.empty(k, max(n - k, 1), dtype=torch.float64, device=M.device)
+    T = torch.empty(k, max(n - k, 1), dtype=M.dtype, device=M.device)
     gaps = torch.empty(k, dtype=torch.float64, device=M.device)
-    ws = lib().rsvd_cpqr_workspace_size(r, n, k)
+    ws = size_fn(r, n, k)
     if ws == 0:
-        raise RsvdError(1, "rsvd_cpqr_workspace_size")
+        raise RsvdError(1, name.replace("_id", "") + "_workspace_size")
     W = _work(ws, M.device)
     info = _info(M.device)
-    st = lib().rsvd_cpqr_id(r, n, k, _ptr(M), M.stride(0), _ptr(J), _ptr(T), T.stride(0),
-                            _ptr(gaps), _ptr(W), W.numel(), _ptr(info), _stream())
-    _raise(st, "rsvd_cpqr_id")
+    st = fn(r, n, k, _ptr(M), M.stride(0), _ptr(J), _ptr(T), T.stride(0), _ptr(gaps), _ptr(W),
+            W.numel(), _ptr(info), _stream())
+    _raise(st, name)
     if check:
-        check_info(info, "rsvd_cpqr_id")
+        check_info(info, name)
     return J, T[:, : n - k], gaps

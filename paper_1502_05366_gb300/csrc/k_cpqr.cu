@@ -79,9 +79,10 @@ __device__ __forceinline__ Top2 merge_top2(Top2 x, Top2 y) {
   return r;
 }
 
-__device__ Top2 block_top2(Top2 v) {
-  __shared__ double sb1[PT / 32], sb2[PT / 32];
-  __shared__ int64_t si1[PT / 32];
+template <int NT>
+__device__ Top2 block_top2_n(Top2 v) {
+  __shared__ double sb1[NT / 32], sb2[NT / 32];
+  __shared__ int64_t si1[NT / 32];
   __shared__ Top2 s_res;
   for (int o = 16; o > 0; o >>= 1) {
     Top2 w;
@@ -99,7 +100,7 @@ __device__ Top2 block_top2(Top2 v) {
   __syncthreads();
   if (threadIdx.x == 0) {
     Top2 r{sb1[0], si1[0], sb2[0]};
-    for (int w = 1; w < PT / 32; ++w) r = merge_top2(r, Top2{sb1[w], si1[w], sb2[w]});
+    for (int w = 1; w < NT / 32; ++w) r = merge_top2(r, Top2{sb1[w], si1[w], sb2[w]});
     s_res = r;
   }
   __syncthreads();
@@ -107,6 +108,9 @@ __device__ Top2 block_top2(Top2 v) {
   __syncthreads();
   return r;
 }
+
+
+__device__ __forceinline__ Top2 block_top2(Top2 v) { return block_top2_n<PT>(v); }
 
 // W is the r x n sketch in FP64, ROW-major (element (i, c) at W[i*n + c]), so a
 // warp's 32 threads, one column each, touch 32 consecutive doubles of a row.
@@ -306,6 +310,426 @@ cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
                                   dyn, s);
   trace_end(tr, s);
   return e;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float variant (sketches of FP32 data).
+//
+// GB300 issues FP64 fused multiply-adds at 2 per clock per SM, 1/64 of the
+// FP32 rate, so the bulk arithmetic of the pivoted QR (dot product and rank-1
+// update on every active entry, 4 flops per entry per step) runs in
+// double-float: every entry of W is the unevaluated sum hi + lo of two floats
+// (about 48 significant bits), held in two planes Wh, Wl.  The dot products
+// use the compensated scheme Dot2 (Ogita, Rump & Oishi 2005: TwoProduct by
+// fma, TwoSum, errors summed in a second float), the updates TwoProduct /
+// TwoSum with a final renormalisation (Dekker 1971).  Per-column and per-step
+// scalars (residual norms, tau, beta, pivots, gaps) stay FP64.  With a
+// relative error near 2^-47 per operation the pivot choices are those of an
+// FP64 computation unless two residual norms agree to about 1e-13.
+// The rounding primitives use the _rn intrinsics so that no product is fused
+// into a neighbouring sum.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// |a| >= |b| or a == 0
+__device__ __forceinline__ void df_fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ double df_to_d(float h, float l) { return (double)h + (double)l; }
+// Warp sum of double-float partial sums (s, e): TwoSum on the leading parts,
+// errors accumulated; every lane ends with the total.
+__device__ __forceinline__ void df_warp_sum(float& s, float& e) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, s, o);
+    const float oe = __shfl_xor_sync(0xffffffffu, e, o);
+    float t;
+    df_two_sum(s, os, s, t);
+    e = __fadd_rn(e, __fadd_rn(oe, t));
+  }
+}
+__device__ __forceinline__ void d_to_df(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+
+// Residual norms as double-float pairs with a total order (hi, then lo); a
+// pivoted column has hi = -1.  All comparisons and norm updates of the
+// double-float kernel run on the FP32 pipe.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ bool df_gt(DF x, DF y) { return x.h > y.h || (x.h == y.h && x.l > y.l); }
+__device__ __forceinline__ bool df_eq(DF x, DF y) { return x.h == y.h && x.l == y.l; }
+struct Top2F {
+  DF b1;
+  int64_t i1;
+  DF b2;
+};
+__device__ __forceinline__ Top2F merge_top2f(Top2F x, Top2F y) {
+  const bool xfirst = df_gt(x.b1, y.b1) || (df_eq(x.b1, y.b1) && x.i1 < y.i1);
+  const Top2F& f = xfirst ? x : y;
+  const Top2F& o = xfirst ? y : x;
+  Top2F r;
+  r.b1 = f.b1;
+  r.i1 = f.i1;
+  r.b2 = df_gt(f.b2, o.b1) ? f.b2 : o.b1;
+  return r;
+}
+template <int NT>
+__device__ Top2F block_top2f(Top2F v) {
+  __shared__ float sb[NT / 32][4];
+  __shared__ int64_t si1[NT / 32];
+  __shared__ Top2F s_res;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Top2F w;
+    w.b1.h = __shfl_xor_sync(0xffffffffu, v.b1.h, o);
+    w.b1.l = __shfl_xor_sync(0xffffffffu, v.b1.l, o);
+    w.i1 = __shfl_xor_sync(0xffffffffu, v.i1, o);
+    w.b2.h = __shfl_xor_sync(0xffffffffu, v.b2.h, o);
+    w.b2.l = __shfl_xor_sync(0xffffffffu, v.b2.l, o);
+    v = merge_top2f(v, w);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sb[warp][0] = v.b1.h;
+    sb[warp][1] = v.b1.l;
+    sb[warp][2] = v.b2.h;
+    sb[warp][3] = v.b2.l;
+    si1[warp] = v.i1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Top2F r{{sb[0][0], sb[0][1]}, si1[0], {sb[0][2], sb[0][3]}};
+    for (int w = 1; w < NT / 32; ++w)
+      r = merge_top2f(r, Top2F{{sb[w][0], sb[w][1]}, si1[w], {sb[w][2], sb[w][3]}});
+    s_res = r;
+  }
+  __syncthreads();
+  Top2F r = s_res;
+  __syncthreads();
+  return r;
+}
+// Double-float square x^2 of a pair.
+__device__ __forceinline__ void df_sqr(float xh, float xl, float& ph, float& pe) {
+  ph = __fmul_rn(xh, xh);
+  pe = __fmaf_rn(xh, xh, -ph);
+  pe = __fmaf_rn(2.0f * xh, xl, pe);
+}
+// Dot2 accumulation of x^2 into (s, e).
+__device__ __forceinline__ void df_acc_sqr(float xh, float xl, float& s, float& e) {
+  float ph, pe, t;
+  df_sqr(xh, xl, ph, pe);
+  df_two_sum(s, ph, s, t);
+  e = __fadd_rn(e, __fadd_rn(t, pe));
+}
+
+// W is COLUMN-major here (element (i, c) in Wh[c*r + i], Wl[c*r + i]), so one
+// warp owns a column per iteration: lane l holds rows j + l + 32 t
+// (t < RPL) of it in registers from the load through the dot product, the
+// warp-shuffle reduction and the update to the store, with no block-wide
+// synchronisation inside the column loop.  Warp 0 builds the Householder
+// vector of the pivot column once per CTA and step (shared memory); its
+// scalars (norm, beta, tau) are the only FP64 arithmetic of a step.
+// The residual norms live in a.nrm as double-float pairs: float2 nrm2[c] =
+// (hi, lo) of nu_c^2 (hi = -1 once pivoted), float nref[c] (the value at the
+// last exact computation) at nrm2 + n.
+template <int RPL, int NT>
+__global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float* svh = (float*)dsm;        // Householder vector, hi parts (r entries)
+  float* svl = svh + a.r;          // lo parts
+  __shared__ double s_beta;
+  __shared__ float s_th, s_tl;     // tau as a double-float pair
+  __shared__ int s_zero;           // zero pivot column: nothing to reflect
+  const int r = a.r;
+  const int64_t n = a.n;
+  const int G = gridDim.x;
+  const int64_t per = ceil_div(n, G);
+  const int64_t c0 = (int64_t)blockIdx.x * per;
+  const int64_t c1 = min(n, c0 + per);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NWARP = NT / 32;
+  float* Wh = reinterpret_cast<float*>(a.W);
+  float* Wl = Wh + (int64_t)r * n;
+  float2* __restrict__ nrm2 = reinterpret_cast<float2*>(a.nrm);
+  float* __restrict__ nref = reinterpret_cast<float*>(nrm2 + n);
+  float4* __restrict__ pv = reinterpret_cast<float4*>(a.pval);   // (b1h, b1l, b2h, b2l)
+  double* __restrict__ diagR = a.diagR;
+  const float tol3z = 1.4901161193847656e-08f;   // sqrt(eps_fp64), as in the FP64 kernel
+
+  // exact initial squared norms, one warp per column
+  for (int64_t c = c0 + warp; c < c1; c += NWARP) {
+    float sh = 0.f, se = 0.f;
+    for (int i = lane; i < r; i += 32) df_acc_sqr(Wh[c * r + i], Wl[c * r + i], sh, se);
+    df_warp_sum(sh, se);
+    if (lane == 0) {
+      float h, l;
+      df_fast_two_sum(sh, se, h, l);
+      nrm2[c] = make_float2(h, l);
+      nref[c] = h;
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int64_t c = tid; c < n; c += NT) {
+      a.J[c] = (int32_t)c;
+      a.where[c] = c;
+    }
+  __syncthreads();
+
+  const DF none{-1.f, 0.f};
+  for (int j = 0; j < a.k; ++j) {
+    Top2F loc{none, 0x7fffffffffffffffLL, none};
+    for (int64_t c = c0 + tid; c < c1; c += NT) {
+      const float2 x = nrm2[c];
+      if (x.x >= 0.f) loc = merge_top2f(loc, Top2F{DF{x.x, x.y}, c, none});
+    }
+    loc = block_top2f<NT>(loc);
+    const int slot = j & 1;
+    if (tid == 0) {
+      pv[(size_t)slot * G + blockIdx.x] = make_float4(loc.b1.h, loc.b1.l, loc.b2.h, loc.b2.l);
+      a.pidx[(size_t)slot * G + blockIdx.x] = loc.i1;
+    }
+    if (!grid_barrier(a.bar, (unsigned)(j + 1) * (unsigned)G, a.d_info)) return;
+    Top2F g{none, 0x7fffffffffffffffLL, none};
+    for (int b = tid; b < G; b += NT) {
+      const float4 q = __ldcg(pv + (size_t)slot * G + b);
+      g = merge_top2f(g, Top2F{DF{q.x, q.y},
+                               __ldcg(reinterpret_cast<const long long*>(a.pidx) +
+                                      (size_t)slot * G + b),
+                               DF{q.z, q.w}});
+    }
+    g = block_top2f<NT>(g);
+    const int64_t p = g.i1;
+    if (p < 0 || p >= n) {
+      set_info(a.d_info, RSVD_ERR_NUMERIC);
+      return;
+    }
+    const int len = r - j;
+    // ---- warp 0: Householder vector of the pivot column (rows j..r-1) ----
+    if (warp == 0) {
+      float ss = 0.f, se = 0.f;
+      for (int i = lane; i < len; i += 32) {
+        const float xh = __ldcg(Wh + p * r + j + i), xl = __ldcg(Wl + p * r + j + i);
+        svh[i] = xh;
+        svl[i] = xl;
+        df_acc_sqr(xh, xl, ss, se);
+      }
+      df_warp_sum(ss, se);
+      if (lane == 0) {
+        const double nx2 = (double)ss + (double)se;
+        const double nx = sqrt(nx2);
+        const double x0 = df_to_d(svh[0], svl[0]);
+        const double beta = (x0 >= 0.0) ? -nx : nx;
+        s_beta = beta;
+        if (nx > 0.0) {
+          const double v0 = x0 - beta;
+          float h0, l0;
+          d_to_df(v0, h0, l0);
+          svh[0] = h0;
+          svl[0] = l0;
+          float th, tl;
+          d_to_df(2.0 / (nx2 - x0 * x0 + v0 * v0), th, tl);
+          s_th = th;
+          s_tl = tl;
+          s_zero = 0;
+        } else {
+          s_th = 0.f;
+          s_tl = 0.f;
+          s_zero = 1;
+        }
+      }
+    }
+    __syncthreads();
+    float vh[RPL], vl[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int i = lane + 32 * t;
+      vh[t] = i < len ? svh[i] : 0.f;
+      vl[t] = i < len ? svl[i] : 0.f;
+    }
+    const float tauh = s_th, taul = s_tl;
+    const bool zero = s_zero != 0;
+    const int nt = (len + 31) >> 5;          // row slots in use (warp-uniform)
+    // ---- every warp: dot, update and norm downdate of its columns ----
+    for (int64_t c = c0 + warp; c < c1; c += NWARP) {
+      if (c == p) continue;                                  // warp-uniform
+      const float2 nc = nrm2[c];
+      if (nc.x < 0.f) continue;                              // already pivoted
+      float* colh = Wh + c * r + j;
+      float* coll = Wl + c * r + j;
+      float wh[RPL], wl[RPL];
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int i = lane + 32 * t;
+        wh[t] = (t < nt && i < len) ? colh[i] : 0.f;
+        wl[t] = (t < nt && i < len) ? coll[i] : 0.f;
+      }
+      if (!zero) {
+        float sd = 0.f, ed = 0.f;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          if (t < nt) {
+            const float ph = __fmul_rn(vh[t], wh[t]);
+            float pe = __fmaf_rn(vh[t], wh[t], -ph);
+            pe = __fmaf_rn(vh[t], wl[t], pe);
+            pe = __fmaf_rn(vl[t], wh[t], pe);
+            float e;
+            df_two_sum(sd, ph, sd, e);
+            ed = __fadd_rn(ed, __fadd_rn(e, pe));
+          }
+        }
+        df_warp_sum(sd, ed);
+        float dh, dl;
+        df_fast_two_sum(sd, ed, dh, dl);
+        // t = tau * (v . w) as a double-float pair
+        const float qh = __fmul_rn(tauh, dh);
+        float qe = __fmaf_rn(tauh, dh, -qh);
+        qe = __fmaf_rn(tauh, dl, qe);
+        qe = __fmaf_rn(taul, dh, qe);
+        float th, tl;
+        df_fast_two_sum(qh, qe, th, tl);
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          if (t < nt) {
+            const float ph = __fmul_rn(th, vh[t]);
+            float pe = __fmaf_rn(th, vh[t], -ph);
+            pe = __fmaf_rn(th, vl[t], pe);
+            pe = __fmaf_rn(tl, vh[t], pe);
+            float sh, se;
+            df_two_sum(wh[t], -ph, sh, se);
+            se = __fadd_rn(se, __fsub_rn(wl[t], pe));
+            df_fast_two_sum(sh, se, wh[t], wl[t]);
+            const int i = lane + 32 * t;
+            if (i < len) {
+              colh[i] = wh[t];
+              coll[i] = wl[t];
+            }
+          }
+        }
+      }
+      // residual norm downdate nu^2 - W(j, c)^2 (lane 0 holds row j), in
+      // double-float; exact recompute on cancellation (LAPACK safeguard)
+      float nh = 0.f, nl = 0.f;
+      int recompute = 0;
+      if (lane == 0) {
+        float ph, pe, sh, se;
+        df_sqr(wh[0], wl[0], ph, pe);
+        df_two_sum(nc.x, -ph, sh, se);
+        se = __fadd_rn(se, __fsub_rn(nc.y, pe));
+        df_fast_two_sum(sh, se, nh, nl);
+        recompute = (!(nh > tol3z * nref[c]) && j + 1 < r) ? 1 : 0;
+      }
+      recompute = __shfl_sync(0xffffffffu, recompute, 0);
+      if (recompute) {
+        float qs = 0.f, qe = 0.f;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int i = lane + 32 * t;
+          if (t < nt && i >= 1 && i < len) df_acc_sqr(wh[t], wl[t], qs, qe);
+        }
+        df_warp_sum(qs, qe);
+        df_fast_two_sum(qs, qe, nh, nl);
+        if (lane == 0) nref[c] = nh;
+      }
+      if (lane == 0) nrm2[c] = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
+    }
+    if (p >= c0 && p < c1 && tid == 0) nrm2[p] = make_float2(-1.f, 0.f);
+    if (blockIdx.x == 0 && tid == 0) {
+      diagR[j] = s_beta;
+      const int64_t P = a.where[p];
+      const int32_t cj = a.J[j];
+      a.J[P] = cj;
+      a.where[cj] = P;
+      a.J[j] = (int32_t)p;
+      a.where[p] = j;
+      if (a.gaps) {
+        const double n1 = sqrt((double)g.b1.h + (double)g.b1.l);
+        a.gaps[j] = (g.b2.h < 0.f)
+                        ? __longlong_as_double(0x7ff0000000000000LL)
+                        : (n1 > 0.0 ? (n1 - sqrt((double)g.b2.h + (double)g.b2.l)) / n1 : 0.0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int RPL, int NT>
+static cudaError_t launch_cpqr_df_t(const CpqrArgs& a, int sms, cudaStream_t s) {
+  auto kern = cpqr_df_kernel<RPL, NT>;
+  const size_t dyn = (size_t)a.r * 2 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, dyn);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // one SM is left to a single-CTA kernel running beside the CPQR on another
+  // stream (the Jacobi SVD of the combined SVD + ID/CUR call)
+  int64_t G = sms > 1 ? sms - 1 : 1;
+  const int64_t byn = ceil_div(a.n, 8);
+  if (G > byn) G = byn;
+  if (G > 1024) G = 1024;
+  if (G < 1) G = 1;
+  e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  CpqrArgs b = a;
+  void* args[] = {(void*)&b};
+  count_launch();
+  const int tr = trace_begin(RSVD_TRACE_CPQR, s);
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)G), dim3(NT), args, dyn, s);
+  trace_end(tr, s);
+  return e;
+}
+
+cudaError_t launch_cpqr_df(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
+  (void)grid_out;
+  if (a.r > 1024) return cudaErrorInvalidValue;
+  const int sms = device_sm_count();
+  if (a.r <= 256) return launch_cpqr_df_t<8, 1024>(a, sms, s);
+  return launch_cpqr_df_t<32, 256>(a, sms, s);
+}
+
+__global__ void id_extract_df_kernel(int r, int64_t n, int k, const float* __restrict__ Wh,
+                                     const float* __restrict__ Wl,
+                                     const int32_t* __restrict__ J,
+                                     const double* __restrict__ diagR, double* __restrict__ S11,
+                                     double* __restrict__ S12) {
+  const int64_t total = n * (int64_t)k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pos = t / k;
+    const int i = (int)(t - pos * k);
+    const int64_t c = J[pos];
+    const int64_t o = c * r + i;            // column-major planes
+    if (pos < k) {
+      double v;
+      if (i < pos) v = df_to_d(Wh[o], Wl[o]);
+      else if (i == pos) v = diagR[pos];
+      else v = 0.0;
+      S11[pos * k + i] = v;
+    } else {
+      S12[(int64_t)i * (n - k) + (pos - k)] = df_to_d(Wh[o], Wl[o]);
+    }
+  }
+}
+
+cudaError_t launch_id_extract_df(int r, int64_t n, int k, const double* W, const int32_t* J,
+                                 const double* diagR, double* S11, double* S12, cudaStream_t s) {
+  const int64_t total = n * (int64_t)k;
+  if (total <= 0) return cudaSuccess;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 16384) blocks = 16384;
+  const float* Wh = reinterpret_cast<const float*>(W);
+  id_extract_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(r, n, k, Wh, Wh + (int64_t)r * n, J,
+                                                        diagR, S11, S12);
+  count_launch();
+  return cudaGetLastError();
 }
 
 // S11 (k x k, column-major, upper triangular incl. beta on the diagonal) and

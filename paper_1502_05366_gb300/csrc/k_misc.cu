@@ -204,6 +204,30 @@ cudaError_t launch_gather_ct(int64_t m, int k, const T* A, int64_t lda, const in
   return cudaGetLastError();
 }
 
+// Double-float planes of W = C^T (k x m), column-major (column r of C^T is
+// row r of C): Wh[r*k + i] = A[r, J[i]], Wl = 0.
+__global__ void gather_ct_df_kernel(int64_t m, int k, const float* __restrict__ A, int64_t lda,
+                                    const int32_t* __restrict__ J, float* __restrict__ Wh,
+                                    float* __restrict__ Wl) {
+  const int64_t total = m * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / k;
+    const int i = (int)(t - r * k);
+    Wh[t] = A[r * lda + J[i]];
+    Wl[t] = 0.0f;
+  }
+}
+
+cudaError_t launch_gather_ct_df(int64_t m, int k, const float* A, int64_t lda, const int32_t* J,
+                                double* W, cudaStream_t s) {
+  if (m <= 0 || k <= 0) return cudaSuccess;
+  float* Wh = reinterpret_cast<float*>(W);
+  gather_ct_df_kernel<<<grid1d(m * k), 256, 0, s>>>(m, k, A, lda, J, Wh, Wh + m * k);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void gather_rows_kernel(int k, int64_t n, const T* __restrict__ A, int64_t lda,
                                    const int32_t* __restrict__ I, T* __restrict__ R,

@@ -1,7 +1,7 @@
 // tcgen05 (5th-generation tensor core) GEMMs for the passes over A.
 //
-//   form 0:  Y (rows x L) = A (rows x K) W       sketch Y = A Omega (Fig. 1 step 2),
-//                                                power step Y = A Z, orth apply X R^-1
+//   form 0:  Y (rows x L) = A (rows x K) W       power step Y = A Z, orth apply X R^-1
+//                                                (the sketch Y = A Omega: k_omega.cu)
 //   form 1:  Z (rows x L) = A^T W, A is K x rows  power step Z = A^* Y (Sec. 3.2),
 //                                                QB step Bt = A^* Q (Alg. 5), Gram X^T X
 //
@@ -24,8 +24,6 @@
 //   warp 1      MMA issuer (one thread) and TMEM owner
 //   warps 4-7   converters: fp32 A tile (shared) -> bf16 hi/lo rows -> TMEM
 //               (tcgen05.st), then the epilogue (tcgen05.ld -> partial tile)
-//   warps 8-15  (Omega only) Philox/Box-Muller generators writing the bf16
-//               Omega tile straight into the swizzled K-major shared layout
 // Partial tiles are summed in a fixed order by tc_reduce_kernel, which writes
 // the fp32 result and, on request, the transposed bf16 hi/lo split that the
 // next GEMM consumes.
@@ -52,13 +50,11 @@ constexpr int A_STAGE_BYTES = BM * BK * 4;   // 16 KB fp32
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TMEM_A0 = 256;   // first TMEM column of the A stages
 constexpr int NCONV = 4;            // converter / epilogue warps (4..7)
-constexpr int NGEN = 8;             // Omega generator warps (8..15)
 
 __host__ __device__ constexpr int w_tile_bytes(int L) { return L * BK * 2; }
 __host__ __device__ constexpr int stages_for(int nw) { return nw == 3 ? 3 : 4; }
-// W tiles per stage: Omega 1, stored 2, R^-1 3, Gram 2.  Omega keeps two slots
-// in the layout for simplicity.
-__host__ __device__ constexpr int w_tiles(int nw) { return nw == 1 ? 2 : (nw == 4 ? 2 : nw); }
+// W tiles per stage: stored 2, R^-1 3, Gram 2.
+__host__ __device__ constexpr int w_tiles(int nw) { return nw == 4 ? 2 : nw; }
 __host__ __device__ constexpr int stage_bytes(int L, int nw) {
   return A_STAGE_BYTES + w_tiles(nw) * w_tile_bytes(L);
 }
@@ -71,14 +67,13 @@ __device__ __forceinline__ int64_t sk_start(int64_t b, int64_t total, int64_t G)
 }
 
 template <int FORM, int NW>
-__global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
+__global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                    const __grid_constant__ CUtensorMap mapW0,
                    const __grid_constant__ CUtensorMap mapW1,
                    const __grid_constant__ CUtensorMap mapW2, TcParams P) {
-  constexpr bool OMEGA = (NW == 1);
   constexpr bool GRAM = (NW == 4);
-  constexpr int NWT = OMEGA ? 1 : w_tiles(NW);   // W tiles loaded per stage
+  constexpr int NWT = w_tiles(NW);   // W tiles loaded per stage
   constexpr int STAGES = stages_for(NW);
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
   if (P.skip && *P.skip) return;
@@ -88,9 +83,8 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
   uint64_t* bars = (uint64_t*)(dsm + STAGES * SB);
   uint64_t* full = bars;                  // TMA landed (A [+ W])
   uint64_t* conv = bars + STAGES;         // A stage written to TMEM
-  uint64_t* genb = bars + 2 * STAGES;     // Omega tile written
-  uint64_t* done = bars + 3 * STAGES;     // MMAs of the stage finished
-  uint64_t* acc_full = bars + 4 * STAGES;
+  uint64_t* done = bars + 2 * STAGES;     // MMAs of the stage finished
+  uint64_t* acc_full = bars + 3 * STAGES;
   uint64_t* acc_empty = acc_full + 1;
   uint32_t* tmem_holder = (uint32_t*)(acc_empty + 1);
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
@@ -104,7 +98,6 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], NCONV);
-      mbar_init(&genb[s], NGEN);
       mbar_init(&done[s], 1);
     }
     mbar_init(acc_full, 1);
@@ -135,7 +128,7 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
     if (lane == 0) {
-      const uint32_t bytes = A_STAGE_BYTES + (OMEGA ? 0u : (uint32_t)NWT * (uint32_t)w_tile_bytes(L));
+      const uint32_t bytes = A_STAGE_BYTES + (uint32_t)NWT * (uint32_t)w_tile_bytes(L);
       int64_t last_issued = -1;
       int64_t tile = it0 / P.kiters, kc = it0 - tile * P.kiters;
       int s = 0;
@@ -194,11 +187,7 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
             break;
         }
         if (!mbar_wait(&conv[s], ph, abort_flag, P.d_info)) break;
-        if (OMEGA) {
-          if (!mbar_wait(&genb[s], ph, abort_flag, P.d_info)) break;
-        } else {
-          if (!mbar_wait(&full[s], ph, abort_flag, P.d_info)) break;
-        }
+        if (!mbar_wait(&full[s], ph, abort_flag, P.d_info)) break;
         tc_fence_after();
         const uint32_t wbase = smem_u32(dsm + s * SB + A_STAGE_BYTES);
         const uint32_t a_col = tmem + TMEM_A0 + 32u * (uint32_t)s;
@@ -333,40 +322,6 @@ __global__ void __launch_bounds__(NW == 1 ? 512 : 256, 1)
         kc = 0;
         ++tile;
       }
-      if (++s == STAGES) {
-        s = 0;
-        ph ^= 1u;
-      }
-    }
-  } else if (OMEGA && warp >= 8 && warp < 8 + NGEN) {
-    // ------------------------- Omega generator warps --------------------------
-    const int gt = threadIdx.x - 8 * 32;   // 0 .. 255
-    const int nq = L / 4;
-    int64_t kc = it0 % P.kiters;
-    int s = 0;
-    uint32_t ph = 0;
-    for (int64_t it = it0; it < it1; ++it) {
-      if (!mbar_wait(&done[s], ph ^ 1u, abort_flag, P.d_info)) break;
-      unsigned char* wt = dsm + s * SB + A_STAGE_BYTES;
-      for (int e = gt; e < BK * nq; e += NGEN * 32) {
-        const int kk = e % BK, qd = e / BK;
-        const int64_t krow = kc * BK + kk;
-        float z[4] = {0.f, 0.f, 0.f, 0.f};
-        if (krow < P.K && 4 * qd < P.lvalid)
-          OmegaGen<float>::quad(P.seed, (uint32_t)krow, (uint32_t)qd, z);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int j = 4 * qd + c;
-          const float val = (j < P.lvalid) ? z[c] : 0.0f;
-          const uint32_t off = (uint32_t)j * 64u + ((((uint32_t)kk >> 3) ^ (((uint32_t)j >> 1) & 3u)) << 4) +
-                               ((uint32_t)kk & 7u) * 2u;
-          *reinterpret_cast<__nv_bfloat16*>(wt + off) = __float2bfloat16_rn(val);
-        }
-      }
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&genb[s]);
-      if (++kc == P.kiters) kc = 0;
       if (++s == STAGES) {
         s = 0;
         ph ^= 1u;
@@ -545,10 +500,9 @@ static cudaError_t launch_form(const CUtensorMap& ma, const CUtensorMap* mw, con
   if (e != cudaSuccess) return e;
   // trace classes (include/rsvd.h): 0 A Omega, 1 A W, 2 A^T W, 3 Gram, 4 orth apply
   const int cls = FORM == 1 ? (NW == 4 ? RSVD_TRACE_GRAM : RSVD_TRACE_AT_W)
-                            : (NW == 1 ? RSVD_TRACE_A_OMEGA
-                                       : (NW == 3 ? RSVD_TRACE_APPLY : RSVD_TRACE_A_W));
+                            : (NW == 3 ? RSVD_TRACE_APPLY : RSVD_TRACE_A_W);
   const int tr = trace_begin(cls, s);
-  kern<<<G, NW == 1 ? 512 : 256, smem, s>>>(ma, mw[0], mw[1], mw[2], P);
+  kern<<<G, 256, smem, s>>>(ma, mw[0], mw[1], mw[2], P);
   count_launch();
   trace_end(tr, s);
   return cudaGetLastError();
@@ -595,10 +549,10 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
                    (uint64_t)g.a_rows_total, (uint64_t)g.lda, BM, BK,
                    CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!ok) return cudaErrorInvalidValue;
-  const int nw = g.omega ? 1 : (g.gram ? 4 : g.wterms);
-  if (nw < 1 || nw > 4 || (nw == 1 && !g.omega) || (g.gram && g.wterms != 2))
+  const int nw = g.gram ? 4 : g.wterms;
+  if (nw < 2 || nw > 4 || (g.gram && g.wterms != 2))
     return cudaErrorInvalidValue;
-  const int nwt = g.omega ? 0 : w_tiles(nw);
+  const int nwt = w_tiles(nw);
   const void* wp[3] = {g.Whi, g.Wlo, g.Wlo2};
   for (int t = 0; t < nwt; ++t) {
     if (!wp[t]) return cudaErrorInvalidValue;
@@ -606,7 +560,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
                    (uint64_t)g.L, (uint64_t)g.ldw, BK, (uint32_t)g.L, CU_TENSOR_MAP_SWIZZLE_64B);
     if (!ok) return cudaErrorInvalidValue;
   }
-  for (int t = nwt; t < 3; ++t) mw[t] = (g.omega ? ma : mw[0]);
+  for (int t = nwt; t < 3; ++t) mw[t] = mw[0];
   const size_t smem = (size_t)stages_for(nw) * stage_bytes(g.L, nw) + 1024 /*align*/ +
                       (4 * MAXST + 2) * 8 + 16;
   cudaError_t e;

@@ -62,6 +62,10 @@ cudaError_t launch_sign_fix(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V
 template <typename T>
 cudaError_t launch_gather_ct(int64_t m, int k, const T* A, int64_t lda, const int32_t* J,
                              double* W, cudaStream_t s);
+// Double-float planes (hi = the fp32 value, lo = 0) of the same W, column-
+// major, in the working area W (2 k m floats).
+cudaError_t launch_gather_ct_df(int64_t m, int k, const float* A, int64_t lda, const int32_t* J,
+                                double* W, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gather_rows(int k, int64_t n, const T* A, int64_t lda, const int32_t* I,
                                T* R, int64_t ldr, cudaStream_t s);
@@ -127,9 +131,16 @@ struct CpqrArgs {
   double* diagR;    // k: diagonal of S (the Householder betas)
   unsigned* bar;    // 1 counter, zeroed by the launcher
   int* d_info;
-  int tpc;          // threads per column (set by the launcher)
+  int tpc;          // set by the launcher: threads per column (FP64 kernel) or
+                    // columns per pass (double-float kernel)
 };
 cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s);
+// Double-float arithmetic on the same working area reinterpreted as two float
+// planes, hi then lo, each r x n COLUMN-major (ld r); used for sketches of
+// FP32 data, r <= 1024.
+cudaError_t launch_cpqr_df(const CpqrArgs& a, int* grid_out, cudaStream_t s);
+cudaError_t launch_id_extract_df(int r, int64_t n, int k, const double* W, const int32_t* J,
+                                 const double* diagR, double* S11, double* S12, cudaStream_t s);
 size_t cpqr_scratch_bytes(int64_t n);
 // Largest triangle the many-right-hand-side solve handles (one 32-thread block
 // of kk doubles each in 220 KB of shared memory).

@@ -508,9 +508,17 @@ struct Engine {
     a.bar = d.bar;
     a.d_info = c.d_info;
     int grid = 0;
-    LK(launch_cpqr(a, &grid, c.stream));
+    // FP32 data: double-float arithmetic on the working area as two float planes
+    constexpr bool DF = sizeof(T) == 4;
+    if (DF)
+      LK(launch_cpqr_df(a, &grid, c.stream));
+    else
+      LK(launch_cpqr(a, &grid, c.stream));
     if (!d.Tt) return RSVD_OK;   // pivots only (row ID of the CUR)
-    LK(launch_id_extract(r, n, k, d.W, d.J, d.diagR, d.S11, d.S12, c.stream));
+    if (DF)
+      LK(launch_id_extract_df(r, n, k, d.W, d.J, d.diagR, d.S11, d.S12, c.stream));
+    else
+      LK(launch_id_extract(r, n, k, d.W, d.J, d.diagR, d.S11, d.S12, c.stream));
     // S11 column-major: U(i, t) = S11[t*k + i]; rhs(i, c) = S12[i*(n-k) + c];
     // out Tt(c, i) = Tt[c*k + i]
     LK(launch_upper_solve<double, T>(k, n - k, d.S11, 1, k, d.S12, n - k, 1, d.Tt, 1, k,
@@ -567,7 +575,10 @@ struct Engine {
                           double* rgaps) {
     const int Kp = padL(k);
     // C^T columns (rows of C = A(:, J[:k])) in the CPQR layout
-    LK(launch_gather_ct<T>(m, k, A, lda, idb.J, u.rid.W, c.stream));
+    if (sizeof(T) == 4)
+      LK(launch_gather_ct_df(m, k, (const float*)A, lda, idb.J, u.rid.W, c.stream));
+    else
+      LK(launch_gather_ct<T>(m, k, A, lda, idb.J, u.rid.W, c.stream));
     rsvd_status st = id_core(u.rid, k, m, k, rgaps);
     if (st != RSVD_OK) return st;
     if (Jc) LK(launch_copy_i32(k, idb.J, Jc, c.stream));
@@ -689,8 +700,16 @@ static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n,
   }
   const bool idcur = (want & (W_ID | W_CUR)) != 0;
   if (idcur) {
-    // B = Bt^T (l x n, row-major FP64), taken before the SVD reuses Bt's buffer
-    LK(launch_transpose<T, double>(n, l, qbb.Z, L, idb.W, n, c.stream));
+    // B = Bt^T (l x n), taken before the SVD reuses Bt's buffer: row-major
+    // FP64, or column-major double-float planes (hi = B, lo = 0) for FP32 data
+    if (sizeof(T) == 4) {
+      // column-major planes: column c of B is row c of Bt
+      float* Wh = reinterpret_cast<float*>(idb.W);
+      LK(launch_copy2d<float, float>(n, l, (const float*)qbb.Z, L, Wh, l, c.stream));
+      LK(cudaMemsetAsync(Wh + (int64_t)l * n, 0, sizeof(float) * (size_t)l * n, c.stream));
+    } else {
+      LK(launch_transpose<T, double>(n, l, qbb.Z, L, idb.W, n, c.stream));
+    }
   }
   // With the ID/CUR requested too, the single-CTA Jacobi sweeps of the SVD run
   // on the auxiliary stream, beside the CPQR and solves (which leave one SM
@@ -1007,18 +1026,27 @@ static rsvd_status small_svd_impl(Ctx& c, const Opts& o, int l, const T* M, int6
   return e.small_svd(l, M, ldm, sb, Uh, lduh, Sh, Vh, ldvh);
 }
 
-static rsvd_status cpqr_impl(Ctx& c, int r, int64_t n, int k, const double* M, int64_t ldm,
-                             int32_t* J, double* T, int64_t ldt, double* gaps) {
+// Column ID of an explicit r x n matrix: FP64 arithmetic for double M, the
+// double-float kernel (as on the FP32 path) for float M.
+template <typename T>
+static rsvd_status cpqr_impl(Ctx& c, int r, int64_t n, int k, const T* M, int64_t ldm,
+                             int32_t* J, T* Tout, int64_t ldt, double* gaps) {
   Opts o;
-  Engine<double> e(c, o, false);
+  Engine<T> e(c, o, false);
   auto idb = e.take_id(r, n, k, true);
   if (c.dry) return RSVD_OK;
   if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
-  LK(launch_copy2d<double, double>(r, n, M, ldm, idb.W, n, c.stream));
+  if (sizeof(T) == 4) {
+    float* Wh = reinterpret_cast<float*>(idb.W);
+    LK(launch_transpose<float, float>(r, n, (const float*)M, ldm, Wh, r, c.stream));
+    LK(cudaMemsetAsync(Wh + (int64_t)r * n, 0, sizeof(float) * (size_t)r * n, c.stream));
+  } else {
+    LK(launch_copy2d<double, double>(r, n, (const double*)M, ldm, idb.W, n, c.stream));
+  }
   rsvd_status st = e.id_core(idb, r, n, k, gaps);
   if (st != RSVD_OK) return st;
   LK(launch_copy_i32(n, idb.J, J, c.stream));
-  if (T && n > k) LK(launch_transpose<double, double>(n - k, k, idb.Tt, k, T, ldt, c.stream));
+  if (Tout && n > k) LK(launch_transpose<T, T>(n - k, k, idb.Tt, k, Tout, ldt, c.stream));
   return RSVD_OK;
 }
 
@@ -1204,7 +1232,7 @@ size_t rsvd_cpqr_workspace_size(int r, int64_t n, int k) {
       n > 0x7fffffffLL)
     return 0;
   Ctx c;
-  cpqr_impl(c, r, n, k, nullptr, n, nullptr, nullptr, 0, nullptr);
+  cpqr_impl<double>(c, r, n, k, nullptr, n, nullptr, nullptr, 0, nullptr);
   return c.off + 256;
 }
 
@@ -1218,7 +1246,29 @@ rsvd_status rsvd_cpqr_id(int r, int64_t n, int k, const double* M, int64_t ldm, 
   if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
   Ctx c = make_ctx(work, work_bytes, d_info, stream);
   reset_info(c);
-  return finish(c, cpqr_impl(c, r, n, k, M, ldm, J, T, ldt, gaps));
+  return finish(c, cpqr_impl<double>(c, r, n, k, M, ldm, J, T, ldt, gaps));
+}
+
+size_t rsvd_cpqr_f32_workspace_size(int r, int64_t n, int k) {
+  if (r < 1 || n < 1 || k < 1 || k > r || k > n || r > 8192 || k > UPPER_SOLVE_MAX_K ||
+      n > 0x7fffffffLL)
+    return 0;
+  Ctx c;
+  cpqr_impl<float>(c, r, n, k, nullptr, n, nullptr, nullptr, 0, nullptr);
+  return c.off + 256;
+}
+
+rsvd_status rsvd_cpqr_id_f32(int r, int64_t n, int k, const float* M, int64_t ldm, int32_t* J,
+                             float* T, int64_t ldt, double* gaps, void* work, size_t work_bytes,
+                             int* d_info, void* stream) {
+  if (r < 1 || n < 1 || k < 1 || k > r || k > n || r > 8192 || n > 0x7fffffffLL)
+    return RSVD_ERR_INVALID_ARG;
+  if (k > UPPER_SOLVE_MAX_K) return RSVD_ERR_UNSUPPORTED;
+  if (!M || !J || ldm < n || (T && n > k && ldt < n - k)) return RSVD_ERR_INVALID_ARG;
+  if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
+  Ctx c = make_ctx(work, work_bytes, d_info, stream);
+  reset_info(c);
+  return finish(c, cpqr_impl<float>(c, r, n, k, M, ldm, J, T, ldt, gaps));
 }
 
 }  // extern "C"

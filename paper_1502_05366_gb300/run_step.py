@@ -8,7 +8,8 @@ path without holding the full matrix A on the device:
   apply_t    Z = A^T X, X m x l stored                         (power step / QB)
   orth       CholeskyQR of an m x l sample                     (re-orthonormalisation)
   small_svd  SVD of an l x l upper-triangular factor           (Alg. 5)
-  cpqr       k-step column-pivoted QR + T = S11^-1 S12 of r x n (Sec. 4, ID)
+  cpqr       k-step column-pivoted QR + T = S11^-1 S12 of r x n (Sec. 4, ID);
+             float32: the double-float kernel of the FP32 path, float64: FP64
 
 Example:  python -m paper_1502_05366_gb300.run_step --step cpqr --r 220 --n 20000 --k 200
 
@@ -43,7 +44,7 @@ def _inputs(args, dev):
         # rows scaled by 1/i like B = Q^T A of the same spectrum
         M = torch.randn(args.r, args.n, generator=g, dtype=torch.float64)
         M = M * (1.0 / torch.arange(1, args.r + 1, dtype=torch.float64))[:, None]
-        return M.to(dev), None
+        return M.to(dev, dt), None
     raise ValueError(args.step)
 
 

@@ -226,6 +226,22 @@ def test_cpqr_id(r, n, k):
         assert np.max(np.abs(T - To)) <= 1e-9 * max(1.0, np.max(np.abs(To)))
 
 
+@pytest.mark.parametrize("r,n,k", [(20, 50, 10), (60, 1000, 50), (220, 5000, 200), (8, 9, 8),
+                                   (33, 4097, 1), (200, 20011, 200)])
+def test_cpqr_id_f32_double_float(r, n, k):
+    """The double-float CPQR of the FP32 path against the FP64 oracle on the same
+    fp32 matrix: pivots identical, gaps to 1e-9, T to fp32 rounding."""
+    rng = np.random.default_rng(r * n + k + 1)
+    M = (rng.standard_normal((r, n)) * np.logspace(0, -4, n)[rng.permutation(n)]).astype(np.float32)
+    J, T, gaps = rs.cpqr_id(_dev(M, torch.float32), k)
+    J, T, gaps = J.cpu().numpy(), T.double().cpu().numpy(), gaps.cpu().numpy()
+    Jo, To, go = orc.id_from_matrix(M.astype(np.float64), k)
+    assert np.array_equal(J, Jo)
+    assert np.allclose(gaps[go < np.inf], go[go < np.inf], rtol=1e-9, atol=1e-12)
+    if n > k:
+        assert np.max(np.abs(T - To)) <= 1e-6 * max(1.0, np.max(np.abs(To)))
+
+
 def test_cpqr_golden_worked_example():
     import os
     M = np.array([[3, 0, 1, 0], [4, 0, 0, 2]], dtype=np.float64)
