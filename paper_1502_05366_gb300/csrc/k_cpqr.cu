@@ -695,11 +695,14 @@ cudaError_t launch_cpqr_df(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   return launch_cpqr_df_t<32, 256>(a, sms, s);
 }
 
+// S11 (k x k, column-major, upper triangular with beta on the diagonal), the
+// reciprocals of its diagonal and S12 (k x (n-k), row-major) as double-float
+// pairs (float2 hi, lo), in pivot order, from the column-major planes.
 __global__ void id_extract_df_kernel(int r, int64_t n, int k, const float* __restrict__ Wh,
                                      const float* __restrict__ Wl,
                                      const int32_t* __restrict__ J,
-                                     const double* __restrict__ diagR, double* __restrict__ S11,
-                                     double* __restrict__ S12) {
+                                     const double* __restrict__ diagR, float2* __restrict__ S11,
+                                     float2* __restrict__ dinv, float2* __restrict__ S12) {
   const int64_t total = n * (int64_t)k;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -708,13 +711,21 @@ __global__ void id_extract_df_kernel(int r, int64_t n, int k, const float* __res
     const int64_t c = J[pos];
     const int64_t o = c * r + i;            // column-major planes
     if (pos < k) {
-      double v;
-      if (i < pos) v = df_to_d(Wh[o], Wl[o]);
-      else if (i == pos) v = diagR[pos];
-      else v = 0.0;
+      float2 v = make_float2(0.f, 0.f);
+      if (i < pos) {
+        v = make_float2(Wh[o], Wl[o]);
+      } else if (i == pos) {
+        float h, l;
+        d_to_df(diagR[pos], h, l);
+        v = make_float2(h, l);
+        const double d = diagR[pos];
+        float ih = 0.f, il = 0.f;
+        if (d != 0.0) d_to_df(1.0 / d, ih, il);
+        dinv[pos] = make_float2(ih, il);
+      }
       S11[pos * k + i] = v;
     } else {
-      S12[(int64_t)i * (n - k) + (pos - k)] = df_to_d(Wh[o], Wl[o]);
+      S12[(int64_t)i * (n - k) + (pos - k)] = make_float2(Wh[o], Wl[o]);
     }
   }
 }
@@ -726,11 +737,201 @@ cudaError_t launch_id_extract_df(int r, int64_t n, int k, const double* W, const
   int64_t blocks = ceil_div(total, 256);
   if (blocks > 16384) blocks = 16384;
   const float* Wh = reinterpret_cast<const float*>(W);
+  float2* s11 = reinterpret_cast<float2*>(S11);
   id_extract_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(r, n, k, Wh, Wh + (int64_t)r * n, J,
-                                                        diagR, S11, S12);
+                                                        diagR, s11, s11 + (int64_t)k * k,
+                                                        reinterpret_cast<float2*>(S12));
   count_launch();
   return cudaGetLastError();
 }
+
+// Double-float back substitution for many right-hand sides,
+// x_i = s_i (1 / U_ii); s_q -= x_i U_qi, with U (column-major k x k, float2)
+// and the reciprocals of its diagonal as written by launch_id_extract_df.
+__device__ __forceinline__ float2 df_mul2(float2 a, float2 b) {
+  const float ph = __fmul_rn(a.x, b.x);
+  float pe = __fmaf_rn(a.x, b.x, -ph);
+  pe = __fmaf_rn(a.x, b.y, pe);
+  pe = __fmaf_rn(a.y, b.x, pe);
+  float h, l;
+  df_fast_two_sum(ph, pe, h, l);
+  return make_float2(h, l);
+}
+// s - x u
+__device__ __forceinline__ float2 df_fms2(float2 s, float2 x, float2 u) {
+  const float ph = __fmul_rn(x.x, u.x);
+  float pe = __fmaf_rn(x.x, u.x, -ph);
+  pe = __fmaf_rn(x.x, u.y, pe);
+  pe = __fmaf_rn(x.y, u.x, pe);
+  float a, b;
+  df_two_sum(s.x, -ph, a, b);
+  b = __fadd_rn(b, __fsub_rn(s.y, pe));
+  float h, l;
+  df_fast_two_sum(a, b, h, l);
+  return make_float2(h, l);
+}
+
+// One warp solves NC right-hand sides at once (kk <= 32 RPL); lane l holds rows l + 32 t (t < RPL) of each.  Step i: the lane owning
+// row i forms x_i = s_i / U_ii and broadcasts it; every lane updates its rows
+// q < i with U(q, i), read coalesced from the column-major U.
+__device__ __forceinline__ float2 load_df(const float2* p) { return *p; }
+__device__ __forceinline__ float2 load_df(const float* p) { return make_float2(*p, 0.f); }
+
+template <typename TR, typename TO, int NC, int RPL>
+__global__ void __launch_bounds__(256) upper_solve_df_warp_kernel(
+    int kk, int64_t ncols, const float2* __restrict__ U, const float2* __restrict__ dinv,
+    const TR* __restrict__ rhs, int64_t rs_i, int64_t rs_c, TO* __restrict__ out,
+    int64_t os_i, int64_t os_c, int* d_info) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nt = (kk + 31) >> 5;
+  for (int64_t grp = gw; grp * NC < ncols; grp += nw) {
+    const int64_t cbase = grp * NC;
+    float sh[NC][RPL], sl[NC][RPL];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int i = lane + 32 * t;
+        float2 v = make_float2(0.f, 0.f);
+        if (t < nt && i < kk && cbase + c < ncols) v = load_df(rhs + i * rs_i + (cbase + c) * rs_c);
+        sh[c][t] = v.x;
+        sl[c][t] = v.y;
+      }
+    for (int i = kk - 1; i >= 0; --i) {
+      const int owner = i & 31, ti = i >> 5;
+      const float2 di = __ldg(dinv + i);
+      if (di.x == 0.f && grp == 0 && lane == 0) set_info(d_info, RSVD_ERR_NUMERIC);
+      float xh[NC], xl[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float vh = 0.f, vl = 0.f;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t)
+          if (t == ti) {
+            vh = sh[c][t];
+            vl = sl[c][t];
+          }
+        const float2 x = df_mul2(make_float2(vh, vl), di);
+        xh[c] = __shfl_sync(0xffffffffu, x.x, owner);
+        xl[c] = __shfl_sync(0xffffffffu, x.y, owner);
+      }
+      const float2* ucol = U + (int64_t)i * kk;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int q = lane + 32 * t;
+        if (t <= ti) {
+          if (q < i) {
+            const float2 u = __ldg(ucol + q);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              const float2 r = df_fms2(make_float2(sh[c][t], sl[c][t]), make_float2(xh[c], xl[c]), u);
+              sh[c][t] = r.x;
+              sl[c][t] = r.y;
+            }
+          } else if (q == i) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              sh[c][t] = xh[c];
+              sl[c][t] = xl[c];
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int i = lane + 32 * t;
+        if (t < nt && i < kk && cbase + c < ncols)
+          out[i * os_i + (cbase + c) * os_c] = (TO)((double)sh[c][t] + (double)sl[c][t]);
+      }
+  }
+}
+
+template <typename TR, typename TO, int NC, int RPL>
+static cudaError_t launch_solve_warp(int kk, int64_t ncols, const double* S11, const TR* rhs,
+                                     int64_t rs_i, int64_t rs_c, TO* out, int64_t os_i,
+                                     int64_t os_c, int* d_info, cudaStream_t s) {
+  const float2* U = reinterpret_cast<const float2*>(S11);
+  // one wave of resident blocks; warps stride over the column groups
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, upper_solve_df_warp_kernel<TR, TO, NC, RPL>, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t warps = ceil_div(ncols, NC);
+  int64_t blocks = ceil_div(warps, 8);
+  const int64_t cap = (int64_t)device_sm_count() * per_sm;
+  if (blocks > cap) blocks = cap;
+  const int tr_ = trace_begin(RSVD_TRACE_SOLVE, s);
+  upper_solve_df_warp_kernel<TR, TO, NC, RPL><<<(unsigned)blocks, 256, 0, s>>>(
+      kk, ncols, U, U + (int64_t)kk * kk, rhs, rs_i, rs_c, out, os_i, os_c, d_info);
+  count_launch();
+  trace_end(tr_, s);
+  return cudaGetLastError();
+}
+
+template <typename TR, typename TO>
+cudaError_t launch_upper_solve_df(int kk, int64_t ncols, const double* S11, const TR* rhs,
+                                  int64_t rs_i, int64_t rs_c, TO* out, int64_t os_i,
+                                  int64_t os_c, int* d_info, cudaStream_t s) {
+  if (kk <= 0 || ncols <= 0) return cudaSuccess;
+  if (kk <= 256)
+    return launch_solve_warp<TR, TO, 4, 8>(kk, ncols, S11, rhs, rs_i, rs_c, out, os_i, os_c,
+                                           d_info, s);
+  if (kk <= 1024)
+    return launch_solve_warp<TR, TO, 1, 32>(kk, ncols, S11, rhs, rs_i, rs_c, out, os_i, os_c,
+                                            d_info, s);
+  return cudaErrorInvalidValue;
+}
+
+// Upper-triangular R (kk x kk, R(i, t) = R[i*ldr + t], fp32 values) as the
+// column-major float2 matrix and diagonal reciprocals of the solve above.
+template <typename T>
+__global__ void upper_to_df_kernel(int kk, const T* __restrict__ R, int64_t ldr,
+                                   float2* __restrict__ U, float2* __restrict__ dinv) {
+  const int64_t total = (int64_t)kk * kk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / kk), i = (int)(e - (int64_t)t * kk);
+    float2 v = make_float2(0.f, 0.f);
+    if (i <= t) {
+      float h, l;
+      d_to_df((double)R[(int64_t)i * ldr + t], h, l);
+      v = make_float2(h, l);
+    }
+    U[e] = v;
+    if (i == t) {
+      const double d = (double)R[(int64_t)i * ldr + i];
+      float ih = 0.f, il = 0.f;
+      if (d != 0.0) d_to_df(1.0 / d, ih, il);
+      dinv[i] = make_float2(ih, il);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_upper_to_df(int kk, const T* R, int64_t ldr, double* S11, cudaStream_t s) {
+  if (kk <= 0) return cudaSuccess;
+  float2* U = reinterpret_cast<float2*>(S11);
+  const int64_t total = (int64_t)kk * kk;
+  int64_t blocks = ceil_div(total, 256);
+  if (blocks > 4096) blocks = 4096;
+  upper_to_df_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(kk, R, ldr, U, U + total);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_upper_to_df<float>(int, const float*, int64_t, double*, cudaStream_t);
+
+template cudaError_t launch_upper_solve_df<float2, float>(int, int64_t, const double*,
+                                                          const float2*, int64_t, int64_t, float*,
+                                                          int64_t, int64_t, int*, cudaStream_t);
+template cudaError_t launch_upper_solve_df<float, float>(int, int64_t, const double*,
+                                                         const float*, int64_t, int64_t, float*,
+                                                         int64_t, int64_t, int*, cudaStream_t);
 
 // S11 (k x k, column-major, upper triangular incl. beta on the diagonal) and
 // S12 (k x (n-k), row-major; column c' = position k + c') in pivot order, from

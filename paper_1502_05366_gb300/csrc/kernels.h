@@ -139,8 +139,22 @@ cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s);
 // planes, hi then lo, each r x n COLUMN-major (ld r); used for sketches of
 // FP32 data, r <= 1024.
 cudaError_t launch_cpqr_df(const CpqrArgs& a, int* grid_out, cudaStream_t s);
+// S11 as k x k float2 pairs followed by k float2 reciprocals of its diagonal
+// (S11 must hold k*k + k doubles), S12 as k x (n-k) float2 pairs.
 cudaError_t launch_id_extract_df(int r, int64_t n, int k, const double* W, const int32_t* J,
                                  const double* diagR, double* S11, double* S12, cudaStream_t s);
+// Back substitution S11 x = rhs for ncols right-hand sides in double-float
+// (kk <= 1024; S11 in the layout written by launch_id_extract_df or
+// launch_upper_to_df); rhs(i, c) = rhs[i*rs_i + c*rs_c] (float2 pairs or
+// floats), out(i, c) = out[i*os_i + c*os_c].
+template <typename TR, typename TO>
+cudaError_t launch_upper_solve_df(int kk, int64_t ncols, const double* S11, const TR* rhs,
+                                  int64_t rs_i, int64_t rs_c, TO* out, int64_t os_i,
+                                  int64_t os_c, int* d_info, cudaStream_t s);
+// Upper-triangular R (R(i, t) = R[i*ldr + t]) into that layout (kk*kk + kk
+// float2 in S11).
+template <typename T>
+cudaError_t launch_upper_to_df(int kk, const T* R, int64_t ldr, double* S11, cudaStream_t s);
 size_t cpqr_scratch_bytes(int64_t n);
 // Largest triangle the many-right-hand-side solve handles (one 32-thread block
 // of kk doubles each in 220 KB of shared memory).

@@ -479,7 +479,7 @@ struct Engine {
     d.bar = c.template take<unsigned>(4);
     d.J = c.template take<int32_t>((size_t)n);
     if (with_T) {
-      d.S11 = c.template take<double>((size_t)k * k);
+      d.S11 = c.template take<double>((size_t)k * k + k);   // + diagonal reciprocals (df path)
       d.S12 = c.template take<double>((size_t)(n - k) * k + 1);
       d.Tt = c.template take<T>((size_t)(n - k) * k + 1);
     } else {
@@ -521,8 +521,12 @@ struct Engine {
       LK(launch_id_extract(r, n, k, d.W, d.J, d.diagR, d.S11, d.S12, c.stream));
     // S11 column-major: U(i, t) = S11[t*k + i]; rhs(i, c) = S12[i*(n-k) + c];
     // out Tt(c, i) = Tt[c*k + i]
-    LK(launch_upper_solve<double, T>(k, n - k, d.S11, 1, k, d.S12, n - k, 1, d.Tt, 1, k,
-                                     c.d_info, c.stream));
+    if (DF)
+      LK(launch_upper_solve_df<float2, float>(k, n - k, d.S11, (const float2*)d.S12, n - k, 1,
+                                              (float*)d.Tt, 1, k, c.d_info, c.stream));
+    else
+      LK(launch_upper_solve<double, T>(k, n - k, d.S11, 1, k, d.S12, n - k, 1, d.Tt, 1, k,
+                                       c.d_info, c.stream));
     return RSVD_OK;
   }
 
@@ -565,7 +569,7 @@ struct Engine {
     int64_t kc;
     tn_split(k, Kp, n - k, sms, &ns, &kc);
     u.mslabs = c.template take<T>((size_t)ns * k * Kp);
-    u.RR64 = c.template take<double>((size_t)Kp * Kp);
+    u.RR64 = c.template take<double>((size_t)Kp * Kp + Kp);
     return u;
   }
 
@@ -605,9 +609,15 @@ struct Engine {
     LK(launch_gather_rows_by_perm<T>(k, Kp, QR, Kp, idb.J, u.M1b, Kp, c.stream));
     LK(launch_add_inplace<T>(k, Kp, u.M1b, Kp, u.M1, Kp, c.stream));
     // U R_R^T = M1  ->  R_R U(c, :)^T = M1(c, :)^T
-    LK(launch_copy2d<T, double>(Kp, Kp, u.ob.Racc, Kp, u.RR64, Kp, c.stream));
-    LK(launch_upper_solve<T, T>(k, k, u.RR64, Kp, 1, u.M1, 1, Kp, Ucur, 1, ldu, c.d_info,
-                                c.stream));
+    if (sizeof(T) == 4 && k <= 1024) {
+      LK(launch_upper_to_df<float>(k, (const float*)u.ob.Racc, Kp, u.RR64, c.stream));
+      LK(launch_upper_solve_df<float, float>(k, k, u.RR64, (const float*)u.M1, 1, Kp,
+                                             (float*)Ucur, 1, ldu, c.d_info, c.stream));
+    } else {
+      LK(launch_copy2d<T, double>(Kp, Kp, u.ob.Racc, Kp, u.RR64, Kp, c.stream));
+      LK(launch_upper_solve<T, T>(k, k, u.RR64, Kp, 1, u.M1, 1, Kp, Ucur, 1, ldu, c.d_info,
+                                  c.stream));
+    }
     return RSVD_OK;
   }
 };
