@@ -429,6 +429,117 @@ __device__ __forceinline__ void df_acc_sqr(float xh, float xl, float& s, float& 
   e = __fadd_rn(e, __fadd_rn(t, pe));
 }
 
+// Row-slot granularity of the specialised column passes: single slots for
+// r <= 256, groups of 4 for r <= 1024 (8 instantiations either way).
+template <int RPL>
+__host__ __device__ constexpr int SLOT_STEP() { return RPL <= 8 ? 1 : RPL / 8; }
+
+// One step's dot products, rank-1 updates and norm downdates over the CTA's
+// columns (one warp per column), with S row slots per lane.
+struct CpqrDfCol {
+  float* Wh;
+  float* Wl;
+  float2* nrm2;
+  float* nref;
+  const float* svh;
+  const float* svl;
+  int r, j, len;
+  int64_t p, c0, c1;
+  float tauh, taul;
+  bool zero;
+  int lane, warp;
+
+  template <int S, int NWARP>
+  __device__ __forceinline__ void run() const {
+    const float tol3z = 1.4901161193847656e-08f;   // sqrt(eps_fp64), as in the FP64 kernel
+    float vh[S], vl[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const int i = lane + 32 * t;
+      vh[t] = i < len ? svh[i] : 0.f;
+      vl[t] = i < len ? svl[i] : 0.f;
+    }
+    for (int64_t c = c0 + warp; c < c1; c += NWARP) {
+      if (c == p) continue;                                  // warp-uniform
+      const float2 nc = nrm2[c];
+      if (nc.x < 0.f) continue;                              // already pivoted
+      float* colh = Wh + c * r + j;
+      float* coll = Wl + c * r + j;
+      float wh[S], wl[S];
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        const int i = lane + 32 * t;
+        wh[t] = i < len ? colh[i] : 0.f;
+        wl[t] = i < len ? coll[i] : 0.f;
+      }
+      if (!zero) {
+        float sd = 0.f, ed = 0.f;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const float ph = __fmul_rn(vh[t], wh[t]);
+          float pe = __fmaf_rn(vh[t], wh[t], -ph);
+          pe = __fmaf_rn(vh[t], wl[t], pe);
+          pe = __fmaf_rn(vl[t], wh[t], pe);
+          float e;
+          df_two_sum(sd, ph, sd, e);
+          ed = __fadd_rn(ed, __fadd_rn(e, pe));
+        }
+        df_warp_sum(sd, ed);
+        float dh, dl;
+        df_fast_two_sum(sd, ed, dh, dl);
+        // t = tau * (v . w) as a double-float pair
+        const float qh = __fmul_rn(tauh, dh);
+        float qe = __fmaf_rn(tauh, dh, -qh);
+        qe = __fmaf_rn(tauh, dl, qe);
+        qe = __fmaf_rn(taul, dh, qe);
+        float th, tl;
+        df_fast_two_sum(qh, qe, th, tl);
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const float ph = __fmul_rn(th, vh[t]);
+          float pe = __fmaf_rn(th, vh[t], -ph);
+          pe = __fmaf_rn(th, vl[t], pe);
+          pe = __fmaf_rn(tl, vh[t], pe);
+          float sh, se;
+          df_two_sum(wh[t], -ph, sh, se);
+          se = __fadd_rn(se, __fsub_rn(wl[t], pe));
+          df_fast_two_sum(sh, se, wh[t], wl[t]);
+          const int i = lane + 32 * t;
+          if (i < len) {
+            colh[i] = wh[t];
+            coll[i] = wl[t];
+          }
+        }
+      }
+      // residual norm downdate nu^2 - W(j, c)^2 (lane 0 holds row j), in
+      // double-float; exact recompute on cancellation (LAPACK safeguard)
+      float nh = 0.f, nl = 0.f;
+      int recompute = 0;
+      if (lane == 0) {
+        float ph, pe, sh, se;
+        df_sqr(wh[0], wl[0], ph, pe);
+        df_two_sum(nc.x, -ph, sh, se);
+        se = __fadd_rn(se, __fsub_rn(nc.y, pe));
+        df_fast_two_sum(sh, se, nh, nl);
+        recompute = (!(nh > tol3z * nref[c]) && j + 1 < r) ? 1 : 0;
+      }
+      recompute = __shfl_sync(0xffffffffu, recompute, 0);
+      if (recompute) {
+        float qs = 0.f, qe = 0.f;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const int i = lane + 32 * t;
+          if (i >= 1 && i < len) df_acc_sqr(wh[t], wl[t], qs, qe);
+        }
+        df_warp_sum(qs, qe);
+        df_fast_two_sum(qs, qe, nh, nl);
+        if (lane == 0) nref[c] = nh;
+      }
+      if (lane == 0) nrm2[c] = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
+    }
+  }
+};
+
 // W is COLUMN-major here (element (i, c) in Wh[c*r + i], Wl[c*r + i]), so one
 // warp owns a column per iteration: lane l holds rows j + l + 32 t
 // (t < RPL) of it in registers from the load through the dot product, the
@@ -461,7 +572,6 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
   float* __restrict__ nref = reinterpret_cast<float*>(nrm2 + n);
   float4* __restrict__ pv = reinterpret_cast<float4*>(a.pval);   // (b1h, b1l, b2h, b2l)
   double* __restrict__ diagR = a.diagR;
-  const float tol3z = 1.4901161193847656e-08f;   // sqrt(eps_fp64), as in the FP64 kernel
 
   // exact initial squared norms, one warp per column
   for (int64_t c = c0 + warp; c < c1; c += NWARP) {
@@ -546,98 +656,21 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
       }
     }
     __syncthreads();
-    float vh[RPL], vl[RPL];
-#pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-      const int i = lane + 32 * t;
-      vh[t] = i < len ? svh[i] : 0.f;
-      vl[t] = i < len ? svl[i] : 0.f;
-    }
     const float tauh = s_th, taul = s_tl;
     const bool zero = s_zero != 0;
-    const int nt = (len + 31) >> 5;          // row slots in use (warp-uniform)
-    // ---- every warp: dot, update and norm downdate of its columns ----
-    for (int64_t c = c0 + warp; c < c1; c += NWARP) {
-      if (c == p) continue;                                  // warp-uniform
-      const float2 nc = nrm2[c];
-      if (nc.x < 0.f) continue;                              // already pivoted
-      float* colh = Wh + c * r + j;
-      float* coll = Wl + c * r + j;
-      float wh[RPL], wl[RPL];
-#pragma unroll
-      for (int t = 0; t < RPL; ++t) {
-        const int i = lane + 32 * t;
-        wh[t] = (t < nt && i < len) ? colh[i] : 0.f;
-        wl[t] = (t < nt && i < len) ? coll[i] : 0.f;
-      }
-      if (!zero) {
-        float sd = 0.f, ed = 0.f;
-#pragma unroll
-        for (int t = 0; t < RPL; ++t) {
-          if (t < nt) {
-            const float ph = __fmul_rn(vh[t], wh[t]);
-            float pe = __fmaf_rn(vh[t], wh[t], -ph);
-            pe = __fmaf_rn(vh[t], wl[t], pe);
-            pe = __fmaf_rn(vl[t], wh[t], pe);
-            float e;
-            df_two_sum(sd, ph, sd, e);
-            ed = __fadd_rn(ed, __fadd_rn(e, pe));
-          }
-        }
-        df_warp_sum(sd, ed);
-        float dh, dl;
-        df_fast_two_sum(sd, ed, dh, dl);
-        // t = tau * (v . w) as a double-float pair
-        const float qh = __fmul_rn(tauh, dh);
-        float qe = __fmaf_rn(tauh, dh, -qh);
-        qe = __fmaf_rn(tauh, dl, qe);
-        qe = __fmaf_rn(taul, dh, qe);
-        float th, tl;
-        df_fast_two_sum(qh, qe, th, tl);
-#pragma unroll
-        for (int t = 0; t < RPL; ++t) {
-          if (t < nt) {
-            const float ph = __fmul_rn(th, vh[t]);
-            float pe = __fmaf_rn(th, vh[t], -ph);
-            pe = __fmaf_rn(th, vl[t], pe);
-            pe = __fmaf_rn(tl, vh[t], pe);
-            float sh, se;
-            df_two_sum(wh[t], -ph, sh, se);
-            se = __fadd_rn(se, __fsub_rn(wl[t], pe));
-            df_fast_two_sum(sh, se, wh[t], wl[t]);
-            const int i = lane + 32 * t;
-            if (i < len) {
-              colh[i] = wh[t];
-              coll[i] = wl[t];
-            }
-          }
-        }
-      }
-      // residual norm downdate nu^2 - W(j, c)^2 (lane 0 holds row j), in
-      // double-float; exact recompute on cancellation (LAPACK safeguard)
-      float nh = 0.f, nl = 0.f;
-      int recompute = 0;
-      if (lane == 0) {
-        float ph, pe, sh, se;
-        df_sqr(wh[0], wl[0], ph, pe);
-        df_two_sum(nc.x, -ph, sh, se);
-        se = __fadd_rn(se, __fsub_rn(nc.y, pe));
-        df_fast_two_sum(sh, se, nh, nl);
-        recompute = (!(nh > tol3z * nref[c]) && j + 1 < r) ? 1 : 0;
-      }
-      recompute = __shfl_sync(0xffffffffu, recompute, 0);
-      if (recompute) {
-        float qs = 0.f, qe = 0.f;
-#pragma unroll
-        for (int t = 0; t < RPL; ++t) {
-          const int i = lane + 32 * t;
-          if (t < nt && i >= 1 && i < len) df_acc_sqr(wh[t], wl[t], qs, qe);
-        }
-        df_warp_sum(qs, qe);
-        df_fast_two_sum(qs, qe, nh, nl);
-        if (lane == 0) nref[c] = nh;
-      }
-      if (lane == 0) nrm2[c] = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
+    // the column pass specialised on the row slots in use, so that no
+    // instruction is spent on slots beyond the active rows
+    const int nt = (len + 31) >> 5;
+    CpqrDfCol cp{Wh, Wl, nrm2, nref, svh, svl, r, j, len, p, c0, c1, tauh, taul, zero, lane, warp};
+    switch ((nt + SLOT_STEP<RPL>() - 1) / SLOT_STEP<RPL>()) {
+      case 1: cp.template run<1 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 2: cp.template run<2 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 3: cp.template run<3 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 4: cp.template run<4 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 5: cp.template run<5 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 6: cp.template run<6 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 7: cp.template run<7 * SLOT_STEP<RPL>(), NWARP>(); break;
+      default: cp.template run<8 * SLOT_STEP<RPL>(), NWARP>(); break;
     }
     if (p >= c0 && p < c1 && tid == 0) nrm2[p] = make_float2(-1.f, 0.f);
     if (blockIdx.x == 0 && tid == 0) {
