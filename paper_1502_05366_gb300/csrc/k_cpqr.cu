@@ -702,9 +702,9 @@ static cudaError_t launch_cpqr_df_t(const CpqrArgs& a, int sms, cudaStream_t s) 
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, dyn);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  // one SM is left to a single-CTA kernel running beside the CPQR on another
-  // stream (the Jacobi SVD of the combined SVD + ID/CUR call)
-  int64_t G = sms > 1 ? sms - 1 : 1;
+  // eight SMs are left to the Jacobi SVD (one 8-CTA cluster) that runs beside
+  // the CPQR on another stream in the combined SVD + ID/CUR call
+  int64_t G = sms > 16 ? sms - 8 : (sms > 1 ? sms - 1 : 1);
   const int64_t byn = ceil_div(a.n, 8);
   if (G > byn) G = byn;
   if (G > 1024) G = 1024;

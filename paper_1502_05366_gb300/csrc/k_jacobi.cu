@@ -11,6 +11,8 @@
 // Pairs are visited in the round-robin (circle) order, l/2 disjoint pairs per
 // round, one warp per pair; one CTA of 1024 threads holds X in shared memory
 // (global memory beyond the limit).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -24,7 +26,14 @@ template <> __device__ __forceinline__ float jeps<float>() { return 5.9604645e-8
 template <> __device__ __forceinline__ double jeps<double>() { return 1.1102230246251565e-16; }
 }  // namespace
 
+// Cluster variant (fp32, 32 <= l <= 256): 8 CTAs of one thread-block cluster.
+constexpr int JC = 8;           // CTAs per cluster
+constexpr int JCT = 512;        // threads per CTA (16 warps: one per pair of a sub-round)
+static inline bool jacobi_use_cluster(int l, int elem) { return elem == 4 && l >= 32 && l <= 256; }
+__host__ __device__ inline int jc_width(int l) { return (l + 2 * JC - 1) / (2 * JC); }
+
 size_t jacobi_scratch_bytes(int l, int elem) {
+  if (jacobi_use_cluster(l, elem)) return (size_t)2 * JC * jc_width(l) * sizeof(double);
   const size_t b = (size_t)l * l * elem;
   return b <= JSMEM_LIMIT ? 0 : b;
 }
@@ -186,6 +195,235 @@ __global__ void __launch_bounds__(jthreads<T>()) jacobi_kernel(int l, const T* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Block one-sided Jacobi on a thread-block cluster (fp32).
+//
+// The l columns (padded with zero columns to 16 w) form 16 blocks of w
+// columns.  CTA c of the 8-CTA cluster holds two blocks ("top" and "bottom")
+// in its shared memory.  A sweep is: the pairs inside every block (first
+// block-round), then 15 block-rounds in the circle order of the 16 blocks
+// (top block of CTA 0 fixed), in which each CTA orthogonalises all w^2 cross
+// pairs between its two blocks, w disjoint pairs per sub-round, one warp per
+// pair.  Between block-rounds the blocks move to the neighbouring CTAs through
+// distributed shared memory (two cluster barriers).  Every pair of columns
+// meets once per sweep, as in the cyclic one-sided method; the rotation of a
+// pair is the same formula as in jacobi_kernel.  The sweep loop ends for all
+// CTAs together (rotation counts exchanged in distributed shared memory), so
+// every CTA passes the same sequence of cluster barriers.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+// Rotate columns xa, xb (l floats each, shared memory) of one warp's pair;
+// true when a rotation was applied.
+__device__ __forceinline__ bool jc_rotate(float* xa, float* xb, int l, float tol, int lane) {
+  float al = 0.f, be = 0.f, ga = 0.f;
+  for (int i = lane; i < l; i += 32) {
+    const float u = xa[i], v = xb[i];
+    al = fmaf(u, u, al);
+    be = fmaf(v, v, be);
+    ga = fmaf(u, v, ga);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  if (!(al > 0.f) || !(be > 0.f)) return false;
+  const float scale = sqrtf(al) * sqrtf(be);
+  if (fabsf(ga) < 64.f * tol * scale) {   // near the threshold: Dot2
+    float gp = 0.f, gs = 0.f;
+    for (int i = lane; i < l; i += 32) {
+      const float u = xa[i], v = xb[i];
+      const float h = u * v;
+      const float hr = fmaf(u, v, -h);
+      float e;
+      two_sum(gp, h, gp, e);
+      gs += e + hr;
+    }
+    warp_sum2(gp, gs);
+    ga = gp + gs;
+  }
+  if (!(fabsf(ga) > tol * scale)) return false;
+  const float zeta = (be - al) / (2.f * ga);
+  const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float c = 1.f / sqrtf(1.f + t * t);
+  const float sn = c * t;
+  for (int i = lane; i < l; i += 32) {
+    const float u = xa[i], v = xb[i];
+    xa[i] = c * u - sn * v;
+    xb[i] = sn * u + c * v;
+  }
+  return true;
+}
+
+__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JCT)
+    jacobi_cluster_kernel(int l, const float* __restrict__ M, int64_t ldm, float* __restrict__ Uh,
+                          int64_t lduh, double* __restrict__ Sh, double* __restrict__ sig,
+                          int max_sweeps, int* d_info) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) float jsm[];
+  __shared__ int s_rot;
+  __shared__ int s_cnt[JC];
+  __shared__ int s_in[2];                    // this CTA's current inbox buffers (top, bottom)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NWARP = JCT / 32;
+  const int w = jc_width(l);
+  const int bsz = w * l;                     // floats per block, column-major X[a*l + i]
+  // buffer roles (indices into the four block buffers)
+  int iT = 0, iB = 1, inT = 2, inB = 3;
+  // initial blocks: top = block c, bottom = block 2 JC - 1 - c; block q holds
+  // columns q w .. q w + w - 1 of M (zero beyond l)
+  {
+    const int qT = rank, qB = 2 * JC - 1 - rank;
+    for (int e = tid; e < 2 * bsz; e += JCT) {
+      const int which = e / bsz, rem = e - which * bsz;
+      const int a = rem / l, i = rem - a * l;
+      const int col = (which == 0 ? qT : qB) * w + a;
+      jsm[(which == 0 ? iT : iB) * bsz + rem] = col < l ? M[(int64_t)i * ldm + col] : 0.f;
+    }
+  }
+  if (tid == 0) {
+    s_rot = 0;
+    s_in[0] = inT;
+    s_in[1] = inB;
+  }
+  __syncthreads();
+  const float tol = sqrtf((float)l) * 5.9604645e-8f;
+  const int wp = w + (w & 1);                // players of the in-block round robin
+  bool converged = false;
+  int sweep = 0;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    // ---- pairs inside the two blocks held now (covers all blocks) ----
+    for (int rr = 0; rr < wp - 1; ++rr) {
+      const int half = wp / 2;
+      if (warp < 2 * half) {
+        const int blk = warp / half, pi = warp - blk * half;
+        int a, b;
+        if (pi == 0) {
+          a = wp - 1;
+          b = rr;
+        } else {
+          a = (rr + pi) % (wp - 1);
+          b = (rr - pi + wp - 1) % (wp - 1);
+        }
+        if (a < w && b < w) {
+          float* base = jsm + (blk == 0 ? iT : iB) * bsz;
+          if (jc_rotate(base + a * l, base + b * l, l, tol, lane) && lane == 0)
+            atomicAdd(&s_rot, 1);
+        }
+      }
+      __syncthreads();
+    }
+    // ---- 2 JC - 1 block-rounds of cross pairs, blocks rotating between CTAs ----
+    for (int br = 0; br < 2 * JC - 1; ++br) {
+      for (int sr = 0; sr < w; ++sr) {
+        if (warp < w) {
+          const int a = warp, b = (warp + sr) % w;
+          if (jc_rotate(jsm + iT * bsz + a * l, jsm + iB * bsz + b * l, l, tol, lane) &&
+              lane == 0)
+            atomicAdd(&s_rot, 1);
+        }
+        __syncthreads();
+      }
+      const bool last = (br == 2 * JC - 2);
+      cluster.sync();                         // (A) every CTA done with its blocks
+      // send: CTA 0 its bottom to CTA 1's top inbox; CTA c in 1..JC-2 its top
+      // to CTA c+1's top inbox; CTA c >= 1 its bottom to CTA c-1's bottom inbox
+      {
+        // the receivers' inbox buffers (their roles differ from this CTA's)
+        float* dstT = nullptr;
+        const float* srcT = nullptr;
+        if (rank <= JC - 2) {
+          const int q = rank + 1;
+          dstT = cluster.map_shared_rank(jsm, q) + *cluster.map_shared_rank(&s_in[0], q) * bsz;
+          srcT = jsm + (rank == 0 ? iB : iT) * bsz;
+        }
+        float* dstB = nullptr;
+        if (rank >= 1) {
+          const int q = rank - 1;
+          dstB = cluster.map_shared_rank(jsm, q) + *cluster.map_shared_rank(&s_in[1], q) * bsz;
+        }
+        const float* srcB = jsm + iB * bsz;
+        for (int e = tid; e < bsz; e += JCT) {
+          if (dstT) dstT[e] = srcT[e];
+          if (dstB) dstB[e] = srcB[e];
+        }
+      }
+      if (last && tid == 0) {
+        // this sweep's rotation count to every CTA of the cluster
+        for (int q = 0; q < JC; ++q) cluster.map_shared_rank(s_cnt, q)[rank] = s_rot;
+      }
+      cluster.sync();                         // (B) inboxes filled
+      if (rank == 0) {
+        const int t = iB;
+        iB = inB;
+        inB = t;
+      } else if (rank <= JC - 2) {
+        int t = iT;
+        iT = inT;
+        inT = t;
+        t = iB;
+        iB = inB;
+        inB = t;
+      } else {
+        const int oT = iT, oB = iB;
+        iT = inT;
+        iB = oT;                              // own top becomes the bottom
+        inT = oB;
+      }
+      if (last) {
+        int tot = 0;
+        for (int q = 0; q < JC; ++q) tot += s_cnt[q];
+        converged = (tot == 0);
+      }
+      // publish the new inbox roles: peers read them only after the next (A)
+      __syncthreads();
+      if (tid == 0) {
+        s_in[0] = inT;
+        s_in[1] = inB;
+        if (last) s_rot = 0;
+      }
+      __syncthreads();
+    }
+  }
+  if (!converged && rank == 0 && tid == 0) set_info(d_info, RSVD_ERR_NO_CONVERGENCE);
+  // ---- sigma of the 2 w columns held, their global ranks, Uh columns ----
+  __shared__ double s_sig[64];
+  for (int a = warp; a < 2 * w; a += NWARP) {
+    const float* x = jsm + (a < w ? iT : iB) * bsz + (a % w) * l;
+    float sq = 0.f;
+    for (int i = lane; i < l; i += 32) sq = fmaf(x[i], x[i], sq);
+    sq = warp_sum(sq);
+    if (lane == 0) {
+      const double sg = (double)sqrtf(sq);
+      s_sig[a] = sg;
+      sig[rank * 2 * w + a] = sg;
+      if (!isfinite(sg)) set_info(d_info, RSVD_ERR_NUMERIC);
+    }
+  }
+  cluster.sync();                             // every sigma written (cluster scope)
+  const int N = 2 * JC * w;
+  for (int a = warp; a < 2 * w; a += NWARP) {
+    const int slot = rank * 2 * w + a;
+    const double sj = s_sig[a];
+    int rk = 0;
+    for (int q = lane; q < N; q += 32) {
+      const double sq = __ldcg(sig + q);
+      rk += (sq > sj || (sq == sj && q < slot)) ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, o);
+    if (rk < l) {
+      const float inv = sj > 0.0 ? (float)(1.0 / sj) : 0.f;
+      const float* x = jsm + (a < w ? iT : iB) * bsz + (a % w) * l;
+      for (int i = lane; i < l; i += 32) Uh[(int64_t)i * lduh + rk] = x[i] * inv;
+      if (lane == 0) Sh[rk] = sj;
+    }
+  }
+  cluster.sync();                             // keep every CTA's shared memory alive to the end
+}
+
 // P = M^T Uh (l x l): sigma_j = ||P(:, j)|| (FP64 accumulation), sorted in
 // descending order (ties: lower column first); Sh, Vh(:, r) = P(:, j) / sigma_j
 // and Uh(:, r) = Uin(:, j) with r the rank of column j.
@@ -253,6 +491,21 @@ cudaError_t launch_jacobi(int l, const T* M, int64_t ldm, T* Uh, int64_t lduh, d
   (void)Vh;
   (void)ldvh;
   if (l > 1024) return cudaErrorInvalidValue;
+  if (jacobi_use_cluster(l, (int)sizeof(T))) {
+    if (!scratch) return cudaErrorInvalidValue;
+    const size_t dyn = (size_t)4 * jc_width(l) * l * sizeof(float);
+    if (dyn > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e != cudaSuccess) return e;
+    }
+    const int tr_ = trace_begin(RSVD_TRACE_JACOBI, s);
+    jacobi_cluster_kernel<<<JC, JCT, dyn, s>>>(l, (const float*)M, ldm, (float*)Uh, lduh, Sh,
+                                               (double*)scratch, max_sweeps, d_info);
+    count_launch();
+    trace_end(tr_, s);
+    return cudaGetLastError();
+  }
   const size_t bytes = (size_t)l * l * sizeof(T);
   size_t dyn = 0;
   T* scr = nullptr;
