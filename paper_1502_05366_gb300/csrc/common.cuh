@@ -106,9 +106,13 @@ __device__ __forceinline__ float minus2log_f(float u) {
   return -1.3862943611198906f * __log2f(u);
 }
 
+// sqrt(x) for the Box-Muller radius (x = -2 ln u >= 2^-23 > 0) as x rsqrt(x):
+// a few ulp, far below the bf16 rounding that follows.
+__device__ __forceinline__ float bm_sqrt(float x) { return x * rsqrtf(x); }
+
 __device__ __forceinline__ void gauss4_f(const Words4& w, float z[4]) {
-  const float r0 = sqrtf(minus2log_f(word_to_uniform_f(w.x0)));
-  const float r1 = sqrtf(minus2log_f(word_to_uniform_f(w.x2)));
+  const float r0 = bm_sqrt(minus2log_f(word_to_uniform_f(w.x0)));
+  const float r1 = bm_sqrt(minus2log_f(word_to_uniform_f(w.x2)));
   float s0, c0, s1, c1;
   __sincosf(6.283185307179586f * (word_to_uniform_f(w.x1) - 0.5f), &s0, &c0);
   __sincosf(6.283185307179586f * (word_to_uniform_f(w.x3) - 0.5f), &s1, &c1);

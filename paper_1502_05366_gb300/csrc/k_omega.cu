@@ -11,16 +11,17 @@
 // memory descriptors.  Arithmetic as in k_tc.cu: a0 w0 + a1 w0 with
 // x ~ a0 + a1 (16 significant bits) and Omega bf16-exact.
 //
-// Roles (640 threads, one CTA per SM, persistent stream-K over the flattened
+// Roles (896 threads, one CTA per SM, persistent stream-K over the flattened
 // (unit, k-chunk) space):
 //   warp 0       TMA producer: fp32 A block (256 rows x 32) into a 3-stage ring
 //   warp 1       MMA issuer (one thread) and TMEM owner
 //   warps 4-11   converters: fp32 rows -> bf16 hi/lo rows (64-byte swizzled,
 //                K-major) in a 2-stage operand ring; then the epilogue of
 //                their TMEM lane quadrant of their tile
-//   warps 12-19  generators: the bf16 Omega tile (same layout) in the operand
-//                ring; one thread makes 8 K-consecutive quads and stores each
-//                of its 4 columns as one 16-byte chunk
+//   warps 12-27  generators: the bf16 Omega tile (same layout) in the operand
+//                ring; one thread makes 4 K-consecutive quads (2 L units per
+//                stage, so that every generator thread has work) and stores
+//                each of its 4 columns as one 8-byte half chunk
 // Every wait is bounded (about 1 s of clock); on expiry the kernel records
 // RSVD_ERR_TIMEOUT, all roles leave, the producer drains its copies in flight
 // and TMEM is freed.
@@ -43,8 +44,8 @@ constexpr int B_ST = 2;                       // bf16 operand stages
 constexpr int F_BYTES = OUNIT * OBK * 4;      // 32 KB
 constexpr int AT_BYTES = OBM * OBK * 2;       // 8 KB: one tile, hi or lo
 constexpr int NCONV = 8;                      // warps 4..11
-constexpr int NGEN = 8;                       // warps 12..19
-constexpr int OTHREADS = 32 * (12 + NGEN);    // 640
+constexpr int NGEN = 16;                      // warps 12..27
+constexpr int OTHREADS = 32 * (12 + NGEN);    // 896
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_STRIDE = 256;          // TMEM column of the second accumulator
 
@@ -62,6 +63,9 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
                "r"(d)
                : "memory");
+}
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 // D[tmem] (+)= A[smem desc] * B[smem desc], kind::f16 (bf16 in, fp32 accumulate).
 __device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
   } else if (warp >= 12 && warp < 12 + NGEN) {
     // ------------------------- Omega generator warps --------------------------
     const int gt = threadIdx.x - 12 * 32;   // 0 .. 32 NGEN - 1
-    const int nunits = L;                   // (L / 4 quads) x (4 chunks of 8 K-rows)
+    const int nunits = 2 * L;               // (L / 4 quads) x (8 groups of 4 K-rows)
     int64_t kc = it0 % P.kiters;
     int bs = 0;
     uint32_t bph = 0;
@@ -324,16 +328,14 @@ __global__ void __launch_bounds__(OTHREADS, 1)
       if (!mbar_wait(&bdone[bs], bph ^ 1u, abort_flag, P.d_info)) break;
       const uint32_t wb = smem_u32(bring + bs * BSB + 4 * AT_BYTES);
       for (int u = gt; u < nunits; u += NGEN * 32) {
-        const int kk8 = u & 3, qd = u >> 2;
-        uint32_t pk[4][4];
+        const int kk4 = u & 7, qd = u >> 3;
+        uint32_t pk[4][2];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) pk[c][w] = 0u;
+        for (int c = 0; c < 4; ++c) pk[c][0] = pk[c][1] = 0u;
         if (4 * qd < P.lvalid) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int64_t krow = kc * OBK + kk8 * 8 + e;
+          for (int e = 0; e < 4; ++e) {
+            const int64_t krow = kc * OBK + kk4 * 4 + e;
             float z[4] = {0.f, 0.f, 0.f, 0.f};
             if (krow < P.K) OmegaGen<float>::quad(P.seed, (uint32_t)krow, (uint32_t)qd, z);
 #pragma unroll
@@ -346,8 +348,8 @@ __global__ void __launch_bounds__(OTHREADS, 1)
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const uint32_t o = sw64_off((uint32_t)(4 * qd + c), (uint32_t)kk8);
-          st_shared_v4(wb + o, pk[c][0], pk[c][1], pk[c][2], pk[c][3]);
+          const uint32_t o = sw64_off((uint32_t)(4 * qd + c), (uint32_t)(kk4 >> 1)) + 8u * (kk4 & 1);
+          st_shared_v2(wb + o, pk[c][0], pk[c][1]);
         }
       }
       fence_proxy_async();
