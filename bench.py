@@ -55,10 +55,11 @@ def a_pass_bytes(m, n, elem=4):
 
 
 # Algorithmic work of one launch of each kernel class at the bench workload:
-# HBM bytes for the passes over A (one read of the m x n fp32 matrix), FP64
-# flops for the pivoted QR and the triangular solves.
+# HBM bytes for the passes over A (one read of the m x n fp32 matrix),
+# FP64-equivalent flops for the pivoted QR and the triangular solves.
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_SM = 4   # 2 DFMA per clock per SM (1.25 TFLOP/s at 2070 MHz, 152 SMs)
+FP32_LANES_PER_SM = 128    # FP32 instructions issued per clock per SM (4 x 32)
 
 
 def cpqr_flops(r, n, k):
@@ -105,18 +106,28 @@ def class_roofline(cls, trace, cfg, peaks, peak_kind, sm_mhz):
         return base
     mhz = sm_mhz or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = SM_COUNT * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
-    # two launches per step in both classes; flops averaged over the pair
+    # two launches per step in both classes; flops averaged over the pair.
+    # Both run in double-float on the FP32 pipe: the peak is the FP32 issue
+    # rate times FP64-equivalent flops per FP32 instruction of the kernel's
+    # inner operation (CPQR: 4 flops per entry-step in 27 instructions; solve:
+    # 2 flops per multiply-add in 16 instructions).
     if cls == "cpqr":
         flops = cpqr_flops(l, n, k) + cpqr_flops(k, m, k)    # ID of B, row ID of C^T
+        per_instr = 4.0 / 27.0
     elif cls == "solve":
         flops = solve_flops(k, n - k) + solve_flops(k, k)      # T = S11^-1 S12, U_cur
+        per_instr = 2.0 / 16.0
     else:
         return dict(base, bound=None, note="no work model for this class")
+    df_peak = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 * per_instr / 1e12
     achieved = (flops / 2.0) / (avg_ms * 1e-3) / 1e12
-    base.update({"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                 "frac": achieved / fp64_peak,
-                 "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x %.0f MHz (measured SM clock)" % mhz,
-                 "work_per_launch": "FP64 flops of the launch (both launches averaged)"})
+    base.update({"bound": "alu", "achieved": achieved, "peak": df_peak,
+                 "unit": "TFLOP/s (FP64-equivalent, double-float)",
+                 "frac": achieved / df_peak,
+                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (measured) x "
+                                "%.3f FP64-equivalent flops per FP32 instruction" % (mhz, per_instr),
+                 "fp64_pipe_peak": fp64_peak,
+                 "work_per_launch": "FP64-equivalent flops of the launch (both launches averaged)"})
     return base
 
 
