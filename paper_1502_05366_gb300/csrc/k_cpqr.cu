@@ -340,6 +340,40 @@ __device__ __forceinline__ void df_fast_two_sum(float a, float b, float& s, floa
   e = __fsub_rn(b, __fsub_rn(s, a));
 }
 __device__ __forceinline__ double df_to_d(float h, float l) { return (double)h + (double)l; }
+// (a_h + a_l) + (b_h + b_l) as a normalised pair.
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
+  float s, e;
+  df_two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  df_fast_two_sum(s, e, h, l);
+}
+// (a_h + a_l)(b_h + b_l) as a normalised pair (the a_l b_l term dropped).
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  df_fast_two_sum(p, e, h, l);
+}
+// sqrt of a positive pair: y = sqrtf(a_h), one Newton step y + (a - y^2) / (2y)
+// with the residual a - y^2 formed exactly (TwoProduct).
+__device__ __forceinline__ void df_sqrt(float ah, float al, float& h, float& l) {
+  const float y = sqrtf(ah);
+  const float yy = __fmul_rn(y, y);
+  const float ye = __fmaf_rn(y, y, -yy);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(ah, yy), ye), al);
+  const float c = __fdiv_rn(r, __fmul_rn(2.f, y));
+  df_fast_two_sum(y, c, h, l);
+}
+// 1 / (b_h + b_l): y = 1 / b_h, one Newton step y + y (1 - b y) with 1 - b y
+// formed from the exact product b_h y.
+__device__ __forceinline__ void df_recip(float bh, float bl, float& h, float& l) {
+  const float y = __frcp_rn(bh);
+  const float p = __fmul_rn(bh, y);
+  const float pe = __fmaf_rn(bh, y, -p);
+  const float r = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(bl, y));
+  df_fast_two_sum(y, __fmul_rn(y, r), h, l);
+}
 // Warp sum of double-float partial sums (s, e): TwoSum on the leading parts,
 // errors accumulated; every lane ends with the total.
 __device__ __forceinline__ void df_warp_sum(float& s, float& e) {
@@ -436,11 +470,16 @@ __host__ __device__ constexpr int SLOT_STEP() { return RPL <= 8 ? 1 : RPL / 8; }
 
 // One step's dot products, rank-1 updates and norm downdates over the CTA's
 // columns (one warp per column), with S row slots per lane.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 struct CpqrDfCol {
   float* Wh;
   float* Wl;
-  float2* nrm2;
+  float2* nrm2;       // residual norms of columns cbase.. (shared or global memory)
   float* nref;
+  int64_t cbase;
   const float* svh;
   const float* svl;
   int r, j, len;
@@ -449,8 +488,11 @@ struct CpqrDfCol {
   bool zero;
   int lane, warp;
 
+  // Returns (on lane 0) the warp's best two residual norms after the step.
   template <int S, int NWARP>
-  __device__ __forceinline__ void run() const {
+  __device__ __forceinline__ Top2F run() const {
+    const DF none{-1.f, 0.f};
+    Top2F best{none, 0x7fffffffffffffffLL, none};
     const float tol3z = 1.4901161193847656e-08f;   // sqrt(eps_fp64), as in the FP64 kernel
     float vh[S], vl[S];
 #pragma unroll
@@ -460,8 +502,20 @@ struct CpqrDfCol {
       vl[t] = i < len ? svl[i] : 0.f;
     }
     for (int64_t c = c0 + warp; c < c1; c += NWARP) {
+      // the warp's next column into L1 while this one is processed (rows from
+      // j + 1, as needed at the next step too)
+      if (c + NWARP < c1) {
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const int i = lane + 32 * t;
+          if (i < len) {
+            prefetch_l1(Wh + (c + NWARP) * r + j + i);
+            prefetch_l1(Wl + (c + NWARP) * r + j + i);
+          }
+        }
+      }
       if (c == p) continue;                                  // warp-uniform
-      const float2 nc = nrm2[c];
+      const float2 nc = nrm2[c - cbase];
       if (nc.x < 0.f) continue;                              // already pivoted
       float* colh = Wh + c * r + j;
       float* coll = Wl + c * r + j;
@@ -473,7 +527,8 @@ struct CpqrDfCol {
         wl[t] = i < len ? coll[i] : 0.f;
       }
       if (!zero) {
-        float sd = 0.f, ed = 0.f;
+        // Dot2 in two independent chains (even / odd slots), then joined
+        float sd = 0.f, ed = 0.f, sd2 = 0.f, ed2 = 0.f;
 #pragma unroll
         for (int t = 0; t < S; ++t) {
           const float ph = __fmul_rn(vh[t], wh[t]);
@@ -481,8 +536,18 @@ struct CpqrDfCol {
           pe = __fmaf_rn(vh[t], wl[t], pe);
           pe = __fmaf_rn(vl[t], wh[t], pe);
           float e;
-          df_two_sum(sd, ph, sd, e);
-          ed = __fadd_rn(ed, __fadd_rn(e, pe));
+          if (t & 1) {
+            df_two_sum(sd2, ph, sd2, e);
+            ed2 = __fadd_rn(ed2, __fadd_rn(e, pe));
+          } else {
+            df_two_sum(sd, ph, sd, e);
+            ed = __fadd_rn(ed, __fadd_rn(e, pe));
+          }
+        }
+        {
+          float e;
+          df_two_sum(sd, sd2, sd, e);
+          ed = __fadd_rn(ed, __fadd_rn(ed2, e));
         }
         df_warp_sum(sd, ed);
         float dh, dl;
@@ -521,7 +586,7 @@ struct CpqrDfCol {
         df_two_sum(nc.x, -ph, sh, se);
         se = __fadd_rn(se, __fsub_rn(nc.y, pe));
         df_fast_two_sum(sh, se, nh, nl);
-        recompute = (!(nh > tol3z * nref[c]) && j + 1 < r) ? 1 : 0;
+        recompute = (!(nh > tol3z * nref[c - cbase]) && j + 1 < r) ? 1 : 0;
       }
       recompute = __shfl_sync(0xffffffffu, recompute, 0);
       if (recompute) {
@@ -533,12 +598,72 @@ struct CpqrDfCol {
         }
         df_warp_sum(qs, qe);
         df_fast_two_sum(qs, qe, nh, nl);
-        if (lane == 0) nref[c] = nh;
+        if (lane == 0) nref[c - cbase] = nh;
       }
-      if (lane == 0) nrm2[c] = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
+      if (lane == 0) {
+        const float2 nv = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
+        nrm2[c - cbase] = nv;
+        best = merge_top2f(best, Top2F{DF{nv.x, nv.y}, c, none});
+      }
     }
+    // the warp's first column of the next step into L1 (stored rows j + 1 ..)
+    {
+      const int64_t c = c0 + warp;
+      if (c < c1) {
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const int i = lane + 32 * t + 1;
+          if (i < len) {
+            prefetch_l1(Wh + c * r + j + i);
+            prefetch_l1(Wl + c * r + j + i);
+          }
+        }
+      }
+    }
+    return best;
   }
 };
+
+// Warp-wide best two of (value, index) proposals; every lane ends with it.
+__device__ __forceinline__ Top2F warp_top2f(Top2F v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Top2F w;
+    w.b1.h = __shfl_xor_sync(0xffffffffu, v.b1.h, o);
+    w.b1.l = __shfl_xor_sync(0xffffffffu, v.b1.l, o);
+    w.i1 = __shfl_xor_sync(0xffffffffu, v.i1, o);
+    w.b2.h = __shfl_xor_sync(0xffffffffu, v.b2.h, o);
+    w.b2.l = __shfl_xor_sync(0xffffffffu, v.b2.l, o);
+    v = merge_top2f(v, w);
+  }
+  return v;
+}
+
+// Grid barrier entered by one warp of each CTA (lane 0 arrives and polls);
+// false on every lane when the wait ran out.
+// Arrival is a release-ordered reduction (no returned value to wait for; the
+// CTA's proposal, written by the same thread before it, is visible to whoever
+// acquires the count); the poll is an acquire load, which orders the reads of
+// other CTAs' proposals.
+__device__ __forceinline__ bool grid_barrier_warp(unsigned* bar, unsigned target, int* d_info) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    const long long t0 = clock64();
+    unsigned it = 0;
+    while (ld_acquire_u32(bar) < target) {
+      if (((++it) & 1023u) == 0 && clock64() - t0 > SPIN_LIMIT_CYCLES) {
+        set_info(d_info, RSVD_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  // lanes other than 0 read the proposals after this; order them after lane
+  // 0's acquire
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
 
 // W is COLUMN-major here (element (i, c) in Wh[c*r + i], Wl[c*r + i]), so one
 // warp owns a column per iteration: lane l holds rows j + l + 32 t
@@ -568,21 +693,49 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
   constexpr int NWARP = NT / 32;
   float* Wh = reinterpret_cast<float*>(a.W);
   float* Wl = Wh + (int64_t)r * n;
-  float2* __restrict__ nrm2 = reinterpret_cast<float2*>(a.nrm);
-  float* __restrict__ nref = reinterpret_cast<float*>(nrm2 + n);
+  // residual norms of this CTA's columns: in shared memory after the
+  // Householder vector when they fit (a.nrm_local), else in global memory
+  const int64_t cbase = a.nrm_local ? c0 : 0;
+  float2* nrm2;
+  float* nref;
+  if (a.nrm_local) {
+    nrm2 = reinterpret_cast<float2*>(svh + 2 * a.r);
+    nref = reinterpret_cast<float*>(nrm2 + per);
+  } else {
+    nrm2 = reinterpret_cast<float2*>(a.nrm);
+    nref = reinterpret_cast<float*>(nrm2 + n);
+  }
   float4* __restrict__ pv = reinterpret_cast<float4*>(a.pval);   // (b1h, b1l, b2h, b2l)
   double* __restrict__ diagR = a.diagR;
 
-  // exact initial squared norms, one warp per column
-  for (int64_t c = c0 + warp; c < c1; c += NWARP) {
-    float sh = 0.f, se = 0.f;
-    for (int i = lane; i < r; i += 32) df_acc_sqr(Wh[c * r + i], Wl[c * r + i], sh, se);
-    df_warp_sum(sh, se);
+  __shared__ float s_wt[NWARP][4];          // per-warp best two norms (hi, lo, hi, lo)
+  __shared__ int64_t s_wi[NWARP];           // per-warp best column
+  __shared__ int64_t s_p;                   // this step's pivot column
+  __shared__ float s_g[4];                  // the step's best two norms (for the gaps)
+  __shared__ int s_abort;
+  const DF none{-1.f, 0.f};
+
+  // exact initial squared norms, one warp per column; each warp keeps its best two
+  {
+    Top2F best{none, 0x7fffffffffffffffLL, none};
+    for (int64_t c = c0 + warp; c < c1; c += NWARP) {
+      float sh = 0.f, se = 0.f;
+      for (int i = lane; i < r; i += 32) df_acc_sqr(Wh[c * r + i], Wl[c * r + i], sh, se);
+      df_warp_sum(sh, se);
+      if (lane == 0) {
+        float h, l;
+        df_fast_two_sum(sh, se, h, l);
+        nrm2[c - cbase] = make_float2(h, l);
+        nref[c - cbase] = h;
+        best = merge_top2f(best, Top2F{DF{h, l}, c, none});
+      }
+    }
     if (lane == 0) {
-      float h, l;
-      df_fast_two_sum(sh, se, h, l);
-      nrm2[c] = make_float2(h, l);
-      nref[c] = h;
+      s_wt[warp][0] = best.b1.h;
+      s_wt[warp][1] = best.b1.l;
+      s_wt[warp][2] = best.b2.h;
+      s_wt[warp][3] = best.b2.l;
+      s_wi[warp] = best.i1;
     }
   }
   if (blockIdx.x == 0)
@@ -590,90 +743,110 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
       a.J[c] = (int32_t)c;
       a.where[c] = c;
     }
+  if (tid == 0) s_abort = 0;
   __syncthreads();
 
-  const DF none{-1.f, 0.f};
   for (int j = 0; j < a.k; ++j) {
-    Top2F loc{none, 0x7fffffffffffffffLL, none};
-    for (int64_t c = c0 + tid; c < c1; c += NT) {
-      const float2 x = nrm2[c];
-      if (x.x >= 0.f) loc = merge_top2f(loc, Top2F{DF{x.x, x.y}, c, none});
-    }
-    loc = block_top2f<NT>(loc);
-    const int slot = j & 1;
-    if (tid == 0) {
-      pv[(size_t)slot * G + blockIdx.x] = make_float4(loc.b1.h, loc.b1.l, loc.b2.h, loc.b2.l);
-      a.pidx[(size_t)slot * G + blockIdx.x] = loc.i1;
-    }
-    if (!grid_barrier(a.bar, (unsigned)(j + 1) * (unsigned)G, a.d_info)) return;
-    Top2F g{none, 0x7fffffffffffffffLL, none};
-    for (int b = tid; b < G; b += NT) {
-      const float4 q = __ldcg(pv + (size_t)slot * G + b);
-      g = merge_top2f(g, Top2F{DF{q.x, q.y},
-                               __ldcg(reinterpret_cast<const long long*>(a.pidx) +
-                                      (size_t)slot * G + b),
-                               DF{q.z, q.w}});
-    }
-    g = block_top2f<NT>(g);
-    const int64_t p = g.i1;
-    if (p < 0 || p >= n) {
-      set_info(a.d_info, RSVD_ERR_NUMERIC);
-      return;
-    }
     const int len = r - j;
-    // ---- warp 0: Householder vector of the pivot column (rows j..r-1) ----
+    // ---- warp 0: CTA proposal, grid barrier, global pivot, Householder vector ----
     if (warp == 0) {
-      float ss = 0.f, se = 0.f;
-      for (int i = lane; i < len; i += 32) {
-        const float xh = __ldcg(Wh + p * r + j + i), xl = __ldcg(Wl + p * r + j + i);
-        svh[i] = xh;
-        svl[i] = xl;
-        df_acc_sqr(xh, xl, ss, se);
-      }
-      df_warp_sum(ss, se);
+      Top2F v{none, 0x7fffffffffffffffLL, none};
+      if (lane < NWARP)
+        v = Top2F{DF{s_wt[lane][0], s_wt[lane][1]}, s_wi[lane], DF{s_wt[lane][2], s_wt[lane][3]}};
+      v = warp_top2f(v);
+      const int slot = j & 1;
       if (lane == 0) {
-        const double nx2 = (double)ss + (double)se;
-        const double nx = sqrt(nx2);
-        const double x0 = df_to_d(svh[0], svl[0]);
-        const double beta = (x0 >= 0.0) ? -nx : nx;
-        s_beta = beta;
-        if (nx > 0.0) {
-          const double v0 = x0 - beta;
-          float h0, l0;
-          d_to_df(v0, h0, l0);
-          svh[0] = h0;
-          svl[0] = l0;
-          float th, tl;
-          d_to_df(2.0 / (nx2 - x0 * x0 + v0 * v0), th, tl);
-          s_th = th;
-          s_tl = tl;
-          s_zero = 0;
+        pv[(size_t)slot * G + blockIdx.x] = make_float4(v.b1.h, v.b1.l, v.b2.h, v.b2.l);
+        a.pidx[(size_t)slot * G + blockIdx.x] = v.i1;
+      }
+      if (!grid_barrier_warp(a.bar, (unsigned)(j + 1) * (unsigned)G, a.d_info)) {
+        if (lane == 0) s_abort = 1;
+      } else {
+        Top2F g{none, 0x7fffffffffffffffLL, none};
+        for (int b0 = 0; b0 < G; b0 += 4 * 32) {     // 4 loads in flight per lane
+          float4 q[4];
+          long long qi[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int b = b0 + u * 32 + lane;
+            if (b < G) {
+              q[u] = __ldcg(pv + (size_t)slot * G + b);
+              qi[u] = __ldcg(reinterpret_cast<const long long*>(a.pidx) + (size_t)slot * G + b);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (b0 + u * 32 + lane < G)
+              g = merge_top2f(g, Top2F{DF{q[u].x, q[u].y}, qi[u], DF{q[u].z, q[u].w}});
+        }
+        g = warp_top2f(g);
+        const int64_t p = g.i1;
+        if (p < 0 || p >= n) {
+          if (lane == 0) {
+            set_info(a.d_info, RSVD_ERR_NUMERIC);
+            s_abort = 1;
+          }
         } else {
-          s_th = 0.f;
-          s_tl = 0.f;
-          s_zero = 1;
+          // the pivot column into shared memory (all loads independent), then
+          // its squared norm
+#pragma unroll 8
+          for (int i = lane; i < len; i += 32) {
+            svh[i] = __ldcg(Wh + p * r + j + i);
+            svl[i] = __ldcg(Wl + p * r + j + i);
+          }
+          __syncwarp();
+          float ss = 0.f, se = 0.f;
+          for (int i = lane; i < len; i += 32) df_acc_sqr(svh[i], svl[i], ss, se);
+          df_warp_sum(ss, se);
+          __syncwarp();
+          if (lane == 0) {
+            s_p = p;
+            // reflector scalars in double-float: nx = sqrt(nx2), beta = -sign(x0) nx,
+            // v0 = x0 - beta, tau = 2 / (nx2 - x0^2 + v0^2) = 1 / (nx (nx + |x0|))
+            float n2h, n2l;
+            df_fast_two_sum(ss, se, n2h, n2l);
+            const float x0h = svh[0], x0l = svl[0];
+            if (n2h > 0.f) {
+              float nxh, nxl;
+              df_sqrt(n2h, n2l, nxh, nxl);
+              const bool pos = (x0h > 0.f) || (x0h == 0.f && x0l >= 0.f);
+              // v0 = x0 + sign(x0) nx (no cancellation)
+              float vh, vl;
+              df_add(x0h, x0l, pos ? nxh : -nxh, pos ? nxl : -nxl, vh, vl);
+              svh[0] = vh;
+              svl[0] = vl;
+              // tau = 1 / (nx (nx + |x0|))
+              float ah, al;
+              df_add(nxh, nxl, pos ? x0h : -x0h, pos ? x0l : -x0l, ah, al);
+              float dh, dl;
+              df_mul(nxh, nxl, ah, al, dh, dl);
+              float th, tl;
+              df_recip(dh, dl, th, tl);
+              s_th = th;
+              s_tl = tl;
+              s_beta = pos ? -((double)nxh + (double)nxl) : ((double)nxh + (double)nxl);
+              s_zero = 0;
+            } else {
+              s_beta = 0.0;
+              s_th = 0.f;
+              s_tl = 0.f;
+              s_zero = 1;
+            }
+            s_g[0] = g.b1.h;
+            s_g[1] = g.b1.l;
+            s_g[2] = g.b2.h;
+            s_g[3] = g.b2.l;
+          }
         }
       }
     }
     __syncthreads();
+    if (s_abort) return;
+    const int64_t p = s_p;
     const float tauh = s_th, taul = s_tl;
     const bool zero = s_zero != 0;
-    // the column pass specialised on the row slots in use, so that no
-    // instruction is spent on slots beyond the active rows
-    const int nt = (len + 31) >> 5;
-    CpqrDfCol cp{Wh, Wl, nrm2, nref, svh, svl, r, j, len, p, c0, c1, tauh, taul, zero, lane, warp};
-    switch ((nt + SLOT_STEP<RPL>() - 1) / SLOT_STEP<RPL>()) {
-      case 1: cp.template run<1 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 2: cp.template run<2 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 3: cp.template run<3 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 4: cp.template run<4 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 5: cp.template run<5 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 6: cp.template run<6 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 7: cp.template run<7 * SLOT_STEP<RPL>(), NWARP>(); break;
-      default: cp.template run<8 * SLOT_STEP<RPL>(), NWARP>(); break;
-    }
-    if (p >= c0 && p < c1 && tid == 0) nrm2[p] = make_float2(-1.f, 0.f);
-    if (blockIdx.x == 0 && tid == 0) {
+    // pivot bookkeeping (block 0, warp 1), off the path to the next barrier
+    if (blockIdx.x == 0 && warp == 1 && lane == 0) {
       diagR[j] = s_beta;
       const int64_t P = a.where[p];
       const int32_t cj = a.J[j];
@@ -682,12 +855,36 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
       a.J[j] = (int32_t)p;
       a.where[p] = j;
       if (a.gaps) {
-        const double n1 = sqrt((double)g.b1.h + (double)g.b1.l);
-        a.gaps[j] = (g.b2.h < 0.f)
-                        ? __longlong_as_double(0x7ff0000000000000LL)
-                        : (n1 > 0.0 ? (n1 - sqrt((double)g.b2.h + (double)g.b2.l)) / n1 : 0.0);
+        const double n1 = sqrt((double)s_g[0] + (double)s_g[1]);
+        a.gaps[j] = (s_g[2] < 0.f) ? __longlong_as_double(0x7ff0000000000000LL)
+                                   : (n1 > 0.0 ? (n1 - sqrt((double)s_g[2] + (double)s_g[3])) / n1
+                                               : 0.0);
       }
     }
+    // the column pass specialised on the row slots in use, so that no
+    // instruction is spent on slots beyond the active rows
+    const int nt = (len + 31) >> 5;
+    CpqrDfCol cp{Wh, Wl, nrm2, nref, cbase, svh, svl, r, j, len, p, c0, c1, tauh, taul, zero,
+                 lane, warp};
+    Top2F best;
+    switch ((nt + SLOT_STEP<RPL>() - 1) / SLOT_STEP<RPL>()) {
+      case 1: best = cp.template run<1 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 2: best = cp.template run<2 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 3: best = cp.template run<3 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 4: best = cp.template run<4 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 5: best = cp.template run<5 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 6: best = cp.template run<6 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 7: best = cp.template run<7 * SLOT_STEP<RPL>(), NWARP>(); break;
+      default: best = cp.template run<8 * SLOT_STEP<RPL>(), NWARP>(); break;
+    }
+    if (lane == 0) {
+      s_wt[warp][0] = best.b1.h;
+      s_wt[warp][1] = best.b1.l;
+      s_wt[warp][2] = best.b2.h;
+      s_wt[warp][3] = best.b2.l;
+      s_wi[warp] = best.i1;
+    }
+    if (p >= c0 && p < c1 && tid == 0) nrm2[p - cbase] = make_float2(-1.f, 0.f);
     __syncthreads();
   }
 }
@@ -695,13 +892,6 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
 template <int RPL, int NT>
 static cudaError_t launch_cpqr_df_t(const CpqrArgs& a, int sms, cudaStream_t s) {
   auto kern = cpqr_df_kernel<RPL, NT>;
-  const size_t dyn = (size_t)a.r * 2 * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, dyn);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // eight SMs are left to the Jacobi SVD (one 8-CTA cluster) that runs beside
   // the CPQR on another stream in the combined SVD + ID/CUR call
   int64_t G = sms > 16 ? sms - 8 : (sms > 1 ? sms - 1 : 1);
@@ -709,9 +899,27 @@ static cudaError_t launch_cpqr_df_t(const CpqrArgs& a, int sms, cudaStream_t s) 
   if (G > byn) G = byn;
   if (G > 1024) G = 1024;
   if (G < 1) G = 1;
+  // the CTA's residual norms (12 bytes a column) go to shared memory when they
+  // fit beside the Householder vector
+  const int64_t per = ceil_div(a.n, G);
+  size_t dyn = (size_t)a.r * 2 * sizeof(float);
+  const size_t local = (size_t)per * (sizeof(float2) + sizeof(float));
+  const bool nrm_local = dyn + local <= (size_t)160 * 1024;
+  if (nrm_local) dyn += local;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  if (e != cudaSuccess) return e;
+  if (dyn > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, dyn);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
   e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   CpqrArgs b = a;
+  b.nrm_local = nrm_local ? 1 : 0;
   void* args[] = {(void*)&b};
   count_launch();
   const int tr = trace_begin(RSVD_TRACE_CPQR, s);
@@ -724,7 +932,7 @@ cudaError_t launch_cpqr_df(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   (void)grid_out;
   if (a.r > 1024) return cudaErrorInvalidValue;
   const int sms = device_sm_count();
-  if (a.r <= 256) return launch_cpqr_df_t<8, 1024>(a, sms, s);
+  if (a.r <= 256) return launch_cpqr_df_t<8, 768>(a, sms, s);
   return launch_cpqr_df_t<32, 256>(a, sms, s);
 }
 

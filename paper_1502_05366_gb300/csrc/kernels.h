@@ -131,8 +131,8 @@ struct CpqrArgs {
   double* diagR;    // k: diagonal of S (the Householder betas)
   unsigned* bar;    // 1 counter, zeroed by the launcher
   int* d_info;
-  int tpc;          // set by the launcher: threads per column (FP64 kernel) or
-                    // columns per pass (double-float kernel)
+  int tpc;          // set by the launcher: threads per column (FP64 kernel)
+  int nrm_local;    // set by the launcher: residual norms in shared memory (double-float kernel)
 };
 cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s);
 // Double-float arithmetic on the same working area reinterpreted as two float
