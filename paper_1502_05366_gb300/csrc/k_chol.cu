@@ -13,7 +13,7 @@
 namespace rsvd {
 
 namespace {
-constexpr int CT = 512;
+constexpr int CT = 256;   // threads (a 255-register budget keeps the unrolled panel code in registers)
 constexpr size_t SMEM_LIMIT = 212 * 1024;   // dynamic part; static arrays take <= 9 KB
 template <typename T> __device__ __forceinline__ T eps_of();
 template <> __device__ __forceinline__ float eps_of<float>() { return 5.9604645e-8f; }
@@ -181,7 +181,7 @@ __device__ void inv_upper_blocked(T* S, int l, T* ttmp) {
   __shared__ T Rd[NB][NB + 1];
   const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
   const int nb = (l + NB - 1) / NB;
-  constexpr int MAXE = 16;
+  constexpr int MAXE = 32;   // ne <= 32 l <= MAXE * 256 threads for l <= 256
   for (int Ib = nb - 1; Ib >= 0; --Ib) {
     const int r0 = Ib * NB, rb = min(NB, l - r0);
     const int ncol = l - r0;
@@ -243,16 +243,238 @@ __device__ void inv_upper_blocked(T* S, int l, T* ttmp) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// fp32 variants on a padded shared-memory matrix (leading dimension ld, a
+// multiple of 4 with ld % 32 == 4, zero padding), so that 4-wide rows load as
+// one conflict-free float4 and every FMA-heavy phase runs on 4 x 4 register
+// tiles spread over all threads.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int chol_ld(int l) {
+  int ld = (l + 3) & ~3;
+  while ((ld & 31) != 4) ld += 4;
+  return ld;
+}
+
+// Upper-triangle tile (ti, tc), tc >= ti, of linear index u in row-major order
+// over an nT x nT tile grid.
+__device__ __forceinline__ void tri_tile(int u, int nT, int* ti, int* tc) {
+  const float b = 2.0f * nT + 1.0f;
+  int r = (int)((b - sqrtf(b * b - 8.0f * (float)u)) * 0.5f);
+  if (r < 0) r = 0;
+  if (r > nT - 1) r = nT - 1;
+  while (r > 0 && r * nT - (r * (r - 1)) / 2 > u) --r;
+  while (r + 1 < nT && (r + 1) * nT - ((r + 1) * r) / 2 <= u) ++r;
+  *ti = r;
+  *tc = r + (u - (r * nT - (r * (r - 1)) / 2));
+}
+
+__device__ void chol_tiled(float* S, int l, int ld, float thr, int* s_fail) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nthr = blockDim.x * blockDim.y;
+  for (int p0 = 0; p0 < l; p0 += NB) {
+    const int pb = min(NB, l - p0);
+    if (warp == 0) {   // (a) diagonal block in registers (lane c holds column c)
+      float d[NB];
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        d[i] = (lane < pb && i <= lane) ? S[(p0 + i) * ld + p0 + lane] : 0.f;
+      int failed = -1;
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj) {
+        if (jj < pb && failed < 0) {
+          const float piv = __shfl_sync(0xffffffffu, d[jj], jj);
+          if (!(piv > thr)) {
+            failed = jj;
+          } else {
+            const float rr = sqrtf(piv);
+            float rj = d[jj];
+            if (lane == jj) rj = rr;
+            else if (lane > jj) rj = rj / rr;
+            d[jj] = rj;
+#pragma unroll
+            for (int i = jj + 1; i < NB; ++i) {
+              const float ri = __shfl_sync(0xffffffffu, rj, i);
+              if (lane >= i) d[i] -= ri * rj;
+            }
+          }
+        }
+      }
+      if (failed < 0) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+          if (lane < pb && i <= lane) S[(p0 + i) * ld + p0 + lane] = d[i];
+      } else if (lane == 0) {
+        *s_fail = p0 + failed;
+      }
+    }
+    __syncthreads();
+    if (*s_fail >= 0) return;
+    const int c0 = p0 + pb, nt = l - c0;
+    if (nt <= 0) return;
+    // (b) X = R_pp^{-T} S(p0:p0+pb, c0:l), forward substitution per column
+    for (int c = c0 + tid; c < l; c += nthr) {
+      float x[NB];
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        if (i < pb) {
+          float acc = S[(p0 + i) * ld + c];
+#pragma unroll
+          for (int t = 0; t < i; ++t) acc -= S[(p0 + t) * ld + p0 + i] * x[t];
+          x[i] = acc / S[(p0 + i) * ld + p0 + i];
+        } else {
+          x[i] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i < pb) S[(p0 + i) * ld + c] = x[i];
+    }
+    __syncthreads();
+    // (c) trailing upper triangle S(i, c) -= sum_t X(t, i) X(t, c), 4 x 4 tiles
+    // over the upper-triangular tile grid only, float4 row loads
+    const int nT = (nt + 3) / 4;
+    const int ntiles = nT * (nT + 1) / 2;
+    for (int u = tid; u < ntiles; u += nthr) {
+      int ti, tc;
+      tri_tile(u, nT, &ti, &tc);
+      const int i0 = c0 + 4 * ti, k0 = c0 + 4 * tc;
+      float acc[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[q][w] = 0.f;
+#pragma unroll 4
+      for (int t = 0; t < pb; ++t) {
+        const float* row = S + (p0 + t) * ld;
+        const float4 xi = *reinterpret_cast<const float4*>(row + i0);
+        const float4 xc = *reinterpret_cast<const float4*>(row + k0);
+        const float a4[4] = {xi.x, xi.y, xi.z, xi.w};
+        const float b4[4] = {xc.x, xc.y, xc.z, xc.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[q][w] = fmaf(a4[q], b4[w], acc[q][w]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int i = i0 + q, c = k0 + w;
+          if (i < l && c < l && c >= i) S[i * ld + c] -= acc[q][w];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// In-place inverse of the upper-triangular R in S (padded ld), block rows
+// from the bottom:  T = E_I - R(I, I+1:) X(I+1:, :) with the product on 4 x 4
+// register tiles (K range clipped to the tile's columns, X upper triangular),
+// then X(I, :) = R_II^{-1} T by back substitution per column.
+__device__ void inv_upper_tiled(float* S, int l, int ld) {
+  __shared__ float Rd[NB][NB + 1];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
+  // the strictly lower triangle holds Gram entries: zero it (X is upper triangular)
+  for (int e = tid; e < l * l; e += nthr) {
+    const int i = e / l, c = e - i * l;
+    if (c < i) S[i * ld + c] = 0.f;
+  }
+  __syncthreads();
+  const int nb = (l + NB - 1) / NB;
+  for (int Ib = nb - 1; Ib >= 0; --Ib) {
+    const int r0 = Ib * NB, rb = min(NB, l - r0);
+    const int cs = r0 + rb;                 // first column of the off-diagonal part
+    for (int t = tid; t < NB * NB; t += nthr) {
+      const int i = t / NB, c = t - i * NB;
+      Rd[i][c] = (i < rb && c < rb && c >= i) ? S[(r0 + i) * ld + r0 + c] : 0.f;
+    }
+    // T(i, c) = -sum_{t = cs}^{c} R(i, t) X(t, c) for c >= cs, in registers
+    // (at most two 4 x 4 tiles per thread: 8 x ceil((l - cs) / 4) <= 2 nthr)
+    const int nTc = (l - cs + 3) / 4;
+    const int ntiles = (NB / 4) * nTc;
+    float acc[2][4][4];
+    int i0s[2], k0s[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int u = tid + h * nthr;
+      i0s[h] = -1;
+      k0s[h] = 0;
+      if (u < ntiles) {
+        const int ti = u / nTc, tc = u - ti * nTc;
+        const int i0 = r0 + 4 * ti, k0 = cs + 4 * tc;
+        i0s[h] = i0;
+        k0s[h] = k0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[h][q][w] = 0.f;
+        const int tmax = min(l, k0 + 4);
+#pragma unroll 2
+        for (int t = cs; t < tmax; ++t) {
+          float a4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) a4[q] = (i0 + q < r0 + rb) ? S[(i0 + q) * ld + t] : 0.f;
+          const float4 xc = *reinterpret_cast<const float4*>(S + t * ld + k0);
+          const float b4[4] = {xc.x, xc.y, xc.z, xc.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[h][q][w] = fmaf(a4[q], b4[w], acc[h][q][w]);
+        }
+      }
+    }
+    __syncthreads();                          // R(I, I+1:) read by everyone before T lands
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (i0s[h] >= 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int i = i0s[h] + q, c = k0s[h] + w;
+            if (i < r0 + rb && c < l) S[i * ld + c] = -acc[h][q][w];
+          }
+      }
+    }
+    // the diagonal block of T is the identity
+    for (int t = tid; t < rb * rb; t += nthr) {
+      const int i = t / rb, c = t - i * rb;
+      S[(r0 + i) * ld + r0 + c] = (i == c) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    // X(I, c) = R_II^{-1} T(:, c)
+    for (int c = r0 + tid; c < l; c += nthr) {
+      float x[NB];
+#pragma unroll
+      for (int i = NB - 1; i >= 0; --i) {
+        if (i < rb) {
+          float acc2 = S[(r0 + i) * ld + c];
+#pragma unroll
+          for (int t = i + 1; t < NB; ++t)
+            if (t < rb) acc2 -= Rd[i][t] * x[t];
+          x[i] = acc2 / Rd[i][i];
+        } else {
+          x[i] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i < rb) S[(r0 + i) * ld + c] = x[i];
+    }
+    __syncthreads();
+  }
+}
+
+// The body of chol_kernel for a matrix S of leading dimension ld; the shared-
+// memory instance receives S derived from the kernel's shared array, so that
+// after inlining every access to it compiles as a shared-memory access (a
+// generic pointer that might alias global memory would serialise the loads).
 template <typename T>
-__global__ void __launch_bounds__(CT) chol_kernel(CholArgs a) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ T red[32];
-  __shared__ T s_maxdiag, s_dev;
-  __shared__ int s_fail;
+__device__ __forceinline__ void chol_body(const CholArgs& a, T* S, int ld, T* red, T& s_maxdiag,
+                                          T& s_dev, int& s_fail) {
   const int l = a.l, L = a.L;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int tx = threadIdx.x, ty = threadIdx.y, nty = blockDim.y;
-  T* S = a.scratch ? (T*)a.scratch : (T*)dsm;
   const T* G = (const T*)a.G;
   const int64_t ldg = a.ldg;
 
@@ -286,10 +508,14 @@ __global__ void __launch_bounds__(CT) chol_kernel(CholArgs a) {
   int fail = -1;
   for (int attempt = 0; attempt < 12; ++attempt) {
     for (int i = ty; i < l; i += nty)
-      for (int c = tx; c < l; c += 32) S[i * l + c] = G[(int64_t)i * ldg + c] + ((i == c) ? shift : T(0));
+      for (int c = tx; c < ld; c += 32)
+        S[i * ld + c] = c < l ? G[(int64_t)i * ldg + c] + ((i == c) ? shift : T(0)) : T(0);
     if (tid == 0) s_fail = -1;
     __syncthreads();
-    chol_blocked<T>(S, l, tau * maxdiag, &s_fail);
+    if (sizeof(T) == 4 && a.sld > 0)
+      chol_tiled((float*)S, l, ld, (float)(tau * maxdiag), &s_fail);
+    else
+      chol_blocked<T>(S, l, tau * maxdiag, &s_fail);
     fail = s_fail;
     __syncthreads();
     if (fail < 0) break;
@@ -320,18 +546,21 @@ __global__ void __launch_bounds__(CT) chol_kernel(CholArgs a) {
     for (int i = ty; i < L; i += nty)
       for (int c = tx; c < L; c += 32) {
         T v;
-        if (i < l && c < l) v = (c >= i) ? S[i * l + c] : T(0);
+        if (i < l && c < l) v = (c >= i) ? S[i * ld + c] : T(0);
         else v = (i == c) ? T(1) : T(0);
         R[i * L + c] = v;
       }
   }
-  inv_upper_blocked<T>(S, l, a.scratch ? (T*)a.scratch + (size_t)l * l : nullptr);
+  if (sizeof(T) == 4 && a.sld > 0)
+    inv_upper_tiled((float*)S, l, ld);
+  else
+    inv_upper_blocked<T>(S, l, a.scratch ? (T*)a.scratch + (size_t)l * l : nullptr);
   if (a.Rinv) {
     T* Ri = (T*)a.Rinv;
     for (int i = ty; i < L; i += nty)
       for (int c = tx; c < L; c += 32) {
         T v;
-        if (i < l && c < l) v = (c >= i) ? S[i * l + c] : T(0);
+        if (i < l && c < l) v = (c >= i) ? S[i * ld + c] : T(0);
         else v = (i == c) ? T(1) : T(0);
         Ri[i * L + c] = v;
       }
@@ -344,7 +573,7 @@ __global__ void __launch_bounds__(CT) chol_kernel(CholArgs a) {
     for (int kk = tx; kk < L; kk += 32) {
       const int t = j * L + kk;
       float v;
-      if (j < l && kk < l) v = (j >= kk) ? (float)S[kk * l + j] : 0.0f;
+      if (j < l && kk < l) v = (j >= kk) ? (float)S[kk * ld + j] : 0.0f;
       else v = (j == kk) ? 1.0f : 0.0f;
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       const float r1 = v - __bfloat162float(h);
@@ -354,6 +583,25 @@ __global__ void __launch_bounds__(CT) chol_kernel(CholArgs a) {
       lo2[t] = __float2bfloat16_rn(r1 - __bfloat162float(mdl));
     }
   }
+}
+
+// S in shared memory (l x ld) ...
+template <typename T>
+__global__ void __launch_bounds__(CT) chol_kernel(CholArgs a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ T red[32];
+  __shared__ T s_maxdiag, s_dev;
+  __shared__ int s_fail;
+  chol_body<T>(a, reinterpret_cast<T*>(dsm), a.sld > 0 ? a.sld : a.l, red, s_maxdiag, s_dev,
+               s_fail);
+}
+// ... or in the global scratch (large l)
+template <typename T>
+__global__ void __launch_bounds__(CT) chol_kernel_global(CholArgs a) {
+  __shared__ T red[32];
+  __shared__ T s_maxdiag, s_dev;
+  __shared__ int s_fail;
+  chol_body<T>(a, (T*)a.scratch, a.l, red, s_maxdiag, s_dev, s_fail);
 }
 
 // Racc <- R * Racc for upper-triangular L x L matrices (through tmp).
@@ -373,8 +621,14 @@ template <typename T>
 cudaError_t launch_chol(const CholArgs& a, cudaStream_t s) {
   const size_t bytes = (size_t)a.l * a.l * sizeof(T);
   CholArgs b = a;
+  b.sld = 0;
   size_t dyn = 0;
-  if (bytes <= SMEM_LIMIT) {
+  const size_t tiled = (size_t)a.l * chol_ld(a.l) * sizeof(float);
+  if (sizeof(T) == 4 && tiled <= SMEM_LIMIT) {   // fp32 register-tiled path
+    b.scratch = nullptr;
+    b.sld = chol_ld(a.l);
+    dyn = tiled;
+  } else if (bytes <= SMEM_LIMIT) {
     b.scratch = nullptr;
     dyn = bytes;
   } else if (a.scratch == nullptr) {
@@ -386,7 +640,10 @@ cudaError_t launch_chol(const CholArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   const int tr_ = trace_begin(RSVD_TRACE_CHOL, s);
-  chol_kernel<T><<<1, dim3(32, CT / 32), dyn, s>>>(b);
+  if (b.scratch)
+    chol_kernel_global<T><<<1, dim3(32, CT / 32), 0, s>>>(b);
+  else
+    chol_kernel<T><<<1, dim3(32, CT / 32), dyn, s>>>(b);
   count_launch();
   trace_end(tr_, s);
   return cudaGetLastError();
