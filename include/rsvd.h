@@ -178,6 +178,24 @@ rsvd_status rsvd_svd_id_cur(int64_t m, int64_t n, int k, int p, int q, uint64_t 
                             void* work, size_t work_bytes, int* d_info, void* stream,
                             const rsvd_opts* opts);
 
+/* -------------------------------------------------------------------------
+ * rsvd_svd_id_cur_host - rsvd_svd_id_cur with A in host memory.
+ * A_host (m x lda, same layout as A; page-locked for the copy to overlap) is
+ * copied into the caller's device buffer A, which holds A on return.  On the
+ * tensor-core path the copy runs in row chunks on an auxiliary stream and the
+ * sketch Y = A Omega (Fig. 1 step 2; its rows are independent) processes each
+ * chunk as it lands; the later passes need all of A.  Workspace size as
+ * rsvd_svd_id_cur_workspace_size.  Outputs and errors as rsvd_svd_id_cur;
+ * RSVD_ERR_INVALID_ARG when A_host is NULL.
+ * ------------------------------------------------------------------------- */
+rsvd_status rsvd_svd_id_cur_host(int64_t m, int64_t n, int k, int p, int q, uint64_t seed,
+                                 int dtype, const void* A_host, void* A, int64_t lda,
+                                 void* U, int64_t ldu, double* S, void* V, int64_t ldv,
+                                 int32_t* J, void* T, int64_t ldt,
+                                 int32_t* Jc, int32_t* Ir, void* Ucur, int64_t lducur,
+                                 void* work, size_t work_bytes, int* d_info, void* stream,
+                                 const rsvd_opts* opts);
+
 /* =========================================================================
  * Step-level entry points (one per step of the path; same conventions).
  * ========================================================================= */

@@ -91,6 +91,10 @@ _SIGS = {
     "rsvd_kernel_launch_count": (_c_i64, []),
     "rsvd_cpqr_id": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp, _vp,
                               _c_size, _vp, _vp]),
+    "rsvd_svd_id_cur_host": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int,
+                                      _vp, _vp, _c_i64, _vp, _c_i64, _vp, _vp, _c_i64, _vp, _vp,
+                                      _c_i64, _vp, _vp, _vp, _c_i64, _vp, _c_size, _vp, _vp,
+                                      _OPTP]),
     "rsvd_cpqr_f32_workspace_size": (_c_size, [_c_int, _c_i64, _c_int]),
     "rsvd_cpqr_id_f32": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
                                   _vp, _c_size, _vp, _vp]),
@@ -316,6 +320,21 @@ class Plan:
             raise RsvdError(1, "rsvd_svd_id_cur_workspace_size")
         self.work = _work(ws, dev)
         self.info = _info(dev)
+
+    def run_host(self, A_host, A, seed):
+        """As run() with A in (page-locked) host memory: A_host is copied into
+        the device buffer A while the sketch consumes it (rsvd_svd_id_cur_host)."""
+        _check_matrix(A, "A")
+        if A_host.is_cuda or A_host.shape != A.shape or A_host.stride() != A.stride():
+            raise ValueError("A_host: a host tensor with the layout of A")
+        k = self.k
+        st = lib().rsvd_svd_id_cur_host(
+            self.m, self.n, k, self.p, self.q, seed, self.dt, A_host.data_ptr(), _ptr(A),
+            A.stride(0), _ptr(self.U), k, _ptr(self.S), _ptr(self.V), k, _ptr(self.J),
+            _ptr(self.T), self.n - k, _ptr(self.Jc), _ptr(self.Ir), _ptr(self.Ucur), k,
+            _ptr(self.work), self.work.numel(), _ptr(self.info), _stream(),
+            _opts_ptr(self.opts))
+        _raise(st, "rsvd_svd_id_cur_host")
 
     def run(self, A, seed):
         _check_matrix(A, "A")

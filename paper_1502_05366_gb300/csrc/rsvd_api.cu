@@ -45,6 +45,10 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   int* d_info = nullptr;
   cudaError_t err = cudaSuccess;
+  // host-input call: A arrives in row chunks, chunk ci complete at chunk_ev[ci]
+  int nchunks = 0;
+  int64_t chunk_rows = 0;
+  cudaEvent_t* chunk_ev = nullptr;
 
   template <typename T>
   T* take(size_t count) {
@@ -336,10 +340,25 @@ struct Engine {
     const int L = padL(l);
     rsvd_status st;
     if (!tc) LK(launch_fill<T>(m, L, b.Y, L, T(0), c.stream));
-    // Y = A Omega (Fig. 1 step 2)
-    st = gemm_n(m, n, L, A, lda, m, n, true, seed, l, nullptr, nullptr, 0, b.Y, L, L, &b.ys,
-                b.part, nullptr);
-    if (st != RSVD_OK) return st;
+    // Y = A Omega (Fig. 1 step 2); for a host-input call, row chunk by row
+    // chunk as the chunks of A land (the rows of Y are independent)
+    if (c.nchunks > 0 && tc) {
+      for (int ci = 0; ci < c.nchunks; ++ci) {
+        const int64_t r0 = ci * c.chunk_rows, r1 = std::min(m, r0 + c.chunk_rows);
+        if (r1 <= r0) break;
+        LK(cudaStreamWaitEvent(c.stream, c.chunk_ev[ci], 0));
+        Split ysc = b.ys;
+        ysc.hi = (uint16_t*)b.ys.hi + r0;
+        ysc.lo = (uint16_t*)b.ys.lo + r0;
+        st = gemm_n(r1 - r0, n, L, A + r0 * lda, lda, r1 - r0, n, true, seed, l, nullptr, nullptr,
+                    0, b.Y + r0 * L, L, L, &ysc, b.part, nullptr);
+        if (st != RSVD_OK) return st;
+      }
+    } else {
+      st = gemm_n(m, n, L, A, lda, m, n, true, seed, l, nullptr, nullptr, 0, b.Y, L, L, &b.ys,
+                  b.part, nullptr);
+      if (st != RSVD_OK) return st;
+    }
     int prod = 0;  // index of the next product with A or A^T (Alg. 5 orth test)
     for (int j = 1; j <= q; ++j) {
       if (prod % o.s == 0) {
@@ -655,10 +674,12 @@ enum Want { W_Q = 1, W_SVD = 2, W_ID = 4, W_CUR = 8 };
 // kept for the life of the process).  The host-side enqueue of a forked call
 // holds the device's mutex so that concurrent callers do not interleave their
 // records of the shared events.
+constexpr int MAX_CHUNKS = 16;
 struct SideStream {
   std::mutex mu;
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t chunk[MAX_CHUNKS] = {};
 };
 static SideStream* side_stream() {
   static SideStream g_side[64];
@@ -676,6 +697,15 @@ static SideStream* side_stream() {
       cudaStreamDestroy(st);
       return nullptr;
     }
+    for (int i = 0; i < MAX_CHUNKS; ++i) {
+      if (cudaEventCreateWithFlags(&ss->chunk[i], cudaEventDisableTiming) != cudaSuccess) {
+        for (int q = 0; q < i; ++q) cudaEventDestroy(ss->chunk[q]);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaStreamDestroy(st);
+        return nullptr;
+      }
+    }
     ss->fork = a;
     ss->join = b;
     ss->s = st;
@@ -688,7 +718,7 @@ static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n,
                            int q, uint64_t seed, const T* A, int64_t lda, int want, T* Qo,
                            int64_t ldq, T* Bto, int64_t ldbt, T* U, int64_t ldu, double* S, T* V,
                            int64_t ldv, int32_t* J, T* Tout, int64_t ldt, int32_t* Jc,
-                           int32_t* Ir, T* Ucur, int64_t lducur) {
+                           int32_t* Ir, T* Ucur, int64_t lducur, const T* A_host = nullptr) {
   Engine<T> e(c, o, tc);
   const int l = k + p, L = padL(l);
   auto qbb = e.take_qb(m, n, L);
@@ -702,7 +732,37 @@ static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n,
   if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
 
   reset_info(c);
+  // host input: A is copied into the caller's device buffer (same leading
+  // dimension); on the tensor-core path in row chunks on the auxiliary stream,
+  // so that the sketch Y = A Omega runs behind the copy
+  std::unique_lock<std::mutex> host_lock;
+  if (A_host) {
+    if (tc) {
+      SideStream* hs = side_stream();
+      if (!hs) return RSVD_ERR_CUDA;
+      host_lock = std::unique_lock<std::mutex>(hs->mu);
+      int nch = (int)std::min<int64_t>(8, ceil_div(m, 256));
+      const int64_t rows = round_up(ceil_div(m, nch), 256);
+      nch = (int)ceil_div(m, rows);
+      LK(cudaEventRecord(hs->fork, c.stream));
+      LK(cudaStreamWaitEvent(hs->s, hs->fork, 0));
+      for (int ci = 0; ci < nch; ++ci) {
+        const int64_t r0 = ci * rows, r1 = std::min(m, r0 + rows);
+        LK(cudaMemcpyAsync((T*)A + r0 * lda, A_host + r0 * lda, sizeof(T) * (size_t)(r1 - r0) * lda,
+                           cudaMemcpyHostToDevice, hs->s));
+        LK(cudaEventRecord(hs->chunk[ci], hs->s));
+      }
+      c.nchunks = nch;
+      c.chunk_rows = rows;
+      c.chunk_ev = hs->chunk;
+    } else {
+      LK(cudaMemcpyAsync((T*)A, A_host, sizeof(T) * (size_t)m * lda, cudaMemcpyHostToDevice,
+                         c.stream));
+    }
+  }
   rsvd_status st = e.qb(qbb, m, n, l, q, seed, A, lda);
+  c.nchunks = 0;
+  if (host_lock.owns_lock()) host_lock.unlock();
   if (st != RSVD_OK) return st;
   if (want & W_Q) {
     if (Qo) LK(launch_copy2d<T, T>(m, l, qbb.Y, L, Qo, ldq, c.stream));
@@ -790,7 +850,7 @@ static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t 
                             int64_t ldv, int32_t* J, void* Tout, int64_t ldt, int32_t* Jc,
                             int32_t* Ir, void* Ucur, int64_t lducur, void* work,
                             size_t work_bytes, int* d_info, void* stream,
-                            const rsvd_opts* opts) {
+                            const rsvd_opts* opts, const void* A_host = nullptr) {
   Opts o;
   if (!read_opts(opts, &o)) return RSVD_ERR_INVALID_ARG;
   if (!base_args_ok(m, n, k, p, q, dtype)) {
@@ -828,7 +888,8 @@ static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t 
     if (d.off > work_bytes) return RSVD_ERR_WORKSPACE;
     st = run_all<double>(c, o, false, m, n, k, p, q, seed, (const double*)A, lda, want,
                          (double*)Qo, ldq, (double*)Bto, ldbt, (double*)U, ldu, S, (double*)V,
-                         ldv, J, (double*)Tout, ldt, Jc, Ir, (double*)Ucur, lducur);
+                         ldv, J, (double*)Tout, ldt, Jc, Ir, (double*)Ucur, lducur,
+                         (const double*)A_host);
   } else {
     const bool tc = want_tc(dtype, o, l, A, lda);
     Ctx d;
@@ -838,7 +899,7 @@ static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t 
     if (d.off > work_bytes) return RSVD_ERR_WORKSPACE;
     st = run_all<float>(c, o, tc, m, n, k, p, q, seed, (const float*)A, lda, want, (float*)Qo,
                         ldq, (float*)Bto, ldbt, (float*)U, ldu, S, (float*)V, ldv, J,
-                        (float*)Tout, ldt, Jc, Ir, (float*)Ucur, lducur);
+                        (float*)Tout, ldt, Jc, Ir, (float*)Ucur, lducur, (const float*)A_host);
   }
   if (st == RSVD_OK && c.err != cudaSuccess) st = RSVD_ERR_CUDA;
   return st;
@@ -947,6 +1008,23 @@ rsvd_status rsvd_svd_id_cur(int64_t m, int64_t n, int k, int p, int q, uint64_t 
   if (!want) return RSVD_ERR_INVALID_ARG;
   return dispatch(m, n, k, p, q, seed, dtype, A, lda, want, nullptr, 0, nullptr, 0, U, ldu, S, V,
                   ldv, J, T, ldt, Jc, Ir, Ucur, lducur, work, work_bytes, d_info, stream, opts);
+}
+
+rsvd_status rsvd_svd_id_cur_host(int64_t m, int64_t n, int k, int p, int q, uint64_t seed,
+                                 int dtype, const void* A_host, void* A, int64_t lda, void* U,
+                                 int64_t ldu, double* S, void* V, int64_t ldv, int32_t* J,
+                                 void* T, int64_t ldt, int32_t* Jc, int32_t* Ir, void* Ucur,
+                                 int64_t lducur, void* work, size_t work_bytes, int* d_info,
+                                 void* stream, const rsvd_opts* opts) {
+  if (!A_host) return RSVD_ERR_INVALID_ARG;
+  int want = 0;
+  if (U || S || V) want |= W_SVD;
+  if (J || T) want |= W_ID;
+  if (Jc || Ir || Ucur) want |= W_ID | W_CUR;
+  if (!want) return RSVD_ERR_INVALID_ARG;
+  return dispatch(m, n, k, p, q, seed, dtype, A, lda, want, nullptr, 0, nullptr, 0, U, ldu, S, V,
+                  ldv, J, T, ldt, Jc, Ir, Ucur, lducur, work, work_bytes, d_info, stream, opts,
+                  A_host);
 }
 
 }  // extern "C"

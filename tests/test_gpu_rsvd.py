@@ -170,3 +170,29 @@ def test_zero_matrix_reports_not_spd():
     with pytest.raises(rs.RsvdError) as e:
         rs.svd(A, 5, 5, 1, 1)
     assert e.value.code in (5, 7)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_host_input_entry_point(dtype):
+    """rsvd_svd_id_cur_host: A copied from page-locked host memory (in row
+    chunks behind the sketch on the FP32 path) gives the device call's results
+    and leaves A in the device buffer."""
+    m, n, k, p, q = 3000, 2000, 40, 10, 2
+    A = make_matrix_np(m, n, spectrum("inv", 2000), noise=1e-4, seed=21, dtype=dtype)
+    tdt = torch.float64 if dtype == "float64" else torch.float32
+    A_dev = _dev(A, tdt)
+    plan = rs.Plan(m, n, k, p, q, tdt, DEV)
+    plan.run(A_dev, 99)
+    torch.cuda.synchronize()
+    rs.check_info(plan.info)
+    S_d, J_d = plan.S.clone(), plan.J.clone()
+    A_host = torch.from_numpy(np.ascontiguousarray(A)).to(tdt).pin_memory()
+    A_dev2 = torch.empty_like(A_dev)
+    plan.run_host(A_host, A_dev2, 99)
+    torch.cuda.synchronize()
+    rs.check_info(plan.info)
+    assert torch.equal(A_dev2, A_dev)
+    tol = 1e-10 if dtype == "float64" else 1e-5
+    rel = (plan.S - S_d).abs() / S_d
+    assert rel.max().item() <= tol
+    assert torch.equal(plan.J[:k], J_d[:k])
