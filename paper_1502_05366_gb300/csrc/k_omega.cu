@@ -139,10 +139,12 @@ __global__ void __launch_bounds__(OTHREADS, 1)
       int64_t unit = it0 / P.kiters, kc = it0 - unit * P.kiters;
       int fs = 0;
       uint32_t fph = 0;
+      const uint64_t pol_a = l2_policy_evict_first();   // A streams through once
       for (int64_t it = it0; it < it1; ++it) {
         if (!mbar_wait(&fempty[fs], fph ^ 1u, abort_flag, P.d_info)) break;
         mbar_arrive_expect_tx(&ffull[fs], (uint32_t)F_BYTES);
-        tma_load_2d(fring + fs * F_BYTES, &mapA, &ffull[fs], (int)(kc * OBK), (int)(unit * OUNIT));
+        tma_load_2d_hint(fring + fs * F_BYTES, &mapA, &ffull[fs], (int)(kc * OBK),
+                         (int)(unit * OUNIT), pol_a);
         last_issued = it - it0;
         if (++kc == P.kiters) {
           kc = 0;

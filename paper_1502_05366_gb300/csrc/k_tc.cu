@@ -133,22 +133,26 @@ __global__ void __launch_bounds__(256, 1)
       int64_t tile = it0 / P.kiters, kc = it0 - tile * P.kiters;
       int s = 0;
       uint32_t ph = 0;
+      // A streams through once: evict first; the W tiles are re-read by every
+      // output tile: evict last
+      const uint64_t pol_a = l2_policy_evict_first(), pol_w = l2_policy_evict_last();
       for (int64_t it = it0; it < it1; ++it) {
         const int64_t li = it - it0;
         if (!mbar_wait(&done[s], ph ^ 1u, abort_flag, P.d_info)) break;
         unsigned char* st = dsm + s * SB;
         mbar_arrive_expect_tx(&full[s], bytes);
         if (FORM == 0)
-          tma_load_2d(st, &mapA, &full[s], (int)(kc * BK), (int)(tile * BM));
+          tma_load_2d_hint(st, &mapA, &full[s], (int)(kc * BK), (int)(tile * BM), pol_a);
         else
-          tma_load_2d(st, &mapA, &full[s], (int)(tile * BM), (int)(kc * BK));
+          tma_load_2d_hint(st, &mapA, &full[s], (int)(tile * BM), (int)(kc * BK), pol_a);
         if (NWT >= 2) {
-          tma_load_2d(st + A_STAGE_BYTES, &mapW0, &full[s], (int)(kc * BK), 0);
-          tma_load_2d(st + A_STAGE_BYTES + w_tile_bytes(L), &mapW1, &full[s], (int)(kc * BK), 0);
+          tma_load_2d_hint(st + A_STAGE_BYTES, &mapW0, &full[s], (int)(kc * BK), 0, pol_w);
+          tma_load_2d_hint(st + A_STAGE_BYTES + w_tile_bytes(L), &mapW1, &full[s], (int)(kc * BK),
+                           0, pol_w);
         }
         if (NWT == 3)
-          tma_load_2d(st + A_STAGE_BYTES + 2 * w_tile_bytes(L), &mapW2, &full[s], (int)(kc * BK),
-                      0);
+          tma_load_2d_hint(st + A_STAGE_BYTES + 2 * w_tile_bytes(L), &mapW2, &full[s],
+                           (int)(kc * BK), 0, pol_w);
         last_issued = li;
         if (++kc == P.kiters) {
           kc = 0;
