@@ -268,7 +268,8 @@ __device__ __forceinline__ void tri_tile(int u, int nT, int* ti, int* tc) {
   *tc = r + (u - (r * nT - (r * (r - 1)) / 2));
 }
 
-__device__ void chol_tiled(float* S, int l, int ld, float thr, int* s_fail) {
+// s_dinv (l floats, shared) receives 1 / R_ii for the solves.
+__device__ void chol_tiled(float* S, int l, int ld, float thr, int* s_fail, float* s_dinv) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nthr = blockDim.x * blockDim.y;
   for (int p0 = 0; p0 < l; p0 += NB) {
@@ -286,11 +287,13 @@ __device__ void chol_tiled(float* S, int l, int ld, float thr, int* s_fail) {
           if (!(piv > thr)) {
             failed = jj;
           } else {
-            const float rr = sqrtf(piv);
+            // one rsqrt on the pivot chain: R_jj = piv rsqrt(piv), R_jc = S_jc rsqrt(piv)
+            const float rinv = rsqrtf(piv);
             float rj = d[jj];
-            if (lane == jj) rj = rr;
-            else if (lane > jj) rj = rj / rr;
+            if (lane == jj) rj = piv * rinv;
+            else if (lane > jj) rj = rj * rinv;
             d[jj] = rj;
+            if (lane == jj) s_dinv[p0 + jj] = rinv;
 #pragma unroll
             for (int i = jj + 1; i < NB; ++i) {
               const float ri = __shfl_sync(0xffffffffu, rj, i);
@@ -320,7 +323,7 @@ __device__ void chol_tiled(float* S, int l, int ld, float thr, int* s_fail) {
           float acc = S[(p0 + i) * ld + c];
 #pragma unroll
           for (int t = 0; t < i; ++t) acc -= S[(p0 + t) * ld + p0 + i] * x[t];
-          x[i] = acc / S[(p0 + i) * ld + p0 + i];
+          x[i] = acc * s_dinv[p0 + i];
         } else {
           x[i] = 0.f;
         }
@@ -371,7 +374,7 @@ __device__ void chol_tiled(float* S, int l, int ld, float thr, int* s_fail) {
 // from the bottom:  T = E_I - R(I, I+1:) X(I+1:, :) with the product on 4 x 4
 // register tiles (K range clipped to the tile's columns, X upper triangular),
 // then X(I, :) = R_II^{-1} T by back substitution per column.
-__device__ void inv_upper_tiled(float* S, int l, int ld) {
+__device__ void inv_upper_tiled(float* S, int l, int ld, const float* s_dinv) {
   __shared__ float Rd[NB][NB + 1];
   const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
   // the strictly lower triangle holds Gram entries: zero it (X is upper triangular)
@@ -452,7 +455,7 @@ __device__ void inv_upper_tiled(float* S, int l, int ld) {
 #pragma unroll
           for (int t = i + 1; t < NB; ++t)
             if (t < rb) acc2 -= Rd[i][t] * x[t];
-          x[i] = acc2 / Rd[i][i];
+          x[i] = acc2 * s_dinv[r0 + i];
         } else {
           x[i] = 0.f;
         }
@@ -471,7 +474,7 @@ __device__ void inv_upper_tiled(float* S, int l, int ld) {
 // generic pointer that might alias global memory would serialise the loads).
 template <typename T>
 __device__ __forceinline__ void chol_body(const CholArgs& a, T* S, int ld, T* red, T& s_maxdiag,
-                                          T& s_dev, int& s_fail) {
+                                          T& s_dev, int& s_fail, float* s_dinv) {
   const int l = a.l, L = a.L;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int tx = threadIdx.x, ty = threadIdx.y, nty = blockDim.y;
@@ -513,7 +516,7 @@ __device__ __forceinline__ void chol_body(const CholArgs& a, T* S, int ld, T* re
     if (tid == 0) s_fail = -1;
     __syncthreads();
     if (sizeof(T) == 4 && a.sld > 0)
-      chol_tiled((float*)S, l, ld, (float)(tau * maxdiag), &s_fail);
+      chol_tiled((float*)S, l, ld, (float)(tau * maxdiag), &s_fail, s_dinv);
     else
       chol_blocked<T>(S, l, tau * maxdiag, &s_fail);
     fail = s_fail;
@@ -552,7 +555,7 @@ __device__ __forceinline__ void chol_body(const CholArgs& a, T* S, int ld, T* re
       }
   }
   if (sizeof(T) == 4 && a.sld > 0)
-    inv_upper_tiled((float*)S, l, ld);
+    inv_upper_tiled((float*)S, l, ld, s_dinv);
   else
     inv_upper_blocked<T>(S, l, a.scratch ? (T*)a.scratch + (size_t)l * l : nullptr);
   if (a.Rinv) {
@@ -592,8 +595,9 @@ __global__ void __launch_bounds__(CT) chol_kernel(CholArgs a) {
   __shared__ T red[32];
   __shared__ T s_maxdiag, s_dev;
   __shared__ int s_fail;
+  __shared__ float s_dinv[256];   // 1 / R_ii of the fp32 tiled path (l <= 256 there)
   chol_body<T>(a, reinterpret_cast<T*>(dsm), a.sld > 0 ? a.sld : a.l, red, s_maxdiag, s_dev,
-               s_fail);
+               s_fail, s_dinv);
 }
 // ... or in the global scratch (large l)
 template <typename T>
@@ -601,7 +605,7 @@ __global__ void __launch_bounds__(CT) chol_kernel_global(CholArgs a) {
   __shared__ T red[32];
   __shared__ T s_maxdiag, s_dev;
   __shared__ int s_fail;
-  chol_body<T>(a, (T*)a.scratch, a.l, red, s_maxdiag, s_dev, s_fail);
+  chol_body<T>(a, (T*)a.scratch, a.l, red, s_maxdiag, s_dev, s_fail, nullptr);
 }
 
 // Racc <- R * Racc for upper-triangular L x L matrices (through tmp).
