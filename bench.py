@@ -246,53 +246,62 @@ def max_over_ranks(x, world, device):
     return float(t.item())
 
 
-def cpu_oracle_sample(cfg, frac_rows=25, frac_cols=5, budget_s=30.0):
-    """The FP64 oracle on a bounded sample of the same recipe (m/frac_rows x n/frac_cols)."""
-    from oracle import rsvd as orc
+def _oracle_sample_setup(cfg, frac_rows=25, frac_cols=5):
+    """A bounded sample of the same recipe (m/frac_rows x n/frac_cols) for the oracle."""
     from synth import make_matrix_np, spectrum
     m = max(cfg["m"] // frac_rows, cfg["k"] + cfg["p"] + 8)
     n = max(cfg["n"] // frac_cols, cfg["k"] + cfg["p"] + 8)
     r = min(cfg["r"], n)
     A = make_matrix_np(m, n, spectrum(cfg["spectrum"], r), noise=cfg["noise"],
                        seed=cfg["a_seed"], dtype=cfg["dtype"]).astype(np.float64)
-    k, p, q = cfg["k"], cfg["p"], cfg["q"]
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        orc.rsvd(A, k, p, q, cfg["omega_seed"], rounding="bf16")
-        orc.rcur(A, k, p, q, cfg["omega_seed"], rounding="bf16")
-        reps += 1
-        if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
-            break
-    dt = (time.perf_counter() - t0) / reps
-    fl = step_flops(m, n, k, p, q)
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
         cores = os.cpu_count()
+    desc = ("FP64 numpy oracle (OpenBLAS threads on all affinity cores), RSVD + ID + CUR of the "
+            "same recipe at m=%d n=%d k=%d p=%d q=%d (1/%d of the rows, 1/%d of the columns)"
+            % (m, n, cfg["k"], cfg["p"], cfg["q"], frac_rows, frac_cols))
+    return A, m, n, cores, desc
+
+
+def _oracle_step(A, cfg):
+    from oracle import rsvd as orc
+    k, p, q = cfg["k"], cfg["p"], cfg["q"]
+    t0 = time.perf_counter()
+    orc.rsvd(A, k, p, q, cfg["omega_seed"], rounding="bf16")
+    orc.rcur(A, k, p, q, cfg["omega_seed"], rounding="bf16")
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_sample(cfg, reps=3):
+    """The FP64 oracle timed on a bounded sample of the same recipe."""
+    A, m, n, cores, desc = _oracle_sample_setup(cfg)
+    dt = float(np.median([_oracle_step(A, cfg) for _ in range(reps)]))
+    fl = step_flops(m, n, cfg["k"], cfg["p"], cfg["q"])
     return {"value": fl / dt / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "FP64 numpy oracle (OpenBLAS threads on all affinity cores), RSVD + ID + "
-                      "CUR of the same recipe at m=%d n=%d k=%d p=%d q=%d (1/%d of the rows, "
-                      "1/%d of the columns), %.2f s per step" % (m, n, k, p, q, frac_rows,
-                                                                 frac_cols, dt)}
+            "sample": desc + ", %.2f s per step (median of %d)" % (dt, reps)}
 
 
 def run_reference(args, cfg, world, rank):
-    """--impl reference: the oracle on the host cores, rank 0 only."""
+    """--impl reference: the oracle on the host cores (rank 0 only), W untimed
+    warm-up steps then K timed steps of the bounded sample."""
     if rank != 0:
         return 0
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
-    samples = []
-    for _ in range(max(1, min(args.steps, 3))):
-        samples.append(cpu_oracle_sample(cfg, budget_s=20.0))
-    v = float(np.median([s["value"] for s in samples]))
-    base = samples[0]
+    A, m, n, cores, desc = _oracle_sample_setup(cfg)
+    for _ in range(min(args.warmup, 3)):
+        _oracle_step(A, cfg)
+    times = [_oracle_step(A, cfg) for _ in range(args.steps)]
+    tot = float(sum(times))
+    fl = step_flops(m, n, cfg["k"], cfg["p"], cfg["q"])
+    v = fl * len(times) / tot / 1e12
+    ms = 1e3 * tot / len(times)
+    sample = desc + ", %.2f s per step" % (tot / len(times))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": len(samples), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "sample": base["sample"]},
-            "cpu_baseline": dict(base, value=v),
+            "steps": len(times), "warmup": min(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg["name"], "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
