@@ -376,7 +376,7 @@ __global__ void tc_reduce_kernel(TcParams P, int G) {
   for (int i = tid; i < nctr; i += 256) {
     const int64_t c = blo + i;
     const int64_t tile0 = ((c * P.total) / G) / P.kiters;
-    s_base[i] = (c * P.maxseg + (t - tile0)) * (int64_t)P.bm * L;
+    s_base[i] = ((c * P.wmul + P.wadd) * P.maxseg + (t - tile0)) * (int64_t)P.bm * L;
   }
   __syncthreads();
   const int rg = blockIdx.x % (P.bm / 32), jg = blockIdx.x / (P.bm / 32);
@@ -390,14 +390,14 @@ __global__ void tc_reduce_kernel(TcParams P, int G) {
   }
   __syncthreads();
   for (int rr = ty; rr < 32; rr += 8) {
-    const int64_t i = t * P.bm + rg * 32 + rr;
+    const int64_t i = t * P.ustride + P.uoff + rg * 32 + rr;
     const int j = jg * 32 + tx;
     if (i < P.rows && j < P.ncols) P.out[i * P.ldo + j] = tile_s[tx][rr];
   }
   if (P.out_hi) {
     for (int jj = ty; jj < 32; jj += 8) {
       const int j = jg * 32 + jj;
-      const int64_t i = t * P.bm + rg * 32 + tx;
+      const int64_t i = t * P.ustride + P.uoff + rg * 32 + tx;
       if (j < L && i < P.rows) {
         const float v = (j < P.ncols) ? tile_s[jj][tx] : 0.0f;
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -482,6 +482,13 @@ size_t tc_part_bytes(int64_t rows, int64_t K, int L) {
     const size_t b = (size_t)G * maxseg * bm * L * sizeof(float);
     if (b > best) best = b;
   }
+  {  // two-CTA Omega kernel: 512-row units over SMs / 2 pairs, 256-row partials per CTA
+    int64_t tiles, kiters, total, G;
+    int maxseg;
+    sk_plan(rows, K, 512, BK, device_sm_count() / 2, &tiles, &kiters, &total, &G, &maxseg);
+    const size_t b = (size_t)2 * G * maxseg * 256 * L * sizeof(float);
+    if (b > best) best = b;
+  }
   return best;
 }
 
@@ -523,6 +530,10 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   P.rows = g.rows;
   P.K = g.K;
   P.bm = BM;
+  P.ustride = BM;
+  P.uoff = 0;
+  P.wmul = 1;
+  P.wadd = 0;
   P.L = g.L;
   P.lvalid = g.lvalid;
   P.seed = g.seed;

@@ -30,6 +30,10 @@ struct TcParams {
   int64_t ldt;
   const int* skip;
   int* d_info;
+  // unit u covers rows u ustride + uoff .. + bm; stream-K worker c is CTA
+  // wmul c + wadd (ustride = bm, uoff = 0, wmul = 1, wadd = 0 for one CTA per worker)
+  int64_t ustride;
+  int uoff, wmul, wadd;
 };
 
 // Fixed-order sum of the stream-K partials of the tiles split between CTAs
@@ -73,10 +77,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+      : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
 }
