@@ -5,15 +5,16 @@
 // (CholeskyQR2/3).  A pass whose Gram has a pivot below tau * max(diag G),
 // tau = 4 l eps, is redone with a diagonal shift (shifted CholeskyQR, Fukaya et
 // al. 2020), the shift growing tenfold per retry; any shifted pass, or a second
-// pass whose Gram is far from I, requests the third pass.  One CTA of 1024
-// threads holds the matrix in shared memory (global memory beyond the limit).
+// pass whose Gram is far from I, requests the third pass.  One CTA holds the
+// matrix in shared memory: 384 threads on register tiles for fp32 up to
+// l = 224, else 256 threads (global memory beyond the shared-memory limit).
 #include "common.cuh"
 #include "kernels.h"
 
 namespace rsvd {
 
 namespace {
-constexpr int CT = 256;   // threads (a 255-register budget keeps the unrolled panel code in registers)
+constexpr int CT = 256;   // threads of the generic kernel (a 255-register budget keeps its unrolled panel code in registers)
 constexpr size_t SMEM_LIMIT = 212 * 1024;   // dynamic part; static arrays take <= 9 KB
 template <typename T> __device__ __forceinline__ T eps_of();
 template <> __device__ __forceinline__ float eps_of<float>() { return 5.9604645e-8f; }
@@ -56,6 +57,23 @@ __device__ void write_identity_outputs(const CholArgs& a) {
       ((__nv_bfloat16*)a.Wlo)[t] = __float2bfloat16_rn(0.0f);
       ((__nv_bfloat16*)a.Wlo2)[t] = __float2bfloat16_rn(0.0f);
     }
+  }
+}
+
+// Pass bookkeeping in a.flags after a successful factorization.  ldev is
+// l * max |G - I| of this pass's Gram.
+__device__ void chol_update_flags(const CholArgs& a, int used_shift, double ldev) {
+  if (!a.flags) return;
+  if (a.pass == 1) {
+    a.flags[1] = used_shift;
+    // conditional second pass (inside the power scheme): only after a shift;
+    // the third pass is skipped unless the second one asks for it
+    a.flags[3] = used_shift ? 0 : 1;
+    a.flags[2] = 1;
+  } else if (a.pass == 2) {
+    a.flags[1] |= used_shift;
+    a.flags[0] = (a.flags[1] || ldev > 0.5) ? 1 : 0;
+    a.flags[2] = 1 - a.flags[0];   // skip flag of the third pass
   }
 }
 
@@ -243,18 +261,6 @@ __device__ void inv_upper_blocked(T* S, int l, T* ttmp) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// fp32 variants on a padded shared-memory matrix (leading dimension ld, a
-// multiple of 4 with ld % 32 == 4, zero padding), so that 4-wide rows load as
-// one conflict-free float4 and every FMA-heavy phase runs on 4 x 4 register
-// tiles spread over all threads.
-// ---------------------------------------------------------------------------
-__host__ __device__ inline int chol_ld(int l) {
-  int ld = (l + 3) & ~3;
-  while ((ld & 31) != 4) ld += 4;
-  return ld;
-}
-
 // Upper-triangle tile (ti, tc), tc >= ti, of linear index u in row-major order
 // over an nT x nT tile grid.
 __device__ __forceinline__ void tri_tile(int u, int nT, int* ti, int* tc) {
@@ -268,203 +274,540 @@ __device__ __forceinline__ void tri_tile(int u, int nT, int* ti, int* tc) {
   *tc = r + (u - (r * nT - (r * (r - 1)) / 2));
 }
 
-// s_dinv (l floats, shared) receives 1 / R_ii for the solves.
-__device__ void chol_tiled(float* S, int l, int ld, float thr, int* s_fail, float* s_dinv) {
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nthr = blockDim.x * blockDim.y;
-  for (int p0 = 0; p0 < l; p0 += NB) {
-    const int pb = min(NB, l - p0);
-    if (warp == 0) {   // (a) diagonal block in registers (lane c holds column c)
-      float d[NB];
+// ---------------------------------------------------------------------------
+// fp32 path for l <= 224: one CTA of 384 threads with the whole matrix in
+// shared memory (leading dimension chf_ld(l), a multiple of 8 so that every
+// 8-column group is one aligned pair of float4; zero padding columns).
+//
+// Factor (right-looking, panels of NB = 32 columns):
+//   (a) warp 0 factors the diagonal block R_pp and forms its inverse D_p
+//       (both in registers, one column per lane; the rows of R_pp and of D_p
+//       are broadcast through shared memory);
+//   (b) the panel row block becomes D_p^T S_panel (4 x 4 register tiles);
+//   (c) the trailing upper triangle is updated with 8 x 8 register tiles,
+//       except the next diagonal block, which warp 0 updates and factors
+//       meanwhile (lookahead).
+// Inverse X = R^{-1}, block rows from the bottom:
+//   T = -R(I, I+1:) X(I+1:, :)
+//   X(I, I+1:) = D_I T,  X(I, I) = D_I   (4 x 4 register tiles).
+// D_p is kept, transposed, in the strictly lower triangle of the diagonal
+// block (1 / R_ii in s_dinv); no phase reads the lower triangle otherwise.
+// ---------------------------------------------------------------------------
+constexpr int CHF_T = 384;     // threads: one register tile each in every phase
+constexpr int CHF_LMAX = 224;  // (b) and the inverse need 8 * ceil((l - 32) / 4) <= CHF_T
+constexpr int CHF_DLD = 36;   // row stride of the current panel's D_p copy
+
+__host__ __device__ inline int chf_ld(int l) {
+  int ld = (l + 7) & ~7;
+  while ((ld & 31) != 8) ld += 8;
+  return ld;
+}
+inline size_t chf_smem(int l) {
+  return (size_t)l * chf_ld(l) * sizeof(float) + (size_t)NB * CHF_DLD * sizeof(float);
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
+// G (+ shift on the diagonal) into S; on the first load also the largest
+// diagonal entry, the largest |G - I| entry and whether G is finite.
+__device__ void chf_load(const CholArgs& a, float* S, int ld, float shift, float* md, float* dev,
+                         bool* bad) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int l = a.l;
+  const float* G = (const float*)a.G;
+  const int64_t ldg = a.ldg;
+  const int nq = ld / 4;
+  const bool vec = (ldg % 4 == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0) &&
+                   ldg >= ((l + 3) & ~3);
+  const int ne = l * nq;
+  for (int e0 = tid; e0 < ne; e0 += 8 * nthr) {
+    float4 v[8];
 #pragma unroll
-      for (int i = 0; i < NB; ++i)
-        d[i] = (lane < pb && i <= lane) ? S[(p0 + i) * ld + p0 + lane] : 0.f;
-      int failed = -1;
-#pragma unroll
-      for (int jj = 0; jj < NB; ++jj) {
-        if (jj < pb && failed < 0) {
-          const float piv = __shfl_sync(0xffffffffu, d[jj], jj);
-          if (!(piv > thr)) {
-            failed = jj;
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nthr;
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < ne) {
+        const int i = e / nq, c = 4 * (e - (e / nq) * nq);
+        if (c < l) {
+          const float* g = G + (int64_t)i * ldg + c;
+          if (vec) {
+            v[u] = *reinterpret_cast<const float4*>(g);
           } else {
-            // one rsqrt on the pivot chain: R_jj = piv rsqrt(piv), R_jc = S_jc rsqrt(piv)
-            const float rinv = rsqrtf(piv);
-            float rj = d[jj];
-            if (lane == jj) rj = piv * rinv;
-            else if (lane > jj) rj = rj * rinv;
-            d[jj] = rj;
-            if (lane == jj) s_dinv[p0 + jj] = rinv;
-#pragma unroll
-            for (int i = jj + 1; i < NB; ++i) {
-              const float ri = __shfl_sync(0xffffffffu, rj, i);
-              if (lane >= i) d[i] -= ri * rj;
-            }
+            v[u].x = g[0];
+            if (c + 1 < l) v[u].y = g[1];
+            if (c + 2 < l) v[u].z = g[2];
+            if (c + 3 < l) v[u].w = g[3];
           }
         }
       }
-      if (failed < 0) {
+    }
 #pragma unroll
-        for (int i = 0; i < NB; ++i)
-          if (lane < pb && i <= lane) S[(p0 + i) * ld + p0 + lane] = d[i];
-      } else if (lane == 0) {
-        *s_fail = p0 + failed;
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nthr;
+      if (e < ne) {
+        const int i = e / nq, c = 4 * (e - (e / nq) * nq);
+        float w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int cc = c + w;
+          if (cc >= l) {
+            w4[w] = 0.f;
+          } else {
+            if (md) {
+              if (!isfinite(w4[w])) *bad = true;
+              if (cc == i) *md = fmaxf(*md, w4[w]);
+              *dev = fmaxf(*dev, fabsf(w4[w] - (cc == i ? 1.f : 0.f)));
+            }
+            if (cc == i) w4[w] += shift;
+          }
+        }
+        *reinterpret_cast<float4*>(S + i * ld + c) = make_float4(w4[0], w4[1], w4[2], w4[3]);
       }
     }
-    __syncthreads();
-    if (*s_fail >= 0) return;
-    const int c0 = p0 + pb, nt = l - c0;
-    if (nt <= 0) return;
-    // (b) X = R_pp^{-T} S(p0:p0+pb, c0:l), forward substitution per column
-    for (int c = c0 + tid; c < l; c += nthr) {
-      float x[NB];
+  }
+}
+
+// (a) by warp 0: R_pp in place (upper triangle, zeros below), D_p = R_pp^{-1}
+// into Dc (row-major, zeros below the diagonal) and transposed into the
+// strictly lower triangle of the block, 1 / R_ii into s_dinv.  Returns the
+// failing column (relative to p0) or -1.
+//
+// Lane i owns row i of the block, unscaled: after step j the row holds
+// S_i. - sum_{t <= j} R_ti R_t. / ... in the form  e_i = R_ii * (row i of R),
+// so that step j needs only the raw pivot row e_j and rinv_j = 1 / sqrt(piv_j):
+// R_ji R_jc = (e_ji rinv_j^2) e_jc.  Every row is scaled by its own rinv at the
+// end.  The per-step chain is: pivot shuffle, rsqrt, two multiplies, the
+// downdate of the next pivot; the exchange of the raw pivot row through shared
+// memory overlaps the rsqrt.  The step loop is rolled with static register
+// indices.
+__device__ int chf_diag(float* S, int ld, int p0, int pb, float thr, float* Dc, float* s_dinv,
+                        float* rowbuf) {
+  const int lane = threadIdx.x & 31;
+  float e[NB];
+  const float* myrow = S + (p0 + lane) * ld + p0;
 #pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        if (i < pb) {
-          float acc = S[(p0 + i) * ld + c];
+  for (int c4 = 0; c4 < NB / 4; ++c4) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < pb && 4 * c4 < pb) v = lds4(myrow + 4 * c4);
+    e[4 * c4] = v.x; e[4 * c4 + 1] = v.y; e[4 * c4 + 2] = v.z; e[4 * c4 + 3] = v.w;
+  }
+  // columns beyond pb read as padding zeros or as the next rows: clear them
 #pragma unroll
-          for (int t = 0; t < i; ++t) acc -= S[(p0 + t) * ld + p0 + i] * x[t];
-          x[i] = acc * s_dinv[p0 + i];
-        } else {
-          x[i] = 0.f;
+  for (int c = 0; c < NB; ++c) e[c] = (c < pb) ? e[c] : 0.f;
+  float diag = lane < pb ? myrow[lane] : 1.f;
+  float myrinv = 0.f;
+  for (int jj = 0; jj < pb; ++jj) {
+    float* rb = rowbuf + (jj & 1) * NB;
+    if (lane == jj) {
+#pragma unroll
+      for (int c4 = 0; c4 < NB / 4; ++c4)
+        *reinterpret_cast<float4*>(rb + 4 * c4) =
+            make_float4(e[4 * c4], e[4 * c4 + 1], e[4 * c4 + 2], e[4 * c4 + 3]);
+    }
+    const float piv = __shfl_sync(0xffffffffu, diag, jj);
+    if (!(piv > thr)) return jj;
+    const float rinv = rsqrtf(piv);
+    if (lane == jj) {
+      myrinv = rinv;
+      s_dinv[p0 + jj] = rinv;
+    }
+    __syncwarp();
+    const float eji = rb[lane];
+    const float coef = eji * (rinv * rinv);   // R_ji / R_jj^... : R_ji R_jc = coef e_jc
+    if (lane > jj) {
+      diag = fmaf(-coef, eji, diag);
+#pragma unroll
+      for (int c4 = 0; c4 < NB / 4; ++c4) {
+        const float4 r4 = lds4(rb + 4 * c4);
+        e[4 * c4] = fmaf(-coef, r4.x, e[4 * c4]);
+        e[4 * c4 + 1] = fmaf(-coef, r4.y, e[4 * c4 + 1]);
+        e[4 * c4 + 2] = fmaf(-coef, r4.z, e[4 * c4 + 2]);
+        e[4 * c4 + 3] = fmaf(-coef, r4.w, e[4 * c4 + 3]);
+      }
+    }
+  }
+  // row i of R = rinv_i e_i on and above the diagonal, zeros below
+  if (lane < pb) {
+#pragma unroll
+    for (int c4 = 0; c4 < NB / 4; ++c4) {
+      if (4 * c4 < pb) {
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = (4 * c4 + u >= lane) ? e[4 * c4 + u] * myrinv : 0.f;
+        *reinterpret_cast<float4*>(S + (p0 + lane) * ld + p0 + 4 * c4) =
+            make_float4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  }
+  __syncwarp();
+  // D_p: lane c solves R_pp x = e_c from the bottom (x_t = 0 for t > c),
+  // unrolled (a rolled loop with a run-time trip count measured 3x slower);
+  // the term of x_{i+1}, the last one known, is added last
+  float x[NB];
+#pragma unroll
+  for (int i = NB - 1; i >= 0; --i) {
+    x[i] = 0.f;
+    if (i < pb) {
+      const float* row = S + (p0 + i) * ld + p0;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      float last = 0.f;
+#pragma unroll
+      for (int i4 = (i + 1) / 4; i4 < NB / 4; ++i4) {
+        if (4 * i4 < pb) {
+          const float4 r4 = lds4(row + 4 * i4);
+          const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int t = 4 * i4 + w;
+            if (t == i + 1) last = rr[w];
+            else if (t > i + 1) acc[w] = fmaf(rr[w], x[t], acc[w]);
+          }
         }
       }
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < pb) S[(p0 + i) * ld + c] = x[i];
+      float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      if (i + 1 < NB) sum = fmaf(last, x[i + 1 < NB ? i + 1 : 0], sum);
+      x[i] = ((lane == i ? 1.f : 0.f) - sum) * s_dinv[p0 + i];
     }
-    __syncthreads();
-    // (c) trailing upper triangle S(i, c) -= sum_t X(t, i) X(t, c), 4 x 4 tiles
-    // over the upper-triangular tile grid only, float4 row loads
-    const int nT = (nt + 3) / 4;
-    const int ntiles = nT * (nT + 1) / 2;
-    for (int u = tid; u < ntiles; u += nthr) {
-      int ti, tc;
-      tri_tile(u, nT, &ti, &tc);
-      const int i0 = c0 + 4 * ti, k0 = c0 + 4 * tc;
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    Dc[i * CHF_DLD + lane] = x[i];
+    if (i < lane && lane < pb) S[(p0 + lane) * ld + p0 + i] = x[i];
+  }
+  return -1;
+}
+
+// By warp 0: the update of the diagonal block at (c0, c0), nb1 columns, by the
+// panel rows p0 .. p0 + pb - 1 (lane c owns column c0 + c).
+__device__ void chf_block_update(float* S, int ld, int p0, int pb, int c0, int nb1) {
+  const int lane = threadIdx.x & 31;
+  float acc[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) acc[i] = 0.f;
+  for (int t = 0; t < pb; ++t) {
+    const float* row = S + (p0 + t) * ld + c0;
+    const float xc = lane < nb1 ? row[lane] : 0.f;
+#pragma unroll
+    for (int i4 = 0; i4 < NB / 4; ++i4) {
+      if (4 * i4 < nb1) {
+        const float4 r4 = lds4(row + 4 * i4);
+        acc[4 * i4] = fmaf(r4.x, xc, acc[4 * i4]);
+        acc[4 * i4 + 1] = fmaf(r4.y, xc, acc[4 * i4 + 1]);
+        acc[4 * i4 + 2] = fmaf(r4.z, xc, acc[4 * i4 + 2]);
+        acc[4 * i4 + 3] = fmaf(r4.w, xc, acc[4 * i4 + 3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i <= lane && lane < nb1) S[(c0 + i) * ld + c0 + lane] -= acc[i];
+}
+
+// Full factorization; returns the failing column or -1 (uniform over the CTA).
+// Lookahead: while other warps apply panel p's update to the trailing matrix,
+// warp 0 applies it to the next diagonal block and factors that block.
+__device__ int chf_factor(float* S, int l, int ld, float thr, float* Dc, float* s_dinv,
+                          float* rowbuf, int* s_fail) {
+  const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x;
+  if (warp == 0) {
+    const int f = chf_diag(S, ld, 0, min(NB, l), thr, Dc, s_dinv, rowbuf);
+    if (tid == 0) *s_fail = f < 0 ? -1 : f;
+  }
+  __syncthreads();
+  if (*s_fail >= 0) return *s_fail;
+  for (int p0 = 0; p0 < l; p0 += NB) {
+    const int pb = min(NB, l - p0);
+    const int c0 = p0 + pb, nt = l - c0;
+    if (nt <= 0) break;
+    // (b) S(p, c0:) <- D_p^T S(p, c0:), 4 x 4 register tiles
+    {
+      const int ncq = (nt + 3) / 4;
+      const bool have = tid < 8 * ncq;
       float acc[4][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[q][w] = 0.f;
-#pragma unroll 4
-      for (int t = 0; t < pb; ++t) {
-        const float* row = S + (p0 + t) * ld;
-        const float4 xi = *reinterpret_cast<const float4*>(row + i0);
-        const float4 xc = *reinterpret_cast<const float4*>(row + k0);
-        const float a4[4] = {xi.x, xi.y, xi.z, xi.w};
-        const float b4[4] = {xc.x, xc.y, xc.z, xc.w};
+      int i0 = 0, c = 0;
+      if (have) {
+        const int rg = tid / ncq;
+        i0 = 4 * rg;
+        c = c0 + 4 * (tid - rg * ncq);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-          for (int w = 0; w < 4; ++w) acc[q][w] = fmaf(a4[q], b4[w], acc[q][w]);
-      }
+          for (int w = 0; w < 4; ++w) acc[q][w] = 0.f;
+        const int tmax = min(pb, i0 + 4);
+#pragma unroll 4
+        for (int t = 0; t < tmax; ++t) {
+          const float4 da = lds4(Dc + t * CHF_DLD + i0);
+          const float4 s4 = lds4(S + (p0 + t) * ld + c);
+          const float dv[4] = {da.x, da.y, da.z, da.w};
+          const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int i = i0 + q, c = k0 + w;
-          if (i < l && c < l && c >= i) S[i * ld + c] -= acc[q][w];
+            for (int w = 0; w < 4; ++w) acc[q][w] = fmaf(dv[q], sv[w], acc[q][w]);
         }
+      }
+      __syncthreads();
+      if (have) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (i0 + q < pb)
+            *reinterpret_cast<float4*>(S + (p0 + i0 + q) * ld + c) =
+                make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+      }
+      __syncthreads();
+    }
+    const int nb1 = min(NB, nt);   // width of the next panel
+    if (warp == 0) {
+      chf_block_update(S, ld, p0, pb, c0, nb1);
+      __syncwarp();
+      const int f = chf_diag(S, ld, c0, nb1, thr, Dc, s_dinv, rowbuf);
+      if (tid == 0) *s_fail = f < 0 ? -1 : c0 + f;
+    } else if ((warp & 3) != 0) {
+      // (c) the rest of the trailing upper triangle, 8 x 8 tiles over the
+      // upper tile grid; the tiles of the next diagonal block (tc < nbT) are
+      // warp 0's.  Warps 4, 8, .. (warp 0's scheduler partition) stay idle so
+      // that warp 0's dependent chain keeps its issue slots.
+      const int nT = (nt + 7) / 8, nbT = (nb1 + 7) / 8;
+      const int ntl = nT * (nT + 1) / 2;
+      const int nwk = (nthr >> 5) - (nthr >> 7);          // working warps
+      const int wk = warp - 1 - (warp >> 2);              // 0 .. nwk - 1
+      for (int u = wk * 32 + (tid & 31); u < ntl; u += nwk * 32) {
+        int ti, tc;
+        tri_tile(u, nT, &ti, &tc);
+        if (tc < nbT) continue;
+        const int i0 = c0 + 8 * ti, k0 = c0 + 8 * tc;
+        float acc[8][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int w = 0; w < 8; ++w) acc[q][w] = 0.f;
+#pragma unroll 2
+        for (int t = 0; t < pb; ++t) {
+          const float* row = S + (p0 + t) * ld;
+          const float4 a0 = lds4(row + i0), a1 = lds4(row + i0 + 4);
+          const float4 b0 = lds4(row + k0), b1 = lds4(row + k0 + 4);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) acc[q][w] = fmaf(av[q], bv[w], acc[q][w]);
+        }
+        if (tc > ti) {   // off-diagonal tile: whole rows (padding columns receive 0)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (i0 + q < l) {
+              float4* o = reinterpret_cast<float4*>(S + (i0 + q) * ld + k0);
+              float4 u0 = o[0], u1 = o[1];
+              u0.x -= acc[q][0]; u0.y -= acc[q][1]; u0.z -= acc[q][2]; u0.w -= acc[q][3];
+              u1.x -= acc[q][4]; u1.y -= acc[q][5]; u1.z -= acc[q][6]; u1.w -= acc[q][7];
+              o[0] = u0;
+              o[1] = u1;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+              const int i = i0 + q, cc = k0 + w;
+              if (i < l && cc < l && cc >= i) S[i * ld + cc] -= acc[q][w];
+            }
+        }
+      }
+    }
+    __syncthreads();
+    if (*s_fail >= 0) return *s_fail;
+  }
+  return -1;
+}
+
+// In-place X = R^{-1} (upper triangle of S), using the D_I blocks left by the
+// factorization.
+__device__ void chf_inverse(float* S, int l, int ld, const float* s_dinv) {
+  const int tid = threadIdx.x;
+  const int nb = (l + NB - 1) / NB;
+  for (int Ib = nb - 1; Ib >= 0; --Ib) {
+    const int r0 = Ib * NB, rb = min(NB, l - r0);
+    const int cs = r0 + rb, ncol = l - cs;   // ncol > 0 only for full blocks
+    if (ncol > 0) {
+      // T(i, c) = -sum_{t = cs}^{c} R(i, t) X(t, c): 4 x 4 register tiles
+      {
+        const int ncq = (ncol + 3) / 4;
+        const bool have = tid < 8 * ncq;
+        float acc[4][4];
+        int i0 = 0, k0 = 0;
+        if (have) {
+          const int rg = tid / ncq;
+          i0 = r0 + 4 * rg;
+          k0 = cs + 4 * (tid - rg * ncq);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[q][w] = 0.f;
+          for (int t = cs; t < k0; t += 4) {   // rows of X above the tile: all upper
+            float ra[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 r4 = lds4(S + (i0 + q) * ld + t);
+              ra[q][0] = r4.x; ra[q][1] = r4.y; ra[q][2] = r4.z; ra[q][3] = r4.w;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float4 x4 = lds4(S + (t + e) * ld + k0);
+              const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[q][w] = fmaf(ra[q][e], xv[w], acc[q][w]);
+            }
+          }
+          const int te = min(l, k0 + 4);
+          for (int t = k0; t < te; ++t) {       // the tile's own diagonal band
+            const float4 x4 = lds4(S + t * ld + k0);
+            const float xr[4] = {x4.x, x4.y, x4.z, x4.w};
+            float xv[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) xv[w] = (k0 + w >= t) ? xr[w] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float r = S[(i0 + q) * ld + t];
+#pragma unroll
+              for (int w = 0; w < 4; ++w) acc[q][w] = fmaf(r, xv[w], acc[q][w]);
+            }
+          }
+        }
+        __syncthreads();
+        if (have) {   // padding columns receive 0 (X is zero there)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4*>(S + (i0 + q) * ld + k0) =
+                make_float4(-acc[q][0], -acc[q][1], -acc[q][2], -acc[q][3]);
+        }
+        __syncthreads();
+      }
+      // X(i, c) = sum_{t >= i} D_I(i, t) T(t, c): 4 x 4 register tiles
+      {
+        const int ncq = (ncol + 3) / 4;
+        const bool have = tid < 8 * ncq;
+        float acc[4][4];
+        int i0 = 0, c = 0;
+        if (have) {
+          const int rg = tid / ncq;
+          i0 = 4 * rg;
+          c = cs + 4 * (tid - rg * ncq);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[q][w] = 0.f;
+          for (int t = i0; t < NB; ++t) {
+            // D_I(i, t), i = i0 .. i0 + 3, sits at S(r0 + t, r0 + i) for t > i
+            const float4 da = lds4(S + (r0 + t) * ld + r0 + i0);
+            float dv[4] = {da.x, da.y, da.z, da.w};
+            if (t < i0 + 4) {
+              const float dd = s_dinv[r0 + t];
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                dv[q] = (t > i0 + q) ? dv[q] : ((t == i0 + q) ? dd : 0.f);
+            }
+            const float4 t4 = lds4(S + (r0 + t) * ld + c);
+            const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int w = 0; w < 4; ++w) acc[q][w] = fmaf(dv[q], tv[w], acc[q][w]);
+          }
+        }
+        __syncthreads();
+        if (have) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4*>(S + (r0 + i0 + q) * ld + c) =
+                make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+        }
+      }
+    }
+    // X(I, I) = D_I into the block's upper triangle (D_I^T stays below)
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      const int i = e >> 5, cc = e & 31;
+      if (i < rb && cc < rb && cc >= i)
+        S[(r0 + i) * ld + r0 + cc] = (cc == i) ? s_dinv[r0 + i] : S[(r0 + cc) * ld + r0 + i];
     }
     __syncthreads();
   }
 }
 
-// In-place inverse of the upper-triangular R in S (padded ld), block rows
-// from the bottom:  T = E_I - R(I, I+1:) X(I+1:, :) with the product on 4 x 4
-// register tiles (K range clipped to the tile's columns, X upper triangular),
-// then X(I, :) = R_II^{-1} T by back substitution per column.
-__device__ void inv_upper_tiled(float* S, int l, int ld, const float* s_dinv) {
-  __shared__ float Rd[NB][NB + 1];
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
-  // the strictly lower triangle holds Gram entries: zero it (X is upper triangular)
-  for (int e = tid; e < l * l; e += nthr) {
-    const int i = e / l, c = e - i * l;
-    if (c < i) S[i * ld + c] = 0.f;
+// Upper triangle of S (identity on the padding up to L) to a row-major L x L
+// fp32 matrix: one row per warp, four columns per lane (L % 4 == 0).
+__device__ void chf_store_upper(const float* S, int l, int ld, int L, float* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < L; i += nw) {
+    for (int c = 4 * lane; c < L; c += 128) {
+      float v[4];
+      if (i < l && c + 3 < ld) {
+        const float4 s4 = lds4(S + i * ld + c);
+        v[0] = s4.x; v[1] = s4.y; v[2] = s4.z; v[3] = s4.w;
+      }
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int cc = c + w;
+        if (i < l && cc < l) v[w] = cc >= i ? v[w] : 0.f;
+        else v[w] = (i == cc) ? 1.f : 0.f;
+      }
+      *reinterpret_cast<float4*>(out + (size_t)i * L + c) = make_float4(v[0], v[1], v[2], v[3]);
+    }
   }
-  __syncthreads();
-  const int nb = (l + NB - 1) / NB;
-  for (int Ib = nb - 1; Ib >= 0; --Ib) {
-    const int r0 = Ib * NB, rb = min(NB, l - r0);
-    const int cs = r0 + rb;                 // first column of the off-diagonal part
-    for (int t = tid; t < NB * NB; t += nthr) {
-      const int i = t / NB, c = t - i * NB;
-      Rd[i][c] = (i < rb && c < rb && c >= i) ? S[(r0 + i) * ld + r0 + c] : 0.f;
-    }
-    // T(i, c) = -sum_{t = cs}^{c} R(i, t) X(t, c) for c >= cs, in registers
-    // (at most two 4 x 4 tiles per thread: 8 x ceil((l - cs) / 4) <= 2 nthr)
-    const int nTc = (l - cs + 3) / 4;
-    const int ntiles = (NB / 4) * nTc;
-    float acc[2][4][4];
-    int i0s[2], k0s[2];
+}
+
+// W^T with W = R^{-1} (Wt[j][kk] = X[kk][j]) as three bf16 terms: each warp
+// takes 32 x 32 tiles; lane j reads column j of the tile (rows kk, coalesced
+// across lanes) and writes its 32 consecutive entries of row j of Wt.
+__device__ void chf_store_w(const float* S, int l, int ld, int L, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, __nv_bfloat16* lo2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nt = (L + 31) / 32;
+  for (int tt = warp; tt < nt * nt; tt += nw) {
+    const int tj = tt / nt, tk = tt - tj * nt;
+    const int j = 32 * tj + lane;
+    if (j >= L) continue;
+    for (int k8 = 0; k8 < 32; k8 += 8) {
+      uint32_t ph[4], pm[4], pl[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int u = tid + h * nthr;
-      i0s[h] = -1;
-      k0s[h] = 0;
-      if (u < ntiles) {
-        const int ti = u / nTc, tc = u - ti * nTc;
-        const int i0 = r0 + 4 * ti, k0 = cs + 4 * tc;
-        i0s[h] = i0;
-        k0s[h] = k0;
+      for (int h = 0; h < 4; ++h) {
+        float v2[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) acc[h][q][w] = 0.f;
-        const int tmax = min(l, k0 + 4);
-#pragma unroll 2
-        for (int t = cs; t < tmax; ++t) {
-          float a4[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) a4[q] = (i0 + q < r0 + rb) ? S[(i0 + q) * ld + t] : 0.f;
-          const float4 xc = *reinterpret_cast<const float4*>(S + t * ld + k0);
-          const float b4[4] = {xc.x, xc.y, xc.z, xc.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc[h][q][w] = fmaf(a4[q], b4[w], acc[h][q][w]);
+        for (int e = 0; e < 2; ++e) {
+          const int kk = 32 * tk + k8 + 2 * h + e;
+          float v;
+          if (j < l && kk < l) v = (j >= kk) ? S[kk * ld + j] : 0.f;
+          else v = (j == kk) ? 1.f : 0.f;
+          v2[e] = v;
         }
-      }
-    }
-    __syncthreads();                          // R(I, I+1:) read by everyone before T lands
+        uint32_t w3[3][2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (i0s[h] >= 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const int i = i0s[h] + q, c = k0s[h] + w;
-            if (i < r0 + rb && c < l) S[i * ld + c] = -acc[h][q][w];
-          }
-      }
-    }
-    // the diagonal block of T is the identity
-    for (int t = tid; t < rb * rb; t += nthr) {
-      const int i = t / rb, c = t - i * rb;
-      S[(r0 + i) * ld + r0 + c] = (i == c) ? 1.f : 0.f;
-    }
-    __syncthreads();
-    // X(I, c) = R_II^{-1} T(:, c)
-    for (int c = r0 + tid; c < l; c += nthr) {
-      float x[NB];
-#pragma unroll
-      for (int i = NB - 1; i >= 0; --i) {
-        if (i < rb) {
-          float acc2 = S[(r0 + i) * ld + c];
-#pragma unroll
-          for (int t = i + 1; t < NB; ++t)
-            if (t < rb) acc2 -= Rd[i][t] * x[t];
-          x[i] = acc2 * s_dinv[r0 + i];
-        } else {
-          x[i] = 0.f;
+        for (int e = 0; e < 2; ++e) {
+          const __nv_bfloat16 b0 = __float2bfloat16_rn(v2[e]);
+          const float r1 = v2[e] - __bfloat162float(b0);
+          const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+          const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+          w3[0][e] = __bfloat16_as_ushort(b0);
+          w3[1][e] = __bfloat16_as_ushort(b1);
+          w3[2][e] = __bfloat16_as_ushort(b2);
         }
+        ph[h] = w3[0][0] | (w3[0][1] << 16);
+        pm[h] = w3[1][0] | (w3[1][1] << 16);
+        pl[h] = w3[2][0] | (w3[2][1] << 16);
       }
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < rb) S[(r0 + i) * ld + c] = x[i];
+      const int kb = 32 * tk + k8;
+      if (kb + 8 <= L) {
+        const size_t o = (size_t)j * L + kb;
+        *reinterpret_cast<uint4*>(hi + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+        *reinterpret_cast<uint4*>(lo + o) = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+        *reinterpret_cast<uint4*>(lo2 + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+      }
     }
-    __syncthreads();
   }
 }
 
@@ -474,7 +817,7 @@ __device__ void inv_upper_tiled(float* S, int l, int ld, const float* s_dinv) {
 // generic pointer that might alias global memory would serialise the loads).
 template <typename T>
 __device__ __forceinline__ void chol_body(const CholArgs& a, T* S, int ld, T* red, T& s_maxdiag,
-                                          T& s_dev, int& s_fail, float* s_dinv) {
+                                          T& s_dev, int& s_fail) {
   const int l = a.l, L = a.L;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int tx = threadIdx.x, ty = threadIdx.y, nty = blockDim.y;
@@ -515,10 +858,7 @@ __device__ __forceinline__ void chol_body(const CholArgs& a, T* S, int ld, T* re
         S[i * ld + c] = c < l ? G[(int64_t)i * ldg + c] + ((i == c) ? shift : T(0)) : T(0);
     if (tid == 0) s_fail = -1;
     __syncthreads();
-    if (sizeof(T) == 4 && a.sld > 0)
-      chol_tiled((float*)S, l, ld, (float)(tau * maxdiag), &s_fail, s_dinv);
-    else
-      chol_blocked<T>(S, l, tau * maxdiag, &s_fail);
+    chol_blocked<T>(S, l, tau * maxdiag, &s_fail);
     fail = s_fail;
     __syncthreads();
     if (fail < 0) break;
@@ -530,19 +870,7 @@ __device__ __forceinline__ void chol_body(const CholArgs& a, T* S, int ld, T* re
     write_identity_outputs<T>(a);
     return;
   }
-  if (tid == 0 && a.flags) {
-    if (a.pass == 1) {
-      a.flags[1] = used_shift;
-      // conditional second pass (inside the power scheme): only after a shift;
-      // the third pass is skipped unless the second one asks for it
-      a.flags[3] = used_shift ? 0 : 1;
-      a.flags[2] = 1;
-    } else if (a.pass == 2) {
-      a.flags[1] |= used_shift;
-      a.flags[0] = (a.flags[1] || T(l) * s_dev > T(0.5)) ? 1 : 0;
-      a.flags[2] = 1 - a.flags[0];   // skip flag of the third pass
-    }
-  }
+  if (tid == 0) chol_update_flags(a, used_shift, (double)l * (double)s_dev);
   // R out (identity on the padding)
   if (a.R) {
     T* R = (T*)a.R;
@@ -554,10 +882,7 @@ __device__ __forceinline__ void chol_body(const CholArgs& a, T* S, int ld, T* re
         R[i * L + c] = v;
       }
   }
-  if (sizeof(T) == 4 && a.sld > 0)
-    inv_upper_tiled((float*)S, l, ld, s_dinv);
-  else
-    inv_upper_blocked<T>(S, l, a.scratch ? (T*)a.scratch + (size_t)l * l : nullptr);
+  inv_upper_blocked<T>(S, l, a.scratch ? (T*)a.scratch + (size_t)l * l : nullptr);
   if (a.Rinv) {
     T* Ri = (T*)a.Rinv;
     for (int i = ty; i < L; i += nty)
@@ -595,9 +920,7 @@ __global__ void __launch_bounds__(CT) chol_kernel(CholArgs a) {
   __shared__ T red[32];
   __shared__ T s_maxdiag, s_dev;
   __shared__ int s_fail;
-  __shared__ float s_dinv[256];   // 1 / R_ii of the fp32 tiled path (l <= 256 there)
-  chol_body<T>(a, reinterpret_cast<T*>(dsm), a.sld > 0 ? a.sld : a.l, red, s_maxdiag, s_dev,
-               s_fail, s_dinv);
+  chol_body<T>(a, reinterpret_cast<T*>(dsm), a.l, red, s_maxdiag, s_dev, s_fail);
 }
 // ... or in the global scratch (large l)
 template <typename T>
@@ -605,7 +928,64 @@ __global__ void __launch_bounds__(CT) chol_kernel_global(CholArgs a) {
   __shared__ T red[32];
   __shared__ T s_maxdiag, s_dev;
   __shared__ int s_fail;
-  chol_body<T>(a, (T*)a.scratch, a.l, red, s_maxdiag, s_dev, s_fail, nullptr);
+  chol_body<T>(a, (T*)a.scratch, a.l, red, s_maxdiag, s_dev, s_fail);
+}
+
+// fp32, l <= 224: the register-tiled kernel on the padded shared-memory matrix
+__global__ void __launch_bounds__(CHF_T, 1) chol_f32_kernel(CholArgs a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ float red[32];
+  __shared__ float s_maxdiag, s_dev;
+  __shared__ int s_fail;
+  __shared__ float s_dinv[256];
+  __shared__ __align__(16) float rowbuf[2 * NB];
+  float* S = reinterpret_cast<float*>(dsm);
+  const int l = a.l, L = a.L, ld = chf_ld(l);
+  float* Dc = S + l * ld;
+  if (a.skip_idx >= 0 && a.flags && a.flags[a.skip_idx] == 1) {  // pass not needed: R = I
+    write_identity_outputs<float>(a);
+    return;
+  }
+  float md = 0.f, dev = 0.f;
+  bool bad = false;
+  chf_load(a, S, ld, 0.f, &md, &dev, &bad);
+  if (bad) set_info(a.d_info, RSVD_ERR_NUMERIC);
+  block_max<float>(md, red, &s_maxdiag);
+  block_max<float>(dev, red, &s_dev);
+  const float maxdiag = s_maxdiag;
+  if (!(maxdiag > 0.f)) {                        // X = 0 or non-finite: no basis
+    set_info(a.d_info, RSVD_ERR_NOT_SPD);
+    write_identity_outputs<float>(a);
+    return;
+  }
+  const float tau = 4.f * (float)l * 5.9604645e-8f;
+  float shift = 0.f;
+  int used_shift = 0, fail = -1;
+  for (int attempt = 0; attempt < 12; ++attempt) {
+    if (attempt > 0) {
+      __syncthreads();
+      chf_load(a, S, ld, shift, nullptr, nullptr, nullptr);
+    }
+    __syncthreads();
+    fail = chf_factor(S, l, ld, tau * maxdiag, Dc, s_dinv, rowbuf, &s_fail);
+    __syncthreads();
+    if (fail < 0) break;
+    shift = (shift == 0.f) ? tau * maxdiag : shift * 10.f;
+    used_shift = 1;
+  }
+  if (fail >= 0) {
+    set_info(a.d_info, RSVD_ERR_NOT_SPD);
+    write_identity_outputs<float>(a);
+    return;
+  }
+  if (threadIdx.x == 0) chol_update_flags(a, used_shift, (double)l * (double)s_dev);
+  if (a.R) chf_store_upper(S, l, ld, L, (float*)a.R);
+  __syncthreads();                               // R read before the inverse overwrites it
+  chf_inverse(S, l, ld, s_dinv);
+  if (a.Rinv) chf_store_upper(S, l, ld, L, (float*)a.Rinv);
+  if (a.Whi)
+    chf_store_w(S, l, ld, L, (__nv_bfloat16*)a.Whi, (__nv_bfloat16*)a.Wlo,
+                (__nv_bfloat16*)a.Wlo2);
 }
 
 // Racc <- R * Racc for upper-triangular L x L matrices (through tmp).
@@ -624,30 +1004,36 @@ __global__ void trmm_upper_kernel(int L, const T* __restrict__ R, const T* __res
 template <typename T>
 cudaError_t launch_chol(const CholArgs& a, cudaStream_t s) {
   const size_t bytes = (size_t)a.l * a.l * sizeof(T);
-  CholArgs b = a;
-  b.sld = 0;
-  size_t dyn = 0;
-  const size_t tiled = (size_t)a.l * chol_ld(a.l) * sizeof(float);
-  if (sizeof(T) == 4 && tiled <= SMEM_LIMIT) {   // fp32 register-tiled path
-    b.scratch = nullptr;
-    b.sld = chol_ld(a.l);
-    dyn = tiled;
-  } else if (bytes <= SMEM_LIMIT) {
-    b.scratch = nullptr;
-    dyn = bytes;
-  } else if (a.scratch == nullptr) {
-    return cudaErrorInvalidValue;
-  }
-  if (dyn > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(chol_kernel<T>,
+  // the fp32 kernel: its matrix plus about 2 KB of static arrays in one CTA,
+  // 16-byte R rows and W rows
+  const bool f32 = sizeof(T) == 4 && a.l <= CHF_LMAX && chf_smem(a.l) + 2048 <= 232448 &&
+                   a.L % 4 == 0 && (a.Whi == nullptr || a.L % 8 == 0);
+  const int tr_ = trace_begin(RSVD_TRACE_CHOL, s);
+  if (f32) {
+    const size_t dyn = chf_smem(a.l);
+    cudaError_t e = cudaFuncSetAttribute(chol_f32_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
+    chol_f32_kernel<<<1, CHF_T, dyn, s>>>(a);
+  } else {
+    CholArgs b = a;
+    size_t dyn = 0;
+    if (bytes <= SMEM_LIMIT) {
+      b.scratch = nullptr;
+      dyn = bytes;
+    } else if (a.scratch == nullptr) {
+      return cudaErrorInvalidValue;
+    }
+    if (dyn > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(chol_kernel<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e != cudaSuccess) return e;
+    }
+    if (b.scratch)
+      chol_kernel_global<T><<<1, dim3(32, CT / 32), 0, s>>>(b);
+    else
+      chol_kernel<T><<<1, dim3(32, CT / 32), dyn, s>>>(b);
   }
-  const int tr_ = trace_begin(RSVD_TRACE_CHOL, s);
-  if (b.scratch)
-    chol_kernel_global<T><<<1, dim3(32, CT / 32), 0, s>>>(b);
-  else
-    chol_kernel<T><<<1, dim3(32, CT / 32), dyn, s>>>(b);
   count_launch();
   trace_end(tr_, s);
   return cudaGetLastError();

@@ -98,8 +98,6 @@ struct CholArgs {
   int pass;       // 1, 2 or 3
   int skip_idx;   // when >= 0 and flags[skip_idx] == 1: write R = I and return
   int* d_info;
-  int sld;        // set by the launcher: leading dimension of the shared-memory
-                  // matrix; > l selects the fp32 register-tiled factor and inverse
 };
 template <typename T>
 cudaError_t launch_chol(const CholArgs& a, cudaStream_t s);

@@ -252,8 +252,8 @@ struct Engine {
       a.L = L;
       a.G = ob.G;
       a.ldg = L;
-      a.R = ob.R;
-      a.Rinv = ob.Rinv;
+      a.R = want_R ? ob.R : nullptr;
+      a.Rinv = tc ? nullptr : ob.Rinv;   // the tensor-core apply takes the bf16 terms
       a.Whi = tc ? ob.Whi : nullptr;
       a.Wlo = tc ? ob.Wlo : nullptr;
       a.Wlo2 = tc ? ob.Wlo2 : nullptr;
