@@ -17,8 +17,16 @@
  * leading dimension ldx sits at X[i*ldx + j], ldx >= c.  Indices are 0-based.
  * l = k + p is the sketch width.  "dtype" is an rsvd_dtype naming the element
  * type of A; floating outputs have the same type as A for RSVD_F64 (double) and
- * are float for RSVD_F32 (and RSVD_BF16, where supported).  Singular values are
- * always double.
+ * are float for RSVD_F32 and RSVD_BF16.  Singular values are always double.
+ *
+ * RSVD_BF16 (A stored as bf16, the mixed-precision path): accepted by the
+ * whole-path calls (rsvd_qb, rsvd_svd, rsvd_id, rsvd_cur, rsvd_svd_id_cur,
+ * rsvd_svd_id_cur_host) and by rsvd_sample / rsvd_apply, on the tensor-core
+ * path only: A 16-byte aligned with lda % 8 == 0, precision RSVD_PREC_TC,
+ * l + padding <= 256; otherwise RSVD_ERR_UNSUPPORTED.  The bf16 values of A are
+ * exact tensor-core operands: each pass over A issues one product per term of
+ * its right-hand operand and reads 2 bytes per entry.  All other arithmetic
+ * (Gram, CholeskyQR, small SVD, pivoted QR, solves) is the FP32 path's.
  *
  * Ownership: every pointer is caller-owned DEVICE memory on the current CUDA
  * device, except `opts` (host memory, may be NULL for defaults).  The library

@@ -163,7 +163,15 @@ def _dtype_code(t):
         return F32
     if t.dtype == torch.float64:
         return F64
-    raise TypeError("unsupported dtype %s (float32 or float64)" % t.dtype)
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError("unsupported dtype %s (float32, float64 or bfloat16)" % t.dtype)
+
+
+def _out_dtype(dtype):
+    """Floating output type for an A of this dtype: bf16 A gives float32."""
+    torch = _torch()
+    return torch.float32 if dtype == torch.bfloat16 else dtype
 
 
 def _check_matrix(t, name):
@@ -217,8 +225,8 @@ def qb(A, k, p, q, seed, opts=None, check=True):
     m, n = A.shape
     l = k + p
     dt = _dtype_code(A)
-    Q = torch.empty(m, l, dtype=A.dtype, device=A.device)
-    Bt = torch.empty(n, l, dtype=A.dtype, device=A.device)
+    Q = torch.empty(m, l, dtype=_out_dtype(A.dtype), device=A.device)
+    Bt = torch.empty(n, l, dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_qb_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
     if ws == 0:
         raise RsvdError(1, "rsvd_qb_workspace_size")
@@ -238,8 +246,8 @@ def svd(A, k, p, q, seed, opts=None, check=True):
     _check_matrix(A, "A")
     m, n = A.shape
     dt = _dtype_code(A)
-    U = torch.empty(m, k, dtype=A.dtype, device=A.device)
-    V = torch.empty(n, k, dtype=A.dtype, device=A.device)
+    U = torch.empty(m, k, dtype=_out_dtype(A.dtype), device=A.device)
+    V = torch.empty(n, k, dtype=_out_dtype(A.dtype), device=A.device)
     S = torch.empty(k, dtype=torch.float64, device=A.device)
     ws = lib().rsvd_svd_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
     if ws == 0:
@@ -261,7 +269,7 @@ def id(A, k, p, q, seed, opts=None, check=True):  # noqa: A001 - the paper's nam
     m, n = A.shape
     dt = _dtype_code(A)
     J = torch.empty(n, dtype=torch.int32, device=A.device)
-    T = torch.empty(k, max(n - k, 1), dtype=A.dtype, device=A.device)
+    T = torch.empty(k, max(n - k, 1), dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_id_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
     if ws == 0:
         raise RsvdError(1, "rsvd_id_workspace_size")
@@ -283,7 +291,7 @@ def cur(A, k, p, q, seed, opts=None, check=True):
     dt = _dtype_code(A)
     Jc = torch.empty(k, dtype=torch.int32, device=A.device)
     Ir = torch.empty(k, dtype=torch.int32, device=A.device)
-    U = torch.empty(k, k, dtype=A.dtype, device=A.device)
+    U = torch.empty(k, k, dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_cur_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
     if ws == 0:
         raise RsvdError(1, "rsvd_cur_workspace_size")
@@ -304,9 +312,10 @@ class Plan:
                  with_cur=True):
         torch = _torch()
         self.m, self.n, self.k, self.p, self.q = m, n, k, p, q
-        self.dt = {torch.float32: F32, torch.float64: F64}[dtype]
+        self.dt = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16}[dtype]
         self.opts = opts
         dev = torch.device(device)
+        dtype = _out_dtype(dtype)
         self.U = torch.empty(m, k, dtype=dtype, device=dev) if with_svd else None
         self.S = torch.empty(k, dtype=torch.float64, device=dev) if with_svd else None
         self.V = torch.empty(n, k, dtype=dtype, device=dev) if with_svd else None
@@ -383,7 +392,7 @@ def sample(A, l, seed, opts=None):
     _check_matrix(A, "A")
     m, n = A.shape
     dt = _dtype_code(A)
-    Y = torch.empty(m, l, dtype=A.dtype, device=A.device)
+    Y = torch.empty(m, l, dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_sample_workspace_size(m, n, l, dt, _opts_ptr(opts))
     W = _work(ws, A.device)
     st = lib().rsvd_sample(m, n, l, seed, dt, _ptr(A), A.stride(0), _ptr(Y), l, _ptr(W),
@@ -400,7 +409,7 @@ def apply(A, X, trans, opts=None):
     l = X.shape[1]
     dt = _dtype_code(A)
     rows = n if trans else m
-    Y = torch.empty(rows, l, dtype=A.dtype, device=A.device)
+    Y = torch.empty(rows, l, dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_apply_workspace_size(m, n, l, dt, _opts_ptr(opts))
     W = _work(ws, A.device)
     st = lib().rsvd_apply(m, n, l, int(trans), dt, _ptr(A), A.stride(0), _ptr(X), X.stride(0),

@@ -206,7 +206,11 @@ cudaError_t launch_gather_ct(int64_t m, int k, const T* A, int64_t lda, const in
 
 // Double-float planes of W = C^T (k x m), column-major (column r of C^T is
 // row r of C): Wh[r*k + i] = A[r, J[i]], Wl = 0.
-__global__ void gather_ct_df_kernel(int64_t m, int k, const float* __restrict__ A, int64_t lda,
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename S>
+__global__ void gather_ct_df_kernel(int64_t m, int k, const S* __restrict__ A, int64_t lda,
                                     const int32_t* __restrict__ J, float* __restrict__ Wh,
                                     float* __restrict__ Wl) {
   const int64_t total = m * k;
@@ -214,16 +218,21 @@ __global__ void gather_ct_df_kernel(int64_t m, int k, const float* __restrict__ 
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t / k;
     const int i = (int)(t - r * k);
-    Wh[t] = A[r * lda + J[i]];
+    Wh[t] = to_f32(A[r * lda + J[i]]);
     Wl[t] = 0.0f;
   }
 }
 
-cudaError_t launch_gather_ct_df(int64_t m, int k, const float* A, int64_t lda, const int32_t* J,
-                                double* W, cudaStream_t s) {
+cudaError_t launch_gather_ct_df(int64_t m, int k, const void* A, int64_t lda, int a_bf16,
+                                const int32_t* J, double* W, cudaStream_t s) {
   if (m <= 0 || k <= 0) return cudaSuccess;
   float* Wh = reinterpret_cast<float*>(W);
-  gather_ct_df_kernel<<<grid1d(m * k), 256, 0, s>>>(m, k, A, lda, J, Wh, Wh + m * k);
+  if (a_bf16)
+    gather_ct_df_kernel<__nv_bfloat16><<<grid1d(m * k), 256, 0, s>>>(
+        m, k, reinterpret_cast<const __nv_bfloat16*>(A), lda, J, Wh, Wh + m * k);
+  else
+    gather_ct_df_kernel<float><<<grid1d(m * k), 256, 0, s>>>(m, k, (const float*)A, lda, J, Wh,
+                                                             Wh + m * k);
   count_launch();
   return cudaGetLastError();
 }
@@ -246,6 +255,28 @@ cudaError_t launch_gather_rows(int k, int64_t n, const T* A, int64_t lda, const 
                                T* R, int64_t ldr, cudaStream_t s) {
   if (k <= 0 || n <= 0) return cudaSuccess;
   gather_rows_kernel<T><<<grid1d((int64_t)k * n), 256, 0, s>>>(k, n, A, lda, I, R, ldr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// R (k x n, fp32) = rows I of a bf16 A.
+__global__ void gather_rows_bf16_kernel(int k, int64_t n, const __nv_bfloat16* __restrict__ A,
+                                        int64_t lda, const int32_t* __restrict__ I,
+                                        float* __restrict__ R, int64_t ldr) {
+  const int64_t total = (int64_t)k * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n);
+    const int64_t c = t - (int64_t)i * n;
+    R[(int64_t)i * ldr + c] = __bfloat162float(A[(int64_t)I[i] * lda + c]);
+  }
+}
+
+cudaError_t launch_gather_rows_bf16(int k, int64_t n, const void* A, int64_t lda,
+                                    const int32_t* I, float* R, int64_t ldr, cudaStream_t s) {
+  if (k <= 0 || n <= 0) return cudaSuccess;
+  gather_rows_bf16_kernel<<<grid1d((int64_t)k * n), 256, 0, s>>>(
+      k, n, reinterpret_cast<const __nv_bfloat16*>(A), lda, I, R, ldr);
   count_launch();
   return cudaGetLastError();
 }

@@ -53,11 +53,6 @@ __host__ __device__ constexpr int w_bytes(int L) { return L * OBK * 2; }
 __host__ __device__ constexpr int b_stage_bytes(int L) { return 4 * AT_BYTES + w_bytes(L); }
 size_t omega_smem(int L) { return 1024 + (size_t)F_ST * F_BYTES + (size_t)B_ST * b_stage_bytes(L) + 256; }
 
-// Byte offset of the 16-byte chunk c (0..3) of row r in a K-major tile of
-// 64-byte rows with the 64-byte swizzle (8-row groups of 512 bytes).
-__device__ __forceinline__ uint32_t sw64_off(uint32_t r, uint32_t c) {
-  return r * 64u + ((c ^ ((r >> 1) & 3u)) << 4);
-}
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
                                              uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
@@ -79,9 +74,6 @@ __device__ __forceinline__ void st_shared_b32(uint32_t addr, uint32_t a) {
 }
 __device__ __forceinline__ void st_cluster_b32(uint32_t addr, uint32_t a) {
   asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(addr), "r"(a) : "memory");
-}
-__device__ __forceinline__ void st_cluster_v2(uint32_t addr, uint32_t a, uint32_t b) {
-  asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
@@ -446,6 +438,10 @@ __global__ void __launch_bounds__(OTHREADS, 1)
 constexpr int NGEN2 = 16;                       // generator warps 12..27
 constexpr int OTHREADS2 = 32 * (12 + NGEN2);    // 896
 
+// ABF: A holds bf16 values; TMA lands each stage as two 64-byte-swizzled
+// K-major M-tiles that the MMAs read directly (one product per M-tile and
+// K-step); the converter warps only run the epilogue.
+template <bool ABF>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
     tc_omega2_kernel(const __grid_constant__ CUtensorMap mapA, TcParams P) {
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
@@ -476,7 +472,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < F_ST; ++s) {
       mbar_init(&ffull[s], 1);
-      mbar_init(&fempty[s], NCONV);
+      mbar_init(&fempty[s], ABF ? 1 : NCONV);   // ABF: released by the MMAs' commit
     }
     for (int s = 0; s < B_ST; ++s) {
       mbar_init(&aready[s], NCONV);
@@ -513,7 +509,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
       const uint64_t pol_a = l2_policy_evict_first();
       for (int64_t it = it0; it < it1; ++it) {
         if (!mbar_wait(&fempty[fs], fph ^ 1u, abort_flag, P.d_info)) break;
-        mbar_arrive_expect_tx(&ffull[fs], (uint32_t)F_BYTES);
+        mbar_arrive_expect_tx(&ffull[fs], (uint32_t)(ABF ? F_BYTES / 2 : F_BYTES));
         tma_load_2d_hint(fring + fs * F_BYTES, &mapA, &ffull[fs], (int)(kc * OBK),
                          (int)(su * 2 * OUNIT + rank * OUNIT), pol_a);
         last_issued = it - it0;
@@ -543,8 +539,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
       const uint32_t idesc = make_idesc(OBM, L);
       int64_t seg = -1;
       int64_t kc = it0 % P.kiters;
-      int bs = 0;
-      uint32_t bph = 0;
+      int bs = 0, fs = 0;
+      uint32_t bph = 0, fph = 0;
       for (int64_t it = it0; it < it1; ++it) {
         const bool seg_start = (it == it0) || (kc == 0);
         if (seg_start) {
@@ -552,10 +548,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
           if (seg > 0 && !mbar_wait(acc_empty, (uint32_t)((seg - 1) & 1), abort_flag, P.d_info))
             break;
         }
-        if (!mbar_wait(&aready[bs], bph, abort_flag, P.d_info)) break;
+        if (ABF) {
+          if (!mbar_wait(&ffull[fs], fph, abort_flag, P.d_info)) break;
+        } else {
+          if (!mbar_wait(&aready[bs], bph, abort_flag, P.d_info)) break;
+        }
         if (!mbar_wait_cluster(&wready[bs], bph, abort_flag, P.d_info)) break;
         tc_fence_after();
         const uint32_t base = smem_u32(bring + bs * BSB);
+        const uint32_t fbase = smem_u32(fring + fs * F_BYTES);
 #pragma unroll
         for (int kk = 0; kk < OBK / 16; ++kk) {
           const uint64_t bw = sw64_desc(base + 4u * AT_BYTES + 32u * kk);
@@ -563,11 +564,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
             const uint32_t d = tmem + ACC_STRIDE * (uint32_t)t;
-            mma_ss(d, sw64_desc(base + (uint32_t)(2 * t) * AT_BYTES + 32u * kk), bw, idesc, acc0);
-            mma_ss(d, sw64_desc(base + (uint32_t)(2 * t + 1) * AT_BYTES + 32u * kk), bw, idesc, 1u);
+            if (ABF) {
+              mma_ss(d, sw64_desc(fbase + (uint32_t)t * AT_BYTES + 32u * kk), bw, idesc, acc0);
+            } else {
+              mma_ss(d, sw64_desc(base + (uint32_t)(2 * t) * AT_BYTES + 32u * kk), bw, idesc,
+                     acc0);
+              mma_ss(d, sw64_desc(base + (uint32_t)(2 * t + 1) * AT_BYTES + 32u * kk), bw, idesc,
+                     1u);
+            }
           }
         }
         mma_commit(&bdone[bs]);
+        if (ABF) mma_commit(&fempty[fs]);
+        if (++fs == F_ST) {
+          fs = 0;
+          fph ^= 1u;
+        }
         const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
         if (seg_end) mma_commit(acc_full);
         if (++kc == P.kiters) kc = 0;
@@ -611,6 +623,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
         ++seg;
         whole = (kc == 0);
       }
+      if (!ABF) {
       if (!mbar_wait(&ffull[fs], fph, abort_flag, P.d_info)) break;
       float x[32];
       const unsigned char* row = fring + fs * F_BYTES + rr * 128;
@@ -638,6 +651,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&aready[bs]);
+      }
       const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
       if (seg_end) {
         if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag, P.d_info)) break;
@@ -778,6 +792,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
   cluster_sync_all();                     // the peer no longer writes into this CTA
 }
 
+template <bool ABF>
+static cudaError_t launch_omega2_kernel(const CUtensorMap& ma, const TcParams& P, int64_t Gc,
+                                        size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(tc_omega2_kernel<ABF>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tr = trace_begin(RSVD_TRACE_A_OMEGA, s);
+  tc_omega2_kernel<ABF><<<(unsigned)(2 * Gc), OTHREADS2, smem, s>>>(ma, P);
+  count_launch();
+  trace_end(tr, s);
+  return cudaGetLastError();
+}
+
 static cudaError_t launch_tc_omega2(const TcGemm& g, cudaStream_t s) {
   int64_t sus, kiters, total, Gc;
   int maxseg;
@@ -809,19 +836,17 @@ static cudaError_t launch_tc_omega2(const TcGemm& g, cudaStream_t s) {
   P.wadd = 0;
   CUtensorMap ma;
   memset(&ma, 0, sizeof(ma));
-  if (!encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, (uint64_t)g.a_cols_total,
-                 (uint64_t)g.a_rows_total, (uint64_t)g.lda, OBK, OUNIT,
-                 CU_TENSOR_MAP_SWIZZLE_128B))
+  const bool abf = g.a_bf16 != 0;
+  // 256-row stages: fp32 rows of 128 bytes (converted to bf16 hi/lo tiles) or
+  // bf16 rows of 64 bytes (read by the MMAs as they land)
+  if (!encode_2d(&ma, abf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                 abf ? 2 : 4, g.A, (uint64_t)g.a_cols_total, (uint64_t)g.a_rows_total,
+                 (uint64_t)g.lda, OBK, OUNIT,
+                 abf ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B))
     return cudaErrorInvalidValue;
   const size_t smem = omega_smem(g.L) + 64;
-  cudaError_t e = cudaFuncSetAttribute(tc_omega2_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int tr = trace_begin(RSVD_TRACE_A_OMEGA, s);
-  tc_omega2_kernel<<<(unsigned)(2 * Gc), OTHREADS2, smem, s>>>(ma, P);
-  count_launch();
-  trace_end(tr, s);
-  e = cudaGetLastError();
+  cudaError_t e = abf ? launch_omega2_kernel<true>(ma, P, Gc, smem, s)
+                      : launch_omega2_kernel<false>(ma, P, Gc, smem, s);
   if (e != cudaSuccess) return e;
   // the two CTAs of a pair form two interleaved stream-K problems (row halves)
   for (int r = 0; r < 2; ++r) {
@@ -837,6 +862,7 @@ static cudaError_t launch_tc_omega2(const TcGemm& g, cudaStream_t s) {
 cudaError_t launch_tc_omega(const TcGemm& g, cudaStream_t s) {
   if (!tc_supported(g.L) || g.form != 0 || !g.omega) return cudaErrorInvalidValue;
   if (device_sm_count() >= 2) return launch_tc_omega2(g, s);
+  if (g.a_bf16) return cudaErrorNotSupported;   // the 1-CTA kernel takes fp32 A only
   int64_t tiles, kiters, total, G;
   int maxseg;
   sk_plan(g.rows, g.K, OUNIT, OBK, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);

@@ -11,6 +11,8 @@
 //   NW = 2  stored matrix of generic data (Q, Z, X): a0 w0 + a1 w0 + a0 w1
 //   NW = 3  the l x l factor R^-1 of CholeskyQR:     a0 w0 + a1 w0 + a0 w1 + a0 w2
 //   NW = 4  Gram X^T X (W = split of X itself):      a0 w0 + a1 w0 + a0 w1 + a1 w1
+// A stored in bf16 (a_bf16) is exact as a0 (a1 = 0): its passes issue one
+// product per W term and stream half the bytes.
 // For two different matrices the dropped term a1 w1 and the rounding residuals
 // are independent from entry to entry and only add noise of relative size
 // 2^-17.  R^-1 is one fixed matrix applied to every row, so its rounding would
@@ -46,7 +48,7 @@ namespace {
 constexpr int BM = 128;             // output rows per tile (MMA M)
 constexpr int BK = 32;              // K per stage
 constexpr int MAXST = 4;            // stages (3 when W has three bf16 terms)
-constexpr int A_STAGE_BYTES = BM * BK * 4;   // 16 KB fp32
+constexpr int A_STAGE_BYTES = BM * BK * 4;   // 16 KB fp32 (a bf16 A tile uses the first half)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TMEM_A0 = 256;   // first TMEM column of the A stages
 constexpr int NCONV = 4;            // converter / epilogue warps (4..7)
@@ -66,7 +68,7 @@ __device__ __forceinline__ int64_t sk_start(int64_t b, int64_t total, int64_t G)
   return (b * total) / G;
 }
 
-template <int FORM, int NW>
+template <int FORM, int NW, bool ABF>
 __global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                    const __grid_constant__ CUtensorMap mapW0,
@@ -128,7 +130,8 @@ __global__ void __launch_bounds__(256, 1)
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
     if (lane == 0) {
-      const uint32_t bytes = A_STAGE_BYTES + (uint32_t)NWT * (uint32_t)w_tile_bytes(L);
+      const uint32_t bytes =
+          (ABF ? A_STAGE_BYTES / 2 : A_STAGE_BYTES) + (uint32_t)NWT * (uint32_t)w_tile_bytes(L);
       int64_t last_issued = -1;
       int64_t tile = it0 / P.kiters, kc = it0 - tile * P.kiters;
       int s = 0;
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(256, 1)
           const uint32_t alo = a_col + 16u + 8u * kk;
           const uint32_t acc0 = (seg_start && kk == 0) ? 0u : 1u;
           mma_ts(tmem, ahi, bhi, idesc, acc0);
-          mma_ts(tmem, alo, bhi, idesc, 1u);
+          if (!ABF) mma_ts(tmem, alo, bhi, idesc, 1u);
 #pragma unroll
           for (int t = 1; t < NWT; ++t) {
             const uint64_t bt = sw64_desc(wbase + (uint32_t)(t * w_tile_bytes(L)) + 32u * kk);
@@ -243,6 +246,28 @@ __global__ void __launch_bounds__(256, 1)
       }
       tc_fence_after();
       const unsigned char* st = dsm + s * SB;
+      const uint32_t a_col = tmem + TMEM_A0 + 32u * (uint32_t)s;
+      if (ABF) {
+        // bf16 A: the tile row (form 0, 64-byte swizzled rows of 32 values) or
+        // column (form 1, plain 32 x 128 tile) goes to TMEM as it is
+        uint32_t hi[16];
+        if (FORM == 0) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint4 v = *reinterpret_cast<const uint4*>(st + sw64_off((uint32_t)r, (uint32_t)c));
+            hi[4 * c] = v.x;
+            hi[4 * c + 1] = v.y;
+            hi[4 * c + 2] = v.z;
+            hi[4 * c + 3] = v.w;
+          }
+        } else {
+          const unsigned short* t = reinterpret_cast<const unsigned short*>(st);
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            hi[k] = (uint32_t)t[(2 * k) * BM + r] | ((uint32_t)t[(2 * k + 1) * BM + r] << 16);
+        }
+        tmem_st16(lane_base + a_col, hi);
+      } else {
       float x[32];
       if (FORM == 0) {
         // 128B-swizzled rows of 32 fp32: 16-byte chunk c of row r sits at c ^ (r & 7)
@@ -263,9 +288,9 @@ __global__ void __launch_bounds__(256, 1)
       }
       uint32_t hi[16], lo[16];
       split_row(x, hi, lo);
-      const uint32_t a_col = tmem + TMEM_A0 + 32u * (uint32_t)s;
       tmem_st16(lane_base + a_col, hi);
       tmem_st16(lane_base + a_col + 16u, lo);
+      }
       tmem_wait_st();
       tc_fence_before();
       __syncwarp();
@@ -502,10 +527,10 @@ cudaError_t launch_tc_reduce(const TcParams& P, int G, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int FORM, int NW>
+template <int FORM, int NW, bool ABF = false>
 static cudaError_t launch_form(const CUtensorMap& ma, const CUtensorMap* mw, const TcParams& P,
                                int G, size_t smem, cudaStream_t s) {
-  auto kern = tc_gemm_kernel<FORM, NW>;
+  auto kern = tc_gemm_kernel<FORM, NW, ABF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -555,18 +580,21 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   memset(&ma, 0, sizeof(ma));
   memset(mw, 0, sizeof(mw));
   bool ok;
-  if (g.form == 0)
-    ok = encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, (uint64_t)g.a_cols_total,
-                   (uint64_t)g.a_rows_total, (uint64_t)g.lda, BK, BM,
-                   CU_TENSOR_MAP_SWIZZLE_128B);
+  const bool abf = g.a_bf16 != 0;
+  const CUtensorMapDataType adt = abf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const int aes = abf ? 2 : 4;
+  if (g.form == 0)   // rows of BK values: 128 bytes (fp32) or 64 bytes (bf16), swizzled
+    ok = encode_2d(&ma, adt, aes, g.A, (uint64_t)g.a_cols_total, (uint64_t)g.a_rows_total,
+                   (uint64_t)g.lda, BK, BM,
+                   abf ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
   else
-    ok = encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, (uint64_t)g.a_cols_total,
-                   (uint64_t)g.a_rows_total, (uint64_t)g.lda, BM, BK,
-                   CU_TENSOR_MAP_SWIZZLE_NONE);
+    ok = encode_2d(&ma, adt, aes, g.A, (uint64_t)g.a_cols_total, (uint64_t)g.a_rows_total,
+                   (uint64_t)g.lda, BM, BK, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!ok) return cudaErrorInvalidValue;
   const int nw = g.gram ? 4 : g.wterms;
   if (nw < 2 || nw > 4 || (g.gram && g.wterms != 2))
     return cudaErrorInvalidValue;
+  if (abf && nw != 2) return cudaErrorInvalidValue;   // bf16 A: stored-W passes only
   const int nwt = w_tiles(nw);
   const void* wp[3] = {g.Whi, g.Wlo, g.Wlo2};
   for (int t = 0; t < nwt; ++t) {
@@ -579,7 +607,11 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   const size_t smem = (size_t)stages_for(nw) * stage_bytes(g.L, nw) + 1024 /*align*/ +
                       (4 * MAXST + 2) * 8 + 16;
   cudaError_t e;
-  if (g.form == 0 && nw == 2)
+  if (abf && g.form == 0)
+    e = launch_form<0, 2, true>(ma, mw, P, (int)G, smem, s);
+  else if (abf)
+    e = launch_form<1, 2, true>(ma, mw, P, (int)G, smem, s);
+  else if (g.form == 0 && nw == 2)
     e = launch_form<0, 2>(ma, mw, P, (int)G, smem, s);
   else if (g.form == 0 && nw == 3)
     e = launch_form<0, 3>(ma, mw, P, (int)G, smem, s);

@@ -62,10 +62,13 @@ cudaError_t launch_sign_fix(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V
 template <typename T>
 cudaError_t launch_gather_ct(int64_t m, int k, const T* A, int64_t lda, const int32_t* J,
                              double* W, cudaStream_t s);
-// Double-float planes (hi = the fp32 value, lo = 0) of the same W, column-
+// Double-float planes (hi = the fp32 or bf16 value, lo = 0) of the same W, column-
 // major, in the working area W (2 k m floats).
-cudaError_t launch_gather_ct_df(int64_t m, int k, const float* A, int64_t lda, const int32_t* J,
-                                double* W, cudaStream_t s);
+cudaError_t launch_gather_ct_df(int64_t m, int k, const void* A, int64_t lda, int a_bf16,
+                                const int32_t* J, double* W, cudaStream_t s);
+// R (k x n, fp32) = rows I of a bf16 A (ld lda)
+cudaError_t launch_gather_rows_bf16(int k, int64_t n, const void* A, int64_t lda,
+                                    const int32_t* I, float* R, int64_t ldr, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gather_rows(int k, int64_t n, const T* A, int64_t lda, const int32_t* I,
                                T* R, int64_t ldr, cudaStream_t s);
@@ -179,8 +182,10 @@ struct TcGemm {
   int64_t K;            // contraction length
   int L;                // output columns (multiple of 16, <= 256)
   int lvalid;           // Omega columns >= lvalid are zero
-  const float* A;       // fp32 source, row-major, 16-byte aligned, lda % 4 == 0
+  const float* A;       // source, row-major, 16-byte aligned rows: fp32 (lda % 4 == 0) or,
+                        // with a_bf16, bf16 values (lda % 8 == 0) behind this pointer
   int64_t lda;          // elements
+  int a_bf16;           // A holds bf16: one product per W term (a0 exact), half the bytes
   int64_t a_rows_total; // rows of the A tensor (form 0: rows, form 1: K)
   int64_t a_cols_total; // cols of the A tensor (form 0: K, form 1: rows)
   int wterms;           // stored W: 2 (hi, lo) or 3 (hi, mid, lo) bf16 terms

@@ -45,6 +45,9 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   int* d_info = nullptr;
   cudaError_t err = cudaSuccess;
+  // A holds bf16 values (RSVD_BF16, tensor-core path): the passes over A read
+  // it as bf16 and the CUR gathers convert; everything else is fp32
+  int abf = 0;
   // host-input call: A arrives in row chunks, chunk ci complete at chunk_ev[ci]
   int nchunks = 0;
   int64_t chunk_rows = 0;
@@ -108,10 +111,11 @@ struct Engine {
   rsvd_status gemm_n(int64_t rows, int64_t K, int L, const T* A, int64_t lda, int64_t a_rows,
                      int64_t a_cols, bool omega, uint64_t seed, int lvalid, const Split* w,
                      const T* Wsimt, int64_t ldws, T* out, int64_t ldo, int ncols, Split* out_split,
-                     float* part, const int* skip) {
+                     float* part, const int* skip, bool a_bf16 = false) {
     if (tc) {
       TcGemm g{};
       g.form = 0;
+      g.a_bf16 = a_bf16 ? 1 : 0;
       g.omega = omega ? 1 : 0;
       g.seed = seed;
       g.rows = rows;
@@ -147,10 +151,12 @@ struct Engine {
   // Z (rows x L) = A^T W with A (K x rows).
   rsvd_status gemm_t(int64_t rows, int64_t K, int L, const T* A, int64_t lda, const Split* w,
                      const T* Wsimt, int64_t ldws, T* out, int64_t ldo, int ncols,
-                     Split* out_split, float* part, T* slabs, const int* skip, bool gram = false) {
+                     Split* out_split, float* part, T* slabs, const int* skip, bool gram = false,
+                     bool a_bf16 = false) {
     if (tc) {
       TcGemm g{};
       g.form = 1;
+      g.a_bf16 = a_bf16 ? 1 : 0;
       g.rows = rows;
       g.K = K;
       g.L = L;
@@ -350,13 +356,15 @@ struct Engine {
         Split ysc = b.ys;
         ysc.hi = (uint16_t*)b.ys.hi + r0;
         ysc.lo = (uint16_t*)b.ys.lo + r0;
-        st = gemm_n(r1 - r0, n, L, A + r0 * lda, lda, r1 - r0, n, true, seed, l, nullptr, nullptr,
-                    0, b.Y + r0 * L, L, L, &ysc, b.part, nullptr);
+        const T* Ac = reinterpret_cast<const T*>(reinterpret_cast<const char*>(A) +
+                                                 r0 * lda * (c.abf ? 2 : (int64_t)sizeof(T)));
+        st = gemm_n(r1 - r0, n, L, Ac, lda, r1 - r0, n, true, seed, l, nullptr, nullptr, 0,
+                    b.Y + r0 * L, L, L, &ysc, b.part, nullptr, c.abf != 0);
         if (st != RSVD_OK) return st;
       }
     } else {
       st = gemm_n(m, n, L, A, lda, m, n, true, seed, l, nullptr, nullptr, 0, b.Y, L, L, &b.ys,
-                  b.part, nullptr);
+                  b.part, nullptr, c.abf != 0);
       if (st != RSVD_OK) return st;
     }
     int prod = 0;  // index of the next product with A or A^T (Alg. 5 orth test)
@@ -368,7 +376,8 @@ struct Engine {
       }
       ++prod;
       // Z = A^* Y (Sec. 3.2)
-      st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr);
+      st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr,
+                  false, c.abf != 0);
       if (st != RSVD_OK) return st;
       if (prod % o.s == 0) {
         st = orth(n, l, L, b.Z, b.Ztmp, &b.zs, b.ob, b.part, b.slabs, false, false);
@@ -378,7 +387,7 @@ struct Engine {
       ++prod;
       // Y = A Z
       st = gemm_n(m, n, L, A, lda, m, n, false, 0, L, &b.zs, b.Z, L, b.Y, L, L, &b.ys, b.part,
-                  nullptr);
+                  nullptr, c.abf != 0);
       if (st != RSVD_OK) return st;
     }
     // Q = orth(Y)
@@ -386,7 +395,8 @@ struct Engine {
     if (st != RSVD_OK) return st;
     std::swap(b.Y, b.Ytmp);
     // Bt = A^* Q (Alg. 5)
-    st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr);
+    st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr, false,
+                c.abf != 0);
     return st;
   }
 
@@ -599,7 +609,7 @@ struct Engine {
     const int Kp = padL(k);
     // C^T columns (rows of C = A(:, J[:k])) in the CPQR layout
     if (sizeof(T) == 4)
-      LK(launch_gather_ct_df(m, k, (const float*)A, lda, idb.J, u.rid.W, c.stream));
+      LK(launch_gather_ct_df(m, k, A, lda, c.abf, idb.J, u.rid.W, c.stream));
     else
       LK(launch_gather_ct<T>(m, k, A, lda, idb.J, u.rid.W, c.stream));
     rsvd_status st = id_core(u.rid, k, m, k, rgaps);
@@ -607,7 +617,10 @@ struct Engine {
     if (Jc) LK(launch_copy_i32(k, idb.J, Jc, c.stream));
     if (Ir) LK(launch_copy_i32(k, u.rid.J, Ir, c.stream));
     // R = A(I, :), R^T (n x Kp, zero padded)
-    LK(launch_gather_rows<T>(k, n, A, lda, u.rid.J, u.R, n, c.stream));
+    if (c.abf)
+      LK(launch_gather_rows_bf16(k, n, A, lda, u.rid.J, (float*)u.R, n, c.stream));
+    else
+      LK(launch_gather_rows<T>(k, n, A, lda, u.rid.J, u.R, n, c.stream));
     LK(cudaMemsetAsync(u.RT, 0, sizeof(T) * n * Kp, c.stream));
     LK(launch_transpose<T, T>(k, n, u.R, n, u.RT, Kp, c.stream));
     if (tc)
@@ -645,7 +658,7 @@ struct Engine {
 // argument checks
 // ------------------------------------------------------------------------
 static bool base_args_ok(int64_t m, int64_t n, int k, int p, int q, int dtype) {
-  if (dtype != RSVD_F32 && dtype != RSVD_F64) return false;
+  if (dtype != RSVD_F32 && dtype != RSVD_F64 && dtype != RSVD_BF16) return false;
   if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 64) return false;
   const int64_t l = (int64_t)k + p;
   if (l > m || l > n || l > 1024) return false;
@@ -655,12 +668,13 @@ static bool base_args_ok(int64_t m, int64_t n, int k, int p, int q, int dtype) {
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Tensor-core path usable: FP32, requested, width fits, A TMA-addressable.
+// Tensor-core path usable: FP32 or BF16 A, requested, width fits, A
+// TMA-addressable (16-byte aligned base and rows).
 static bool want_tc(int dtype, const Opts& o, int l, const void* A, int64_t lda) {
-  if (dtype != RSVD_F32 || o.precision != RSVD_PREC_TC) return false;
+  if ((dtype != RSVD_F32 && dtype != RSVD_BF16) || o.precision != RSVD_PREC_TC) return false;
   if (!tc_supported(padL(l))) return false;
   if (A && !aligned16(A)) return false;
-  if (lda % 4 != 0) return false;
+  if (lda % (dtype == RSVD_BF16 ? 8 : 4) != 0) return false;
   return true;
 }
 
@@ -748,16 +762,17 @@ static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n,
       LK(cudaStreamWaitEvent(hs->s, hs->fork, 0));
       for (int ci = 0; ci < nch; ++ci) {
         const int64_t r0 = ci * rows, r1 = std::min(m, r0 + rows);
-        LK(cudaMemcpyAsync((T*)A + r0 * lda, A_host + r0 * lda, sizeof(T) * (size_t)(r1 - r0) * lda,
-                           cudaMemcpyHostToDevice, hs->s));
+        const size_t es = c.abf ? 2 : sizeof(T);
+        LK(cudaMemcpyAsync((char*)A + r0 * lda * es, (const char*)A_host + r0 * lda * es,
+                           es * (size_t)(r1 - r0) * lda, cudaMemcpyHostToDevice, hs->s));
         LK(cudaEventRecord(hs->chunk[ci], hs->s));
       }
       c.nchunks = nch;
       c.chunk_rows = rows;
       c.chunk_ev = hs->chunk;
     } else {
-      LK(cudaMemcpyAsync((T*)A, A_host, sizeof(T) * (size_t)m * lda, cudaMemcpyHostToDevice,
-                         c.stream));
+      LK(cudaMemcpyAsync((T*)A, A_host, (c.abf ? 2 : sizeof(T)) * (size_t)m * lda,
+                         cudaMemcpyHostToDevice, c.stream));
     }
   }
   rsvd_status st = e.qb(qbb, m, n, l, q, seed, A, lda);
@@ -838,11 +853,14 @@ static size_t ws_query(int64_t m, int64_t n, int k, int p, int q, int dtype,
   if (!read_opts(opts, &o) || !base_args_ok(m, n, k, p, q, dtype)) return 0;
   const bool tc = want_tc(dtype, o, k + p, nullptr, 0);
   if (dtype == RSVD_F64) return size_all<double>(o, false, m, n, k, p, want);
+  if (dtype == RSVD_BF16) return tc ? size_all<float>(o, true, m, n, k, p, want) : 0;
   // Both variants may be chosen at call time (alignment of A): report the max.
   size_t s1 = size_all<float>(o, false, m, n, k, p, want);
   size_t s2 = tc ? size_all<float>(o, true, m, n, k, p, want) : 0;
   return s1 > s2 ? s1 : s2;
 }
+
+static int d_abf(int dtype) { return dtype == RSVD_BF16 ? 1 : 0; }
 
 static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
                             const void* A, int64_t lda, int want, void* Qo, int64_t ldq,
@@ -853,10 +871,7 @@ static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t 
                             const rsvd_opts* opts, const void* A_host = nullptr) {
   Opts o;
   if (!read_opts(opts, &o)) return RSVD_ERR_INVALID_ARG;
-  if (!base_args_ok(m, n, k, p, q, dtype)) {
-    if (dtype == RSVD_BF16) return RSVD_ERR_UNSUPPORTED;
-    return RSVD_ERR_INVALID_ARG;
-  }
+  if (!base_args_ok(m, n, k, p, q, dtype)) return RSVD_ERR_INVALID_ARG;
   if (!A || lda < n) return RSVD_ERR_INVALID_ARG;
   const int l = k + p;
   if ((want & W_Q) && ((Qo && ldq < l) || (Bto && ldbt < l) || (!Qo && !Bto)))
@@ -892,7 +907,11 @@ static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t 
                          (const double*)A_host);
   } else {
     const bool tc = want_tc(dtype, o, l, A, lda);
+    // bf16 A runs on the tensor-core path only (its SIMT kernels read fp32)
+    if (dtype == RSVD_BF16 && !tc) return RSVD_ERR_UNSUPPORTED;
+    c.abf = d_abf(dtype);
     Ctx d;
+    d.abf = c.abf;
     run_all<float>(d, o, tc, m, n, k, p, q, seed, nullptr, lda, want, nullptr, 0, nullptr, 0,
                    nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr,
                    nullptr, 0);
@@ -1035,6 +1054,8 @@ rsvd_status rsvd_svd_id_cur_host(int64_t m, int64_t n, int k, int p, int q, uint
 namespace rsvd {
 
 static bool dtype_ok(int dtype) { return dtype == RSVD_F32 || dtype == RSVD_F64; }
+// The passes over A (sample, apply) also take bf16 A, on the tensor-core path.
+static bool a_dtype_ok(int dtype) { return dtype_ok(dtype) || dtype == RSVD_BF16; }
 
 template <typename T>
 static rsvd_status sample_impl(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n, int l,
@@ -1045,7 +1066,7 @@ static rsvd_status sample_impl(Ctx& c, const Opts& o, bool tc, int64_t m, int64_
   if (c.dry) return RSVD_OK;
   if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
   return e.gemm_n(m, n, L, A, lda, m, n, true, seed, l, nullptr, nullptr, 0, Y, ldy, l, nullptr,
-                  part, nullptr);
+                  part, nullptr, c.abf != 0);
 }
 
 template <typename T>
@@ -1070,8 +1091,9 @@ static rsvd_status apply_impl(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t
   if (tc) LK(launch_split_transpose(K, l, L, (const float*)X, ldx, w.hi, w.lo, w.ld, c.stream));
   if (!trans)
     return e.gemm_n(rows, K, L, A, lda, m, n, false, 0, L, &w, X, ldx, Y, ldy, l, nullptr, part,
-                    nullptr);
-  return e.gemm_t(rows, K, L, A, lda, &w, X, ldx, Y, ldy, l, nullptr, part, slabs, nullptr);
+                    nullptr, c.abf != 0);
+  return e.gemm_t(rows, K, L, A, lda, &w, X, ldx, Y, ldy, l, nullptr, part, slabs, nullptr, false,
+                  c.abf != 0);
 }
 
 template <typename T>
@@ -1180,9 +1202,10 @@ static bool sizes_ok(int64_t m, int64_t n, int l) {
 
 size_t rsvd_sample_workspace_size(int64_t m, int64_t n, int l, int dtype, const rsvd_opts* opts) {
   Opts o;
-  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(m, n, l)) return 0;
+  if (!read_opts(opts, &o) || !a_dtype_ok(dtype) || !sizes_ok(m, n, l)) return 0;
   Ctx c;
   const bool tc = want_tc(dtype, o, l, nullptr, 0);
+  if (dtype == RSVD_BF16 && !tc) return 0;
   if (dtype == RSVD_F64)
     sample_impl<double>(c, o, false, m, n, l, 0, nullptr, n, nullptr, l);
   else
@@ -1194,7 +1217,8 @@ rsvd_status rsvd_sample(int64_t m, int64_t n, int l, uint64_t seed, int dtype, c
                         int64_t lda, void* Y, int64_t ldy, void* work, size_t work_bytes,
                         void* stream, const rsvd_opts* opts) {
   Opts o;
-  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(m, n, l)) return RSVD_ERR_INVALID_ARG;
+  if (!read_opts(opts, &o) || !a_dtype_ok(dtype) || !sizes_ok(m, n, l))
+    return RSVD_ERR_INVALID_ARG;
   if (!A || !Y || lda < n || ldy < l) return RSVD_ERR_INVALID_ARG;
   if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
   Ctx c = make_ctx(work, work_bytes, nullptr, stream);
@@ -1203,6 +1227,8 @@ rsvd_status rsvd_sample(int64_t m, int64_t n, int l, uint64_t seed, int dtype, c
     st = sample_impl<double>(c, o, false, m, n, l, seed, (const double*)A, lda, (double*)Y, ldy);
   } else {
     const bool tc = want_tc(dtype, o, l, A, lda);
+    if (dtype == RSVD_BF16 && !tc) return RSVD_ERR_UNSUPPORTED;
+    c.abf = dtype == RSVD_BF16 ? 1 : 0;
     st = sample_impl<float>(c, o, tc, m, n, l, seed, (const float*)A, lda, (float*)Y, ldy);
   }
   return finish(c, st);
@@ -1210,7 +1236,8 @@ rsvd_status rsvd_sample(int64_t m, int64_t n, int l, uint64_t seed, int dtype, c
 
 size_t rsvd_apply_workspace_size(int64_t m, int64_t n, int l, int dtype, const rsvd_opts* opts) {
   Opts o;
-  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(m, n, l)) return 0;
+  if (!read_opts(opts, &o) || !a_dtype_ok(dtype) || !sizes_ok(m, n, l)) return 0;
+  if (dtype == RSVD_BF16 && !want_tc(dtype, o, l, nullptr, 0)) return 0;
   size_t best = 0;
   for (int trans = 0; trans < 2; ++trans) {
     Ctx c;
@@ -1232,7 +1259,8 @@ rsvd_status rsvd_apply(int64_t m, int64_t n, int l, int trans, int dtype, const 
                        int64_t lda, const void* X, int64_t ldx, void* Y, int64_t ldy, void* work,
                        size_t work_bytes, void* stream, const rsvd_opts* opts) {
   Opts o;
-  if (!read_opts(opts, &o) || !dtype_ok(dtype) || !sizes_ok(m, n, l)) return RSVD_ERR_INVALID_ARG;
+  if (!read_opts(opts, &o) || !a_dtype_ok(dtype) || !sizes_ok(m, n, l))
+    return RSVD_ERR_INVALID_ARG;
   if (trans != 0 && trans != 1) return RSVD_ERR_INVALID_ARG;
   if (!A || !X || !Y || lda < n || ldx < l || ldy < l) return RSVD_ERR_INVALID_ARG;
   if (work && ((uintptr_t)work & 15u)) return RSVD_ERR_INVALID_ARG;
@@ -1243,6 +1271,8 @@ rsvd_status rsvd_apply(int64_t m, int64_t n, int l, int trans, int dtype, const 
                             ldx, (double*)Y, ldy);
   } else {
     const bool tc = want_tc(dtype, o, l, A, lda);
+    if (dtype == RSVD_BF16 && !tc) return RSVD_ERR_UNSUPPORTED;
+    c.abf = dtype == RSVD_BF16 ? 1 : 0;
     st = apply_impl<float>(c, o, tc, m, n, l, trans, (const float*)A, lda, (const float*)X, ldx,
                            (float*)Y, ldy);
   }

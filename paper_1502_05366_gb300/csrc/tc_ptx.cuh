@@ -181,6 +181,13 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
+// Byte offset of the 16-byte chunk c (0..3) of row r in a K-major tile of
+// 64-byte rows with the 64-byte swizzle (8-row groups of 512 bytes): the layout
+// TMA writes with CU_TENSOR_MAP_SWIZZLE_64B and sw64_desc describes.
+__device__ __forceinline__ uint32_t sw64_off(uint32_t r, uint32_t c) {
+  return r * 64u + ((c ^ ((r >> 1) & 3u)) << 4);
+}
+
 // Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups of
 // 512 bytes (SBO), version 1 (bit 46), layout code 4 in bits 61-63.
 __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
