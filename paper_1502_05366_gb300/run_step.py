@@ -4,6 +4,7 @@ Used to time or profile a single kernel at the sizes it sees inside the full
 path without holding the full matrix A on the device:
 
   sample     Y = A Omega (Sec. 3.1, Omega generated in the kernel), A m x n
+             (--dtype bfloat16 for A stored as bf16 in sample / apply_n / apply_t)
   apply_n    Y = A X,  X n x l stored                          (power step)
   apply_t    Z = A^T X, X m x l stored                         (power step / QB)
   orth       CholeskyQR of an m x l sample                     (re-orthonormalisation)
@@ -26,11 +27,13 @@ import paper_1502_05366_gb300 as rs
 
 def _inputs(args, dev):
     g = torch.Generator(device="cpu").manual_seed(args.seed)
-    dt = {"float32": torch.float32, "float64": torch.float64}[args.dtype]
+    dt = {"float32": torch.float32, "float64": torch.float64,
+          "bfloat16": torch.bfloat16}[args.dtype]
     if args.step in ("sample", "apply_n", "apply_t"):
         A = torch.randn(args.m, args.n, generator=g, dtype=torch.float32).to(dev, dt)
         rows = args.n if args.step == "apply_n" else args.m
-        X = torch.randn(rows, args.l, generator=g, dtype=torch.float32).to(dev, dt)
+        xdt = torch.float32 if dt == torch.bfloat16 else dt   # bf16 A takes an fp32 X
+        X = torch.randn(rows, args.l, generator=g, dtype=torch.float32).to(dev, xdt)
         return A, X
     if args.step == "orth":
         return torch.randn(args.m, args.l, generator=g, dtype=torch.float64).to(dev, dt), None
@@ -74,7 +77,8 @@ def main(argv=None):
     ap.add_argument("--l", type=int, default=220)
     ap.add_argument("--r", type=int, default=220)
     ap.add_argument("--k", type=int, default=200)
-    ap.add_argument("--dtype", default="float32", choices=["float32", "float64"])
+    ap.add_argument("--dtype", default="float32", choices=["float32", "float64", "bfloat16"],
+                    help="element type of A (bfloat16: the passes over A only)")
     ap.add_argument("--seed", type=int, default=0x5EED)
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
