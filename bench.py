@@ -320,15 +320,13 @@ def rel_err_device(rs, A, U, S, V):
     return (max(e2, 0.0) / a2) ** 0.5
 
 
-def mixed_precision_line(rs, A, plan32, cfg, args, seed, world, dev, ms32, peaks, peak_kind):
-    """The same step with A stored as bf16 (RSVD_BF16): time, A-pass traffic and
-    the relative error of both paths against the FP32 A (equal-error check)."""
+def _time_variant(rs, Ad, opts, cfg, args, seed, world, dev):
+    """(ms per step, per-class trace, plan) of the whole step on A as given."""
     import torch
     m, n, k, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["q"]
-    Ab = A.to(torch.bfloat16)
-    plan = rs.Plan(m, n, k, p, q, torch.bfloat16, dev)
+    plan = rs.Plan(m, n, k, p, q, Ad.dtype, dev, opts)
     for _ in range(args.warmup):
-        plan.run(Ab, seed)
+        plan.run(Ad, seed)
     torch.cuda.synchronize()
     rs.check_info(plan.info, "mixed warmup")
     stream = torch.cuda.current_stream()
@@ -340,35 +338,62 @@ def mixed_precision_line(rs, A, plan32, cfg, args, seed, world, dev, ms32, peaks
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        plan.run(Ab, seed)
+        plan.run(Ad, seed)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     trace = rs.trace_read()
     rs.trace_enable(False)
     rs.check_info(plan.info, "mixed steps")
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    return max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev), trace, plan
+
+
+def mixed_precision_line(rs, A, plan32, cfg, args, seed, world, dev, ms32, peaks, peak_kind):
+    """The same step in the mixed-precision forms, each timed like the main
+    line and judged by its relative error against the FP32 A next to the FP32
+    path's (equal-error comparison):
+      bf16_storage        A held as bf16 (RSVD_BF16), RSVD_PREC_TC arithmetic;
+      bf16_storage_mixed  A as bf16 and single-term bf16 power scheme (RSVD_PREC_MIXED);
+      f32_mixed           fp32 A, single-term bf16 power scheme (RSVD_PREC_MIXED)."""
+    import torch
+    m, n, k, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["q"]
     flops = step_flops(m, n, k, p, q)
-    e16 = rel_err_device(rs, A, plan.U, plan.S, plan.V)
     e32 = rel_err_device(rs, A, plan32.U, plan32.S, plan32.V)
-    pass_ms = sum(v[0] for c, v in trace.items() if c in ("a_omega", "a_w", "at_w")) / args.steps
-    gbs = (2 * q + 2) * a_pass_bytes(m, n, 2) / (pass_ms * 1e-3) / 1e9 if pass_ms else None
+    Ab = A.to(torch.bfloat16)
+    mixed_opts = rs.make_opts(precision=rs.PREC_MIXED)
+    out = {"rel_err_fp32": e32,
+           "rel_err_definition": "||A - U S V^T||_F / ||A||_F against the FP32 A",
+           "fp32_ms_per_step": ms32}
+    for name, Ad, opts, elem, what in (
+            ("bf16_storage", Ab, None, 2,
+             "A in bf16 (RSVD_BF16): sketch, power and QB passes on exact bf16 A, one "
+             "tensor-core product per stored-operand term; the rest as the FP32 path"),
+            ("bf16_storage_mixed", Ab, mixed_opts, 2,
+             "A in bf16 and RSVD_PREC_MIXED: the power scheme's passes take one bf16 term "
+             "of the stored operand (one product per K-step); Bt = A^T Q split"),
+            ("f32_mixed", A, mixed_opts, 4,
+             "fp32 A and RSVD_PREC_MIXED: the power scheme's passes take a0 w0 only")):
+        ms, trace, plan = _time_variant(rs, Ad, opts, cfg, args, seed, world, dev)
+        e = rel_err_device(rs, A, plan.U, plan.S, plan.V)
+        pass_ms = sum(v[0] for c, v in trace.items()
+                      if c in ("a_omega", "a_w", "at_w")) / args.steps
+        gbs = (2 * q + 2) * a_pass_bytes(m, n, elem) / (pass_ms * 1e-3) / 1e9 if pass_ms else None
+        out[name] = {
+            "what": what,
+            "value": world * flops / (ms * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": ms,
+            "speedup_vs_fp32": ms32 / ms, "rel_err": e, "rel_err_ratio_vs_fp32": e / e32,
+            "a_pass_ms_per_step": pass_ms,
+            "a_pass_hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": gbs / peaks["hbm_gbs"] if gbs else None,
+                           "peak_source": peak_kind + " STREAM-style copy",
+                           "work": "m n %d bytes per pass" % elem},
+            "kernels": {c: {"ms_per_step": v[0] / args.steps,
+                            "launches_per_step": v[1] / args.steps}
+                        for c, v in trace.items()},
+        }
+        del plan
     del Ab
-    return {
-        "storage": "A in bf16 (RSVD_BF16); sketch, power and QB passes on exact bf16 A "
-                   "(one tensor-core product per stored-operand term); rest as FP32 path",
-        "value": world * flops / (ms * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": ms,
-        "speedup_vs_fp32": ms32 / ms,
-        "rel_err": e16, "rel_err_fp32": e32, "rel_err_ratio": e16 / e32,
-        "rel_err_definition": "||A - U S V^T||_F / ||A||_F against the FP32 A",
-        "a_pass_ms_per_step": pass_ms,
-        "a_pass_hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                       "frac": gbs / peaks["hbm_gbs"] if gbs else None,
-                       "peak_source": peak_kind + " STREAM-style copy",
-                       "work": "m n 2 bytes per pass"},
-        "kernels": {c: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
-                    for c, v in trace.items()},
-    }
+    return out
 
 
 def main():

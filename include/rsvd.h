@@ -22,7 +22,8 @@
  * RSVD_BF16 (A stored as bf16, the mixed-precision path): accepted by the
  * whole-path calls (rsvd_qb, rsvd_svd, rsvd_id, rsvd_cur, rsvd_svd_id_cur,
  * rsvd_svd_id_cur_host) and by rsvd_sample / rsvd_apply, on the tensor-core
- * path only: A 16-byte aligned with lda % 8 == 0, precision RSVD_PREC_TC,
+ * path only: A 16-byte aligned with lda % 8 == 0, precision RSVD_PREC_TC or
+ * RSVD_PREC_MIXED,
  * l + padding <= 256; otherwise RSVD_ERR_UNSUPPORTED.  The bf16 values of A are
  * exact tensor-core operands: each pass over A issues one product per term of
  * its right-hand operand and reads 2 bytes per entry.  All other arithmetic
@@ -81,7 +82,13 @@ typedef enum { RSVD_F32 = 0, RSVD_F64 = 1, RSVD_BF16 = 2 } rsvd_dtype;
 typedef enum {
   RSVD_PREC_TC = 0,   /* FP32 inputs: tcgen05 tensor-core products of bf16 splits
                          (two-term split of each fp32 operand, fp32 accumulation) */
-  RSVD_PREC_SIMT = 1  /* FP32 inputs: plain fp32 FMA kernels (slower; cross-check) */
+  RSVD_PREC_SIMT = 1, /* FP32 inputs: plain fp32 FMA kernels (slower; cross-check) */
+  RSVD_PREC_MIXED = 2 /* FP32 or BF16 inputs, tensor cores: the passes of the power
+                         scheme (Z = A^T Y, Y = A Z) take one bf16 term of A and of the
+                         stored operand, one product per K-step; the sketch
+                         Y = A Omega, the orthonormalisations and Bt = A^T Q keep the
+                         RSVD_PREC_TC arithmetic (the subspace iteration tolerates
+                         bf16 rounding, the projection onto it does not) */
 } rsvd_precision;
 
 /* Options.  Pass NULL for the defaults set by rsvd_opts_default(). */

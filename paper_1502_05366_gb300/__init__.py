@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librsvd.so")
 
 F32, F64, BF16 = 0, 1, 2
-PREC_TC, PREC_SIMT = 0, 1
+PREC_TC, PREC_SIMT, PREC_MIXED = 0, 1, 2
 
 STATUS = {
     0: "RSVD_OK", 1: "RSVD_ERR_INVALID_ARG", 2: "RSVD_ERR_WORKSPACE", 3: "RSVD_ERR_CUDA",

@@ -7,7 +7,8 @@
 //
 // Arithmetic: every fp32 entry x of A is split as x ~ a0 + a1 with a0 = bf16(x),
 // a1 = bf16(x - a0) (16 significant bits).  W comes in NW bf16 terms:
-//   NW = 1  Omega, bf16-exact by construction:      a0 w0 + a1 w0
+//   NW = 1  one term (the mixed-precision power scheme): a0 w0 only
+//           (Omega, bf16-exact, takes a0 w0 + a1 w0 in k_omega.cu)
 //   NW = 2  stored matrix of generic data (Q, Z, X): a0 w0 + a1 w0 + a0 w1
 //   NW = 3  the l x l factor R^-1 of CholeskyQR:     a0 w0 + a1 w0 + a0 w1 + a0 w2
 //   NW = 4  Gram X^T X (W = split of X itself):      a0 w0 + a1 w0 + a0 w1 + a1 w1
@@ -109,10 +110,8 @@ __global__ void __launch_bounds__(256, 1)
   }
   if (warp == 0 && lane == 0) {
     prefetch_map(&mapA);
-    if (NWT >= 2) {
-      prefetch_map(&mapW0);
-      prefetch_map(&mapW1);
-    }
+    prefetch_map(&mapW0);
+    if (NWT >= 2) prefetch_map(&mapW1);
     if (NWT == 3) prefetch_map(&mapW2);
   }
   if (warp == 1) {
@@ -148,11 +147,10 @@ __global__ void __launch_bounds__(256, 1)
           tma_load_2d_hint(st, &mapA, &full[s], (int)(kc * BK), (int)(tile * BM), pol_a);
         else
           tma_load_2d_hint(st, &mapA, &full[s], (int)(tile * BM), (int)(kc * BK), pol_a);
-        if (NWT >= 2) {
-          tma_load_2d_hint(st + A_STAGE_BYTES, &mapW0, &full[s], (int)(kc * BK), 0, pol_w);
+        tma_load_2d_hint(st + A_STAGE_BYTES, &mapW0, &full[s], (int)(kc * BK), 0, pol_w);
+        if (NWT >= 2)
           tma_load_2d_hint(st + A_STAGE_BYTES + w_tile_bytes(L), &mapW1, &full[s], (int)(kc * BK),
                            0, pol_w);
-        }
         if (NWT == 3)
           tma_load_2d_hint(st + A_STAGE_BYTES + 2 * w_tile_bytes(L), &mapW2, &full[s],
                            (int)(kc * BK), 0, pol_w);
@@ -205,7 +203,7 @@ __global__ void __launch_bounds__(256, 1)
           const uint32_t alo = a_col + 16u + 8u * kk;
           const uint32_t acc0 = (seg_start && kk == 0) ? 0u : 1u;
           mma_ts(tmem, ahi, bhi, idesc, acc0);
-          if (!ABF) mma_ts(tmem, alo, bhi, idesc, 1u);
+          if (!ABF && NW != 1) mma_ts(tmem, alo, bhi, idesc, 1u);
 #pragma unroll
           for (int t = 1; t < NWT; ++t) {
             const uint64_t bt = sw64_desc(wbase + (uint32_t)(t * w_tile_bytes(L)) + 32u * kk);
@@ -592,9 +590,9 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
                    (uint64_t)g.lda, BM, BK, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!ok) return cudaErrorInvalidValue;
   const int nw = g.gram ? 4 : g.wterms;
-  if (nw < 2 || nw > 4 || (g.gram && g.wterms != 2))
+  if (nw < 1 || nw > 4 || (g.gram && g.wterms != 2))
     return cudaErrorInvalidValue;
-  if (abf && nw != 2) return cudaErrorInvalidValue;   // bf16 A: stored-W passes only
+  if (abf && nw > 2) return cudaErrorInvalidValue;   // bf16 A: stored-W passes only
   const int nwt = w_tiles(nw);
   const void* wp[3] = {g.Whi, g.Wlo, g.Wlo2};
   for (int t = 0; t < nwt; ++t) {
@@ -607,7 +605,12 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   const size_t smem = (size_t)stages_for(nw) * stage_bytes(g.L, nw) + 1024 /*align*/ +
                       (4 * MAXST + 2) * 8 + 16;
   cudaError_t e;
-  if (abf && g.form == 0)
+  if (nw == 1)
+    e = g.form == 0 ? (abf ? launch_form<0, 1, true>(ma, mw, P, (int)G, smem, s)
+                           : launch_form<0, 1, false>(ma, mw, P, (int)G, smem, s))
+                    : (abf ? launch_form<1, 1, true>(ma, mw, P, (int)G, smem, s)
+                           : launch_form<1, 1, false>(ma, mw, P, (int)G, smem, s));
+  else if (abf && g.form == 0)
     e = launch_form<0, 2, true>(ma, mw, P, (int)G, smem, s);
   else if (abf)
     e = launch_form<1, 2, true>(ma, mw, P, (int)G, smem, s);

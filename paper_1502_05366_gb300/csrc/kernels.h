@@ -188,7 +188,7 @@ struct TcGemm {
   int a_bf16;           // A holds bf16: one product per W term (a0 exact), half the bytes
   int64_t a_rows_total; // rows of the A tensor (form 0: rows, form 1: K)
   int64_t a_cols_total; // cols of the A tensor (form 0: K, form 1: rows)
-  int wterms;           // stored W: 2 (hi, lo) or 3 (hi, mid, lo) bf16 terms
+  int wterms;           // stored W: 1 (hi: one product a0 w0), 2 (hi, lo) or 3 (hi, mid, lo)
   int gram;             // form 1 with W = split of A itself: adds the lo*lo product
   const void* Whi;      // L x K bf16 (K contiguous): leading term of W^T (stored W only)
   const void* Wlo;      // second term

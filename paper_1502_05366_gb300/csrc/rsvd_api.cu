@@ -26,7 +26,9 @@ static bool read_opts(const rsvd_opts* o, Opts* out) {
   Opts d;
   if (o) {
     if (o->s < 1 || o->max_sweeps < 1 || o->max_sweeps > 1000) return false;
-    if (o->precision != RSVD_PREC_TC && o->precision != RSVD_PREC_SIMT) return false;
+    if (o->precision != RSVD_PREC_TC && o->precision != RSVD_PREC_SIMT &&
+        o->precision != RSVD_PREC_MIXED)
+      return false;
     for (int i = 0; i < 13; ++i)
       if (o->reserved[i] != 0) return false;
     d.s = o->s;
@@ -129,7 +131,7 @@ struct Engine {
       g.Whi = w ? w->hi : nullptr;
       g.Wlo = w ? w->lo : nullptr;
       g.Wlo2 = w ? w->lo2 : nullptr;
-      g.wterms = (w && w->lo2) ? 3 : 2;
+      g.wterms = (w && !w->lo) ? 1 : ((w && w->lo2) ? 3 : 2);
       g.ldw = w ? w->ld : 0;
       g.part = part;
       g.out = (float*)out;
@@ -168,7 +170,7 @@ struct Engine {
       g.Whi = w->hi;
       g.Wlo = w->lo;
       g.Wlo2 = nullptr;
-      g.wterms = 2;
+      g.wterms = w->lo ? 2 : 1;
       g.gram = gram ? 1 : 0;
       g.ldw = w->ld;
       g.part = part;
@@ -367,6 +369,12 @@ struct Engine {
                   b.part, nullptr, c.abf != 0);
       if (st != RSVD_OK) return st;
     }
+    // RSVD_PREC_MIXED: the passes of the power scheme take one bf16 term of the
+    // stored operand (one product per K-step); the sketch, the orthonormalisations
+    // and Bt = A^T Q keep the split arithmetic
+    const bool mixed = tc && o.precision == RSVD_PREC_MIXED;
+    Split ys1 = b.ys, zs1 = b.zs;
+    if (mixed) ys1.lo = zs1.lo = nullptr;
     int prod = 0;  // index of the next product with A or A^T (Alg. 5 orth test)
     for (int j = 1; j <= q; ++j) {
       if (prod % o.s == 0) {
@@ -376,8 +384,8 @@ struct Engine {
       }
       ++prod;
       // Z = A^* Y (Sec. 3.2)
-      st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr,
-                  false, c.abf != 0);
+      st = gemm_t(n, m, L, A, lda, mixed ? &ys1 : &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs,
+                  nullptr, false, c.abf != 0);
       if (st != RSVD_OK) return st;
       if (prod % o.s == 0) {
         st = orth(n, l, L, b.Z, b.Ztmp, &b.zs, b.ob, b.part, b.slabs, false, false);
@@ -386,8 +394,8 @@ struct Engine {
       }
       ++prod;
       // Y = A Z
-      st = gemm_n(m, n, L, A, lda, m, n, false, 0, L, &b.zs, b.Z, L, b.Y, L, L, &b.ys, b.part,
-                  nullptr, c.abf != 0);
+      st = gemm_n(m, n, L, A, lda, m, n, false, 0, L, mixed ? &zs1 : &b.zs, b.Z, L, b.Y, L, L,
+                  &b.ys, b.part, nullptr, c.abf != 0);
       if (st != RSVD_OK) return st;
     }
     // Q = orth(Y)
@@ -671,7 +679,8 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // Tensor-core path usable: FP32 or BF16 A, requested, width fits, A
 // TMA-addressable (16-byte aligned base and rows).
 static bool want_tc(int dtype, const Opts& o, int l, const void* A, int64_t lda) {
-  if ((dtype != RSVD_F32 && dtype != RSVD_BF16) || o.precision != RSVD_PREC_TC) return false;
+  if (dtype != RSVD_F32 && dtype != RSVD_BF16) return false;
+  if (o.precision != RSVD_PREC_TC && o.precision != RSVD_PREC_MIXED) return false;
   if (!tc_supported(padL(l))) return false;
   if (A && !aligned16(A)) return false;
   if (lda % (dtype == RSVD_BF16 ? 8 : 4) != 0) return false;

@@ -165,3 +165,44 @@ def test_bf16_unsupported_forms():
     with pytest.raises(rs.RsvdError) as e:
         rs.svd(Ab2, 5, 5, 1, 1)
     assert e.value.code in (1, 4)
+
+
+# ---------------------------------------------------------------------------
+# RSVD_PREC_MIXED: single-term bf16 products in the power scheme
+# ---------------------------------------------------------------------------
+MIXED_CASES = [
+    # name, m, n, k, p, q, spectrum, noise, storage
+    ("c2_like_mixed_f32", 3000, 2000, 40, 10, 2, "inv", 1e-4, "float32"),
+    ("c2_like_mixed_bf16", 3000, 2000, 40, 10, 2, "inv", 1e-4, "bfloat16"),
+    ("c5_like_mixed_f32", 2048, 1024, 64, 16, 2, "sqrtgap64", 0.0, "float32"),
+]
+
+
+@pytest.mark.parametrize("case", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_mixed_precision_power_scheme(case):
+    """The power scheme in single-term bf16 products perturbs the basis by
+    ~2^-9 per iteration; the Ritz values of the final (split-precision)
+    projection then move by about its square (quadratic in the subspace
+    angle).  Bars: sigma relative 1e-4 against the oracle, reconstruction
+    error within 1 % of the oracle's, and of the TC path's."""
+    name, m, n, k, p, q, spec, noise, storage = case
+    r = min(m, n) if spec != "inv" else min(2000, n)
+    A32 = make_matrix_np(m, n, spectrum(spec, r), noise=noise, seed=0xC000 + m, dtype="float32")
+    if storage == "bfloat16":
+        Ad, A64 = _bf16(A32)
+    else:
+        Ad, A64 = torch.from_numpy(A32).to(DEV), A32.astype(np.float64)
+    seed = 0x5EED + k
+    mixed = rs.make_opts(precision=rs.PREC_MIXED)
+    U, S, V = (t.double().cpu().numpy() for t in rs.svd(Ad, k, p, q, seed, mixed))
+    Ut, St, Vt = (t.double().cpu().numpy() for t in rs.svd(Ad, k, p, q, seed))
+    Uo, So, Vo, _ = orc.rsvd(A64, k, p, q, seed, rounding="bf16")
+    rel = np.abs(S - So) / So
+    print(name, "mixed sigma max rel %.2e, TC %.2e" % (rel.max(), (np.abs(St - So) / So).max()))
+    assert rel.max() <= 1e-4, (name, rel.max())
+    e_m = orc.rel_err_svd(A64, U, S, V)
+    e_o = orc.rel_err_svd(A64, Uo, So, Vo)
+    e_t = orc.rel_err_svd(A64, Ut, St, Vt)
+    assert abs(e_m - e_o) <= 0.01 * e_o + 1e-12, (e_m, e_o)
+    assert abs(e_m - e_t) <= 0.01 * e_t + 1e-12, (e_m, e_t)
+    assert np.linalg.norm(U.T @ U - np.eye(k)) <= 5e-5
