@@ -546,6 +546,8 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   if (!tc_supported(g.L)) return cudaErrorInvalidValue;
   if (g.form == 1 && g.omega) return cudaErrorInvalidValue;
   if (g.form == 0 && g.omega) return launch_tc_omega(g, s);
+  // the passes over A with a stored operand: two M-tiles per CTA (k_tc2.cu)
+  if (tc_unit_supported(g)) return launch_tc_unit(g, s);
   int64_t tiles, kiters, total, G;
   int maxseg;
   sk_plan(g.rows, g.K, BM, BK, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);

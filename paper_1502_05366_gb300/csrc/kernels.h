@@ -209,6 +209,10 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s);
 // Y = A Omega with two M-tiles per CTA sharing each generated Omega stage
 // (k_omega.cu); called by launch_tc_gemm for form 0 with omega set.
 cudaError_t launch_tc_omega(const TcGemm& g, cudaStream_t s);
+// Stored-operand GEMMs (wterms 1 or 2, no Gram) on 256-row units, two M-tiles
+// per CTA sharing each W stage (k_tc2.cu); called by launch_tc_gemm.
+bool tc_unit_supported(const TcGemm& g);
+cudaError_t launch_tc_unit(const TcGemm& g, cudaStream_t s);
 bool tc_supported(int L);
 int device_sm_count();
 
