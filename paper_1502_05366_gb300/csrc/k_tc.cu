@@ -404,12 +404,29 @@ __global__ void tc_reduce_kernel(TcParams P, int G) {
   __syncthreads();
   const int rg = blockIdx.x % (P.bm / 32), jg = blockIdx.x / (P.bm / 32);
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-  for (int jj = ty; jj < 32; jj += 8) {
-    const int j = jg * 32 + jj;
-    float sum = 0.f;
-    if (j < L)
-      for (int i = 0; i < nctr; ++i) sum += P.part[s_base[i] + (int64_t)j * P.bm + rg * 32 + tx];
-    tile_s[jj][tx] = sum;
+  // contributors are added in increasing order; each thread's four rows and 8
+  // contributors are loaded together so that a load's latency is not paid per
+  // contributor
+  {
+    float sum[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i0 = 0; i0 < nctr; i0 += 8) {
+      float v[4][8];
+#pragma unroll
+      for (int a4 = 0; a4 < 4; ++a4) {
+        const int j = jg * 32 + ty + 8 * a4;
+        const int64_t off = (int64_t)j * P.bm + rg * 32 + tx;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          v[a4][u] = (j < L && i0 + u < nctr) ? P.part[s_base[min(i0 + u, nctr - 1)] + off] : 0.f;
+      }
+#pragma unroll
+      for (int a4 = 0; a4 < 4; ++a4)
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u < nctr) sum[a4] += v[a4][u];
+    }
+#pragma unroll
+    for (int a4 = 0; a4 < 4; ++a4) tile_s[ty + 8 * a4][tx] = sum[a4];
   }
   __syncthreads();
   for (int rr = ty; rr < 32; rr += 8) {
