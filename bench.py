@@ -143,7 +143,7 @@ def sketch_roofline(trace, cfg, peaks, peak_kind):
         return None
     achieved = nl * a_pass_bytes(m, n) / (ms * 1e-3) / 1e9
     t = load_traffic()
-    return {"kernels": "tc_omega2_kernel (A Omega), tc_gemm_kernel (A W, A^T W)",
+    return {"kernels": "tc_omega2_kernel (A Omega), tc_unit_kernel (A W, A^T W)",
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "passes_timed": nl,
             "per_class_ms": {c: trace[c][0] / trace[c][1] for c in cls},
