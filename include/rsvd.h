@@ -333,6 +333,41 @@ int rsvd_trace_read(double* ms, int64_t* launches, int nclass);
 /* Number of kernels the library has launched since it was loaded. */
 int64_t rsvd_kernel_launch_count(void);
 
+/* ------------------------------------------------------------------------
+ * Batched RSVD of many small FP32 matrices of different sizes (Alg. 5 for each
+ * problem: the power scheme with orthonormalisation before every product,
+ * s = 1, then the SVD of B through the QR of Bt).  Every step is one launch
+ * over the whole batch, so a batch of hundreds of problems costs a few dozen
+ * launches instead of a few dozen per problem.
+ *
+ * items (HOST array of `batch` entries) gives, per problem i:
+ *   m, n     A_i is m x n, row-major with leading dimension n, at A + a_off;
+ *   k        rank; l = k + p must satisfy l <= min(m, n) and l <= 128;
+ *   u_off    U_i (m x k, row-major, leading dimension k) at U + u_off;
+ *   v_off    V_i (n x k, leading dimension k) at V + v_off;
+ *   s_off    S_i (k doubles, descending) at S + s_off.
+ * A, U, V, S are device buffers holding all problems at the given element
+ * offsets; outputs must not overlap.  Omega of problem i is the Philox stream
+ * of `seed` with the problem index as the counter's batch word (counter (row,
+ * column / 4, 0, i)), rounded to bf16 as on the FP32 path.  Products are fp32
+ * (SIMT), the l x l factorisations fp32 with the CholeskyQR shift fallback.
+ * Sign rule and ordering as rsvd_svd.  The work buffer (256-byte aligned)
+ * holds per-problem scratch and the task tables, which are copied from the
+ * host with cudaMemcpyAsync on `stream` (no host synchronisation).
+ * Errors: RSVD_ERR_INVALID_ARG (a bad item, size or pointer),
+ * RSVD_ERR_WORKSPACE, RSVD_ERR_CUDA; device failures in *d_info.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t m, n;
+  int k;
+  int64_t a_off, u_off, v_off, s_off;
+} rsvd_batch_item;
+
+size_t rsvd_svd_batched_workspace_size(int batch, const rsvd_batch_item* items, int p, int q);
+rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int q,
+                             uint64_t seed, const float* A, float* U, double* S, float* V,
+                             void* work, size_t work_bytes, int* d_info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,13 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 13)]
 
 
+class BatchItem(ctypes.Structure):
+    """rsvd_batch_item: one problem of rsvd_svd_batched (sizes, rank, element offsets)."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int),
+                ("a_off", ctypes.c_int64), ("u_off", ctypes.c_int64), ("v_off", ctypes.c_int64),
+                ("s_off", ctypes.c_int64)]
+
+
 _lib = None
 _c_i64 = ctypes.c_int64
 _c_int = ctypes.c_int
@@ -96,6 +103,10 @@ _SIGS = {
                                       _c_i64, _vp, _vp, _vp, _c_i64, _vp, _c_size, _vp, _vp,
                                       _OPTP]),
     "rsvd_cpqr_f32_workspace_size": (_c_size, [_c_int, _c_i64, _c_int]),
+    "rsvd_svd_batched_workspace_size": (_c_size, [_c_int, ctypes.POINTER(BatchItem), _c_int,
+                                                  _c_int]),
+    "rsvd_svd_batched": (_c_int, [_c_int, ctypes.POINTER(BatchItem), _c_int, _c_int, _c_u64, _vp,
+                                  _vp, _vp, _vp, _vp, _c_size, _vp, _vp]),
     "rsvd_cpqr_id_f32": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
                                   _vp, _c_size, _vp, _vp]),
 }
@@ -486,3 +497,81 @@ def cpqr_id(M, k, check=True):
     if check:
         check_info(info, name)
     return J, T[:, : n - k], gaps
+
+
+# ---------------------------------------------------------------------------
+# batched problems
+# ---------------------------------------------------------------------------
+class BatchPlan:
+    """Packed outputs and workspace for rsvd_svd_batched over fixed problem sizes.
+
+    Problem i is A_i (ms[i] x ns[i], row-major) at element a_off[i] of one packed
+    float32 buffer; U_i (m x k), V_i (n x k) and S_i (k, float64) live in packed
+    outputs at their offsets."""
+
+    def __init__(self, ms, ns, ks, p, q, device):
+        torch = _torch()
+        self.batch = len(ms)
+        self.ms, self.ns, self.ks = [int(x) for x in ms], [int(x) for x in ns], [int(x) for x in ks]
+        self.p, self.q = int(p), int(q)
+        dev = torch.device(device)
+        items = (BatchItem * self.batch)()
+        a = u = v = sk = 0
+        self.a_off, self.u_off, self.v_off, self.s_off = [], [], [], []
+        for i, (m, n, k) in enumerate(zip(self.ms, self.ns, self.ks)):
+            items[i].m, items[i].n, items[i].k = m, n, k
+            items[i].a_off, items[i].u_off, items[i].v_off, items[i].s_off = a, u, v, sk
+            self.a_off.append(a)
+            self.u_off.append(u)
+            self.v_off.append(v)
+            self.s_off.append(sk)
+            a += m * n
+            u += m * k
+            v += n * k
+            sk += k
+        self.items = items
+        self.a_elems = a
+        self.U = torch.empty(max(u, 1), dtype=torch.float32, device=dev)
+        self.V = torch.empty(max(v, 1), dtype=torch.float32, device=dev)
+        self.S = torch.empty(max(sk, 1), dtype=torch.float64, device=dev)
+        ws = lib().rsvd_svd_batched_workspace_size(self.batch, items, self.p, self.q)
+        if ws == 0:
+            raise RsvdError(1, "rsvd_svd_batched_workspace_size")
+        self.work = _work(ws, dev)
+        self.info = _info(dev)
+
+    def pack(self, mats):
+        """One packed float32 buffer holding the matrices at their offsets."""
+        torch = _torch()
+        return torch.cat([m.reshape(-1).to(torch.float32) for m in mats])
+
+    def run(self, A_packed, seed):
+        torch = _torch()
+        if (not A_packed.is_cuda or A_packed.dtype != torch.float32 or A_packed.dim() != 1 or
+                A_packed.numel() < self.a_elems):
+            raise ValueError("A_packed: a 1-D float32 CUDA tensor of the packed matrices")
+        st = lib().rsvd_svd_batched(self.batch, self.items, self.p, self.q, seed, _ptr(A_packed),
+                                    _ptr(self.U), _ptr(self.S), _ptr(self.V), _ptr(self.work),
+                                    self.work.numel(), _ptr(self.info), _stream())
+        _raise(st, "rsvd_svd_batched")
+
+    def result(self, i):
+        m, n, k = self.ms[i], self.ns[i], self.ks[i]
+        U = self.U[self.u_off[i]:self.u_off[i] + m * k].view(m, k)
+        V = self.V[self.v_off[i]:self.v_off[i] + n * k].view(n, k)
+        S = self.S[self.s_off[i]:self.s_off[i] + k]
+        return U, S, V
+
+
+def svd_batched(mats, ks, p, q, seed, check=True):
+    """[(U_i, S_i, V_i)]: the RSVD of every float32 CUDA matrix in `mats`
+    (ranks ks, common p and q) in one batched call (rsvd_svd_batched)."""
+    for t in mats:
+        _check_matrix(t, "A_i")
+    plan = BatchPlan([t.shape[0] for t in mats], [t.shape[1] for t in mats], ks, p, q,
+                     mats[0].device)
+    Ap = plan.pack(mats)
+    plan.run(Ap, seed)
+    if check:
+        check_info(plan.info, "rsvd_svd_batched")
+    return [plan.result(i) for i in range(plan.batch)]

@@ -1001,6 +1001,68 @@ __global__ void trmm_upper_kernel(int L, const T* __restrict__ R, const T* __res
   }
 }
 
+// One CTA per problem of a batch: the factor and inverse of chol_kernel
+// (shifted retries included) on the problem's l x l Gram, without the pass
+// bookkeeping of CholeskyQR2/3 (the batched path always runs two passes).
+__global__ void __launch_bounds__(CT) chol_batched_kernel(const BChol* __restrict__ tasks,
+                                                          int* d_info) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ float red[32];
+  __shared__ float s_maxdiag, s_dev;
+  __shared__ int s_fail;
+  const BChol tk = tasks[blockIdx.x];
+  CholArgs a{};
+  a.l = tk.l;
+  a.L = tk.l;
+  a.G = tk.G;
+  a.ldg = tk.l;
+  a.R = tk.R;
+  a.Rinv = tk.Rinv;
+  a.pass = 1;
+  a.skip_idx = -1;
+  a.d_info = d_info;
+  chol_body<float>(a, reinterpret_cast<float*>(dsm), tk.l, red, s_maxdiag, s_dev, s_fail);
+}
+
+cudaError_t launch_chol_batched(const BChol* tasks, int batch, int lmax, int* d_info,
+                                cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  if (lmax > BATCH_LMAX) return cudaErrorInvalidValue;
+  const size_t dyn = (size_t)lmax * lmax * sizeof(float);
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(chol_batched_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  const int tr_ = trace_begin(RSVD_TRACE_CHOL, s);
+  chol_batched_kernel<<<batch, dim3(32, CT / 32), dyn, s>>>(tasks, d_info);
+  count_launch();
+  trace_end(tr_, s);
+  return cudaGetLastError();
+}
+
+// Racc <- R Racc per problem (upper triangular), one CTA each.
+__global__ void trmm_batched_kernel(const BTrmm* __restrict__ tasks) {
+  const BTrmm tk = tasks[blockIdx.x];
+  const int l = tk.l;
+  for (int t = threadIdx.x; t < l * l; t += blockDim.x) {
+    const int i = t / l, c = t - (t / l) * l;
+    float acc = 0.f;
+    if (c >= i)
+      for (int q = i; q <= c; ++q) acc = fmaf(tk.R[i * l + q], tk.Racc[q * l + c], acc);
+    tk.tmp[t] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < l * l; t += blockDim.x) tk.Racc[t] = tk.tmp[t];
+}
+
+cudaError_t launch_trmm_batched(const BTrmm* tasks, int batch, cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  trmm_batched_kernel<<<batch, 256, 0, s>>>(tasks);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_chol(const CholArgs& a, cudaStream_t s) {
   const size_t bytes = (size_t)a.l * a.l * sizeof(T);

@@ -82,17 +82,13 @@ __host__ __device__ constexpr int jthreads() { return sizeof(T) == 8 ? 512 : 102
 // each lane strides over the rows with step 8.  The dot products are plain;
 // when a pair's cosine is within a factor 64 of the threshold, gamma is
 // recomputed with Dot2 so convergence is judged on accurate values.
-template <typename T>
-__global__ void __launch_bounds__(jthreads<T>()) jacobi_kernel(int l, const T* __restrict__ M,
-                                                              int64_t ldm, T* __restrict__ Uh,
-                                                              int64_t lduh,
-                                                              double* __restrict__ Sh, T* scratch,
-                                                              int max_sweeps, int* d_info) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ double s_sig[1024];
-  __shared__ int s_rot;
-  T* X = scratch ? scratch : (T*)dsm;  // column-major: X[j*l + i]
-  constexpr int NT = jthreads<T>();
+// The sweeps and the sorted output of one matrix by one CTA of NT threads; X
+// (l*l, column-major: X[j*l + i]) and s_sig (l doubles) are the CTA's working
+// storage.
+template <typename T, int NT>
+__device__ void jacobi_body(int l, const T* __restrict__ M, int64_t ldm, T* __restrict__ Uh,
+                            int64_t lduh, double* __restrict__ Sh, T* X, double* s_sig,
+                            int& s_rot, int max_sweeps, int* d_info) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = NT / 32;
   const int g = tid >> 3, gl = tid & 7, ngroups = NT / 8;
   const unsigned gmask = 0xffu << (lane & ~7);
@@ -193,6 +189,19 @@ __global__ void __launch_bounds__(jthreads<T>()) jacobi_kernel(int l, const T* _
     for (int i = lane; i < l; i += 32) Uh[(int64_t)i * lduh + rank] = xj[i] * inv;
     if (lane == 0) Sh[rank] = sj;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(jthreads<T>()) jacobi_kernel(int l, const T* __restrict__ M,
+                                                              int64_t ldm, T* __restrict__ Uh,
+                                                              int64_t lduh,
+                                                              double* __restrict__ Sh, T* scratch,
+                                                              int max_sweeps, int* d_info) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ double s_sig[1024];
+  __shared__ int s_rot;
+  T* X = scratch ? scratch : (T*)dsm;
+  jacobi_body<T, jthreads<T>()>(l, M, ldm, Uh, lduh, Sh, X, s_sig, s_rot, max_sweeps, d_info);
 }
 
 // ---------------------------------------------------------------------------
@@ -483,6 +492,82 @@ template cudaError_t launch_svd_finalize<float>(int, const float*, int64_t, cons
 template cudaError_t launch_svd_finalize<double>(int, const double*, int64_t, const double*,
                                                  int64_t, double*, int64_t, double*, double*,
                                                  int64_t, int*, cudaStream_t);
+
+// One CTA per problem: Jacobi sweeps on M (l x l <= 128, row-major ld l),
+// P = M^T Uj, sigma_j = ||P(:, j)||, Vh(:, rank) = P(:, j) / sigma_j,
+// Uh(:, rank) = Uj(:, j) (the steps of jacobi_kernel and svd_finalize_kernel).
+constexpr int SB_T = 256;
+__global__ void __launch_bounds__(SB_T) small_svd_batched_kernel(const BSvd* __restrict__ tasks,
+                                                                  int max_sweeps, int* d_info) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ double s_sig[BATCH_LMAX];
+  __shared__ int s_rot;
+  const BSvd tk = tasks[blockIdx.x];
+  const int l = tk.l;
+  float* X = reinterpret_cast<float*>(dsm);          // l*l
+  float* Ms = X + l * l;                              // l*l
+  float* Pm = Ms + l * l;                             // l*l
+  jacobi_body<float, SB_T>(l, tk.M, l, tk.Uj, l, tk.Sh, X, s_sig, s_rot, max_sweeps, d_info);
+  __syncthreads();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = SB_T / 32;
+  for (int t = tid; t < l * l; t += SB_T) {
+    Ms[t] = tk.M[t];
+    X[t] = tk.Uj[t];
+  }
+  __syncthreads();
+  for (int t = tid; t < l * l; t += SB_T) {   // P[i][j] = sum_r M[r][i] Uj[r][j]
+    const int i = t / l, j = t - (t / l) * l;
+    float acc = 0.f;
+    for (int r = 0; r < l; ++r) acc = fmaf(Ms[r * l + i], X[r * l + j], acc);
+    Pm[t] = acc;
+  }
+  __syncthreads();
+  for (int j = warp; j < l; j += nwarp) {
+    double sq = 0.0;
+    for (int i = lane; i < l; i += 32) {
+      const double v = (double)Pm[i * l + j];
+      sq = fma(v, v, sq);
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) {
+      s_sig[j] = sqrt(sq);
+      if (!isfinite(sq)) set_info(d_info, RSVD_ERR_NUMERIC);
+    }
+  }
+  __syncthreads();
+  for (int j = warp; j < l; j += nwarp) {
+    const double sj = s_sig[j];
+    int rank = 0;
+    for (int i = lane; i < l; i += 32) {
+      const double si = s_sig[i];
+      rank += (si > sj || (si == sj && i < j)) ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+    for (int i = lane; i < l; i += 32) {
+      tk.Vh[i * l + rank] = (float)((double)Pm[i * l + j] * inv);
+      tk.Uh[i * l + rank] = X[i * l + j];
+    }
+    if (lane == 0) tk.Sh[rank] = sj;
+  }
+}
+
+cudaError_t launch_small_svd_batched(const BSvd* tasks, int batch, int lmax, int max_sweeps,
+                                     int* d_info, cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  if (lmax > BATCH_LMAX) return cudaErrorInvalidValue;
+  const size_t dyn = (size_t)3 * lmax * lmax * sizeof(float);
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(small_svd_batched_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  const int tr_ = trace_begin(RSVD_TRACE_JACOBI, s);
+  small_svd_batched_kernel<<<batch, SB_T, dyn, s>>>(tasks, max_sweeps, d_info);
+  count_launch();
+  trace_end(tr_, s);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_jacobi(int l, const T* M, int64_t ldm, T* Uh, int64_t lduh, double* Sh,

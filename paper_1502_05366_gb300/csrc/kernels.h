@@ -216,4 +216,68 @@ cudaError_t launch_tc_unit(const TcGemm& g, cudaStream_t s);
 bool tc_supported(int L);
 int device_sm_count();
 
+// ----- batched problems (k_batched.cu, k_chol.cu, k_jacobi.cu) -------------
+// One GEMM of a batch: C (M x N, ld ldc) = op(A) W with op(A) = A (M x K, ld
+// lda) or, with transA, A^T for A stored K x M (ld lda); W is K x N (ld ldw)
+// or, when null, the Omega of problem `batch` (bf16-rounded Gaussians, Philox
+// counter (row, column / 4, 0, batch)).  Only the first ncol columns are
+// written.
+struct BGemm {
+  const float* A;
+  int64_t lda;
+  const float* W;
+  int64_t ldw;
+  float* C;
+  int64_t ldc;
+  int M, N, K, ncol;
+  int transA;
+  int batch;
+};
+// tasks: (gemm index, first output row), one CTA each
+cudaError_t launch_bgemm(const BGemm* gemms, const int2* tasks, int ntasks, uint64_t seed,
+                         cudaStream_t s);
+constexpr int BGEMM_TM = 64;        // output rows per task
+constexpr int BATCH_LMAX = 128;     // largest sketch width of the batched path
+// Cholesky R^T R = G and R^-1 of one l x l Gram per CTA (the shifted CholeskyQR
+// factorisation of chol_kernel); R, Rinv l x l (ld l)
+struct BChol {
+  const float* G;
+  float* R;
+  float* Rinv;
+  int l;
+};
+cudaError_t launch_chol_batched(const BChol* tasks, int batch, int lmax, int* d_info,
+                                cudaStream_t s);
+// Racc <- R Racc (upper triangular l x l) per problem, through tmp
+struct BTrmm {
+  const float* R;
+  float* Racc;
+  float* tmp;
+  int l;
+};
+cudaError_t launch_trmm_batched(const BTrmm* tasks, int batch, cudaStream_t s);
+// SVD of one l x l core M per CTA: M = Uh diag(Sh) Vh^T (Jacobi for the left
+// vectors, sigma_j = ||M^T u_j||, sorted descending); Uj is working storage
+struct BSvd {
+  const float* M;
+  float* Uj;
+  float* Uh;
+  float* Vh;
+  double* Sh;
+  int l;
+};
+cudaError_t launch_small_svd_batched(const BSvd* tasks, int batch, int lmax, int max_sweeps,
+                                     int* d_info, cudaStream_t s);
+// Sign rule per problem (largest |entry| of each v_j positive, lowest index on
+// ties) applied to U (m x k) and V (n x k), and S[0:k] = Sh[0:k]
+struct BSign {
+  float* U;
+  float* V;
+  double* S;
+  const double* Sh;
+  int64_t m, n;
+  int k;
+};
+cudaError_t launch_sign_batched(const BSign* tasks, int batch, cudaStream_t s);
+
 }  // namespace rsvd

@@ -1,0 +1,314 @@
+// rsvd_svd_batched: the RSVD of Alg. 5 (QB through the power scheme with
+// orthonormalisation before every product, s = 1; B's SVD through the QR of
+// Bt) for a batch of small FP32 problems of different sizes.  Each step is one
+// launch over the whole batch: grouped GEMM tasks (k_batched.cu), one CTA per
+// problem for the l x l factorisations (k_chol.cu, k_jacobi.cu).  The task
+// tables are built on the host from the problem sizes and copied into the
+// workspace once per call.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "rsvd.h"
+
+namespace rsvd {
+
+namespace {
+
+struct Carve {   // workspace carving; dry when base is null
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T) + 16;
+    return p;
+  }
+};
+
+struct ProbBufs {
+  float *Y, *Yt, *Z, *Zt, *G, *R, *Rinv, *Racc, *tmp, *Uj, *Uh, *Vh;
+  double* Sh;
+};
+
+enum StageKind { ST_GEMM, ST_CHOL, ST_TRMM, ST_SVD, ST_SIGN };
+struct Stage {
+  int kind;
+  int first, count;   // into the table of the kind (gemm: tasks; others: problems)
+};
+
+struct Plan {
+  std::vector<BGemm> gemms;
+  std::vector<int2> tasks;
+  std::vector<BChol> chols;
+  std::vector<BTrmm> trmms;
+  std::vector<BSvd> svds;
+  std::vector<BSign> signs;
+  std::vector<Stage> stages;
+  int lmax = 0;
+};
+
+bool items_ok(int batch, const rsvd_batch_item* it, int p, int q) {
+  if (batch < 1 || !it || p < 0 || q < 0 || q > 64) return false;
+  for (int i = 0; i < batch; ++i) {
+    const int64_t l = (int64_t)it[i].k + p;
+    if (it[i].k < 1 || it[i].m < 1 || it[i].n < 1) return false;
+    if (l > it[i].m || l > it[i].n || l > BATCH_LMAX) return false;
+    if (it[i].m > 0x7fffffffLL || it[i].n > 0x7fffffffLL) return false;
+    if (it[i].a_off < 0 || it[i].u_off < 0 || it[i].v_off < 0 || it[i].s_off < 0) return false;
+  }
+  return true;
+}
+
+// One GEMM per problem, tasks over 64-row blocks of the output.
+void add_gemm_stage(Plan& P, const std::vector<BGemm>& gs) {
+  Stage st{ST_GEMM, (int)P.tasks.size(), 0};
+  for (const BGemm& g : gs) {
+    const int gi = (int)P.gemms.size();
+    P.gemms.push_back(g);
+    for (int r0 = 0; r0 < g.M; r0 += BGEMM_TM) P.tasks.push_back(make_int2(gi, r0));
+  }
+  st.count = (int)P.tasks.size() - st.first;
+  P.stages.push_back(st);
+}
+
+BGemm gemm_of(const float* A, int64_t lda, int transA, const float* W, int64_t ldw, float* C,
+              int64_t ldc, int64_t M, int N, int64_t K, int ncol, int batch) {
+  BGemm g;
+  g.A = A;
+  g.lda = lda;
+  g.W = W;
+  g.ldw = ldw;
+  g.C = C;
+  g.ldc = ldc;
+  g.M = (int)M;
+  g.N = N;
+  g.K = (int)K;
+  g.ncol = ncol;
+  g.transA = transA;
+  g.batch = batch;
+  return g;
+}
+
+// CholeskyQR2 of X (rows x l per problem, ld l) in place, through Xt; with
+// want_R the triangular factor R = R2 R1 ends in Racc.
+void add_orth(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<ProbBufs>& b,
+              bool on_z, bool want_R) {
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<BGemm> gram, apply;
+    Stage sc{ST_CHOL, (int)P.chols.size(), batch};
+    for (int i = 0; i < batch; ++i) {
+      const int l = it[i].k + p;
+      const int64_t rows = on_z ? it[i].n : it[i].m;
+      float* X = on_z ? b[i].Z : b[i].Y;
+      float* Xt = on_z ? b[i].Zt : b[i].Yt;
+      const float* src = pass == 0 ? X : Xt;
+      float* dst = pass == 0 ? Xt : X;
+      gram.push_back(gemm_of(src, l, 1, src, l, b[i].G, l, l, l, rows, l, i));
+      BChol c;
+      c.G = b[i].G;
+      c.R = (want_R && pass == 0) ? b[i].Racc : b[i].R;
+      c.Rinv = b[i].Rinv;
+      c.l = l;
+      P.chols.push_back(c);
+      apply.push_back(gemm_of(src, l, 0, b[i].Rinv, l, dst, l, rows, l, l, l, i));
+    }
+    add_gemm_stage(P, gram);
+    P.stages.push_back(sc);
+    add_gemm_stage(P, apply);
+  }
+  if (want_R) {
+    Stage st{ST_TRMM, (int)P.trmms.size(), batch};
+    for (int i = 0; i < batch; ++i) {
+      BTrmm t;
+      t.R = b[i].R;
+      t.Racc = b[i].Racc;
+      t.tmp = b[i].tmp;
+      t.l = it[i].k + p;
+      P.trmms.push_back(t);
+    }
+    P.stages.push_back(st);
+  }
+}
+
+// Carves the per-problem buffers and the plan; returns the workspace bytes.
+size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A, float* U,
+             double* S, float* V, char* base, Plan& P, char** tables) {
+  Carve cv;
+  cv.base = base;
+  std::vector<ProbBufs> b(batch);
+  for (int i = 0; i < batch; ++i) {
+    const int64_t m = it[i].m, n = it[i].n;
+    const int l = it[i].k + p;
+    P.lmax = std::max(P.lmax, l);
+    b[i].Y = cv.take<float>((size_t)m * l);
+    b[i].Yt = cv.take<float>((size_t)m * l);
+    b[i].Z = cv.take<float>((size_t)n * l);
+    b[i].Zt = cv.take<float>((size_t)n * l);
+    b[i].G = cv.take<float>((size_t)l * l);
+    b[i].R = cv.take<float>((size_t)l * l);
+    b[i].Rinv = cv.take<float>((size_t)l * l);
+    b[i].Racc = cv.take<float>((size_t)l * l);
+    b[i].tmp = cv.take<float>((size_t)l * l);
+    b[i].Uj = cv.take<float>((size_t)l * l);
+    b[i].Uh = cv.take<float>((size_t)l * l);
+    b[i].Vh = cv.take<float>((size_t)l * l);
+    b[i].Sh = cv.take<double>((size_t)l);
+  }
+  // Y = A Omega (Sec. 3.1, Fig. 1 step 2)
+  std::vector<BGemm> gs;
+  for (int i = 0; i < batch; ++i) {
+    const int l = it[i].k + p;
+    gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 0, nullptr, 0, b[i].Y, l,
+                         it[i].m, l, it[i].n, l, i));
+  }
+  add_gemm_stage(P, gs);
+  // power scheme, orthonormalising before every product (Alg. 5, s = 1)
+  for (int j = 0; j < q; ++j) {
+    add_orth(P, batch, it, p, b, false, false);
+    gs.clear();
+    for (int i = 0; i < batch; ++i) {   // Z = A^T Y
+      const int l = it[i].k + p;
+      gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 1, b[i].Y, l, b[i].Z, l,
+                           it[i].n, l, it[i].m, l, i));
+    }
+    add_gemm_stage(P, gs);
+    add_orth(P, batch, it, p, b, true, false);
+    gs.clear();
+    for (int i = 0; i < batch; ++i) {   // Y = A Z
+      const int l = it[i].k + p;
+      gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 0, b[i].Z, l, b[i].Y, l,
+                           it[i].m, l, it[i].n, l, i));
+    }
+    add_gemm_stage(P, gs);
+  }
+  add_orth(P, batch, it, p, b, false, false);   // Q = orth(Y)
+  gs.clear();
+  for (int i = 0; i < batch; ++i) {             // Bt = A^T Q
+    const int l = it[i].k + p;
+    gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 1, b[i].Y, l, b[i].Z, l,
+                         it[i].n, l, it[i].m, l, i));
+  }
+  add_gemm_stage(P, gs);
+  add_orth(P, batch, it, p, b, true, true);     // Bt = Qh Rh
+  {
+    Stage st{ST_SVD, (int)P.svds.size(), batch};   // Rh = Uh diag(Sh) Vh^T
+    for (int i = 0; i < batch; ++i) {
+      BSvd s;
+      s.M = b[i].Racc;
+      s.Uj = b[i].Uj;
+      s.Uh = b[i].Uh;
+      s.Vh = b[i].Vh;
+      s.Sh = b[i].Sh;
+      s.l = it[i].k + p;
+      P.svds.push_back(s);
+    }
+    P.stages.push_back(st);
+  }
+  gs.clear();
+  for (int i = 0; i < batch; ++i) {   // U = Q Vh(:, :k), V = Qh Uh(:, :k)
+    const int l = it[i].k + p, k = it[i].k;
+    gs.push_back(gemm_of(b[i].Y, l, 0, b[i].Vh, l, U ? U + it[i].u_off : nullptr, k, it[i].m, k,
+                         l, k, i));
+    gs.push_back(gemm_of(b[i].Z, l, 0, b[i].Uh, l, V ? V + it[i].v_off : nullptr, k, it[i].n, k,
+                         l, k, i));
+  }
+  add_gemm_stage(P, gs);
+  {
+    Stage st{ST_SIGN, (int)P.signs.size(), batch};
+    for (int i = 0; i < batch; ++i) {
+      BSign s;
+      s.U = U ? U + it[i].u_off : nullptr;
+      s.V = V ? V + it[i].v_off : nullptr;
+      s.S = S ? S + it[i].s_off : nullptr;
+      s.Sh = b[i].Sh;
+      s.m = it[i].m;
+      s.n = it[i].n;
+      s.k = it[i].k;
+      P.signs.push_back(s);
+    }
+    P.stages.push_back(st);
+  }
+  // the tables themselves
+  *tables = cv.base ? cv.base + ((cv.off + 255) & ~(size_t)255) : nullptr;
+  cv.take<BGemm>(P.gemms.size());
+  cv.take<int2>(P.tasks.size());
+  cv.take<BChol>(P.chols.size());
+  cv.take<BTrmm>(P.trmms.size());
+  cv.take<BSvd>(P.svds.size());
+  cv.take<BSign>(P.signs.size());
+  return cv.off + 256;
+}
+
+}  // namespace
+
+}  // namespace rsvd
+
+using namespace rsvd;
+
+extern "C" {
+
+size_t rsvd_svd_batched_workspace_size(int batch, const rsvd_batch_item* items, int p, int q) {
+  if (!items_ok(batch, items, p, q)) return 0;
+  Plan P;
+  char* tables = nullptr;
+  return build(batch, items, p, q, nullptr, nullptr, nullptr, nullptr, nullptr, P, &tables);
+}
+
+rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int q,
+                             uint64_t seed, const float* A, float* U, double* S, float* V,
+                             void* work, size_t work_bytes, int* d_info, void* stream) {
+  if (!items_ok(batch, items, p, q) || !A || !U || !S || !V) return RSVD_ERR_INVALID_ARG;
+  if (!work || ((uintptr_t)work & 255u)) return RSVD_ERR_INVALID_ARG;
+  Plan dry;
+  char* t0 = nullptr;
+  const size_t need = build(batch, items, p, q, nullptr, nullptr, nullptr, nullptr, nullptr, dry,
+                            &t0);
+  if (need > work_bytes) return RSVD_ERR_WORKSPACE;
+  Plan P;
+  char* tables = nullptr;
+  build(batch, items, p, q, A, U, S, V, (char*)work, P, &tables);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (d_info && cudaMemsetAsync(d_info, 0, sizeof(int), s) != cudaSuccess) return RSVD_ERR_CUDA;
+  // upload the tables (same carving as in build)
+  Carve cv;
+  cv.base = (char*)work;
+  cv.off = (size_t)(tables - (char*)work);
+  BGemm* dg = cv.take<BGemm>(P.gemms.size());
+  int2* dt = cv.take<int2>(P.tasks.size());
+  BChol* dc = cv.take<BChol>(P.chols.size());
+  BTrmm* dm = cv.take<BTrmm>(P.trmms.size());
+  BSvd* dv = cv.take<BSvd>(P.svds.size());
+  BSign* dsg = cv.take<BSign>(P.signs.size());
+#define UPLOAD(dst, vec)                                                                 \
+  if (!vec.empty() && cudaMemcpyAsync(dst, vec.data(), vec.size() * sizeof(vec[0]),      \
+                                      cudaMemcpyHostToDevice, s) != cudaSuccess)         \
+    return RSVD_ERR_CUDA;
+  UPLOAD(dg, P.gemms);
+  UPLOAD(dt, P.tasks);
+  UPLOAD(dc, P.chols);
+  UPLOAD(dm, P.trmms);
+  UPLOAD(dv, P.svds);
+  UPLOAD(dsg, P.signs);
+#undef UPLOAD
+  for (const Stage& st : P.stages) {
+    cudaError_t e = cudaSuccess;
+    switch (st.kind) {
+      case ST_GEMM: e = launch_bgemm(dg, dt + st.first, st.count, seed, s); break;
+      case ST_CHOL: e = launch_chol_batched(dc + st.first, st.count, P.lmax, d_info, s); break;
+      case ST_TRMM: e = launch_trmm_batched(dm + st.first, st.count, s); break;
+      case ST_SVD:
+        e = launch_small_svd_batched(dv + st.first, st.count, P.lmax, 30, d_info, s);
+        break;
+      case ST_SIGN: e = launch_sign_batched(dsg + st.first, st.count, s); break;
+      default: break;
+    }
+    if (e != cudaSuccess) return RSVD_ERR_CUDA;
+  }
+  return RSVD_OK;
+}
+
+}  // extern "C"

@@ -11,4 +11,5 @@ matrices) and D a prescribed decaying spectrum, plus optional i.i.d. Gaussian
 noise of standard deviation ``noise``.
 """
 from .matrices import (CONFIGS, config, spectrum, make_matrix_np,  # noqa: F401
-                       make_matrix_torch, low_rank_np)
+                       make_matrix_torch, low_rank_np, BATCH_CONFIGS, batch_sizes,
+                       make_batch_torch)

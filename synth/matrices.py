@@ -14,6 +14,43 @@ CONFIGS = {
                              spectrum="sqrtgap64", r=4096, noise=0.0),
 }
 
+# The batched workload: 512 FP32 problems, m ~ U[256, 4096], n ~ U[128, 2048]
+# with n <= m, k drawn from {8, 16, 32, 64}, p = 8, q = 1, sigma_j = exp(-j/k).
+BATCH_CONFIGS = {
+    "c4_f32_batched512": dict(index=4, batch=512, m_range=(256, 4096), n_range=(128, 2048),
+                              ks=(8, 16, 32, 64), p=8, q=1, dtype="float32", spectrum="expk"),
+}
+
+
+def batch_sizes(name, batch=None):
+    """(ms, ns, ks) of a batched workload, drawn with the workload's seed."""
+    c = BATCH_CONFIGS[name]
+    b = c["batch"] if batch is None else batch
+    rng = np.random.default_rng(0xA000 + c["index"])
+    ms = rng.integers(c["m_range"][0], c["m_range"][1] + 1, size=b)
+    ns = rng.integers(c["n_range"][0], c["n_range"][1] + 1, size=b)
+    ns = np.minimum(ns, ms)
+    ks = rng.choice(np.asarray(c["ks"]), size=b)
+    ns = np.maximum(ns, ks + c["p"])     # l = k + p <= n
+    return [int(x) for x in ms], [int(x) for x in ns], [int(x) for x in ks]
+
+
+def make_batch_torch(ms, ns, ks, seed, device="cuda", tail=6):
+    """A_i = U_i diag(sigma) V_i^T with sigma_j = exp(-j/k_i), j <= min(n_i, tail k_i)
+    (the spectrum is cut where it falls below e^-tail), U_i and V_i orthonormalised
+    Gaussian matrices drawn and factored on ``device`` (torch QR).  float32 list."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = []
+    for m, n, k in zip(ms, ns, ks):
+        r = int(min(n, tail * k))
+        sig = torch.exp(-torch.arange(1, r + 1, device=device, dtype=torch.float64) / k)
+        U = torch.linalg.qr(torch.randn(m, r, generator=g, device=device, dtype=torch.float64))[0]
+        V = torch.linalg.qr(torch.randn(n, r, generator=g, device=device, dtype=torch.float64))[0]
+        out.append(((U * sig[None, :]) @ V.T).to(torch.float32).contiguous())
+    return out
+
 
 def config(name):
     c = dict(CONFIGS[name])
