@@ -396,6 +396,77 @@ def mixed_precision_line(rs, A, plan32, cfg, args, seed, world, dev, ms32, peaks
     return out
 
 
+def batched_line(rs, args, world, dev, peaks, peak_kind, name="c4_f32_batched512"):
+    """The batched workload (512 FP32 problems of uneven sizes): the batched
+    call timed like the main line, against the same problems run one by one
+    through the FP32 path (rsvd_svd), both judged by their relative errors."""
+    import torch
+    from synth import BATCH_CONFIGS, batch_sizes, make_batch_torch
+    c = BATCH_CONFIGS[name]
+    p, q = c["p"], c["q"]
+    ms, ns, ks = batch_sizes(name)
+    seed = 0x5EED + c["index"]
+    mats = make_batch_torch(ms, ns, ks, 0xA000 + c["index"], device=dev)
+    plan = rs.BatchPlan(ms, ns, ks, p, q, dev)
+    Ap = plan.pack(mats)
+    for _ in range(args.warmup):
+        plan.run(Ap, seed)
+    torch.cuda.synchronize()
+    rs.check_info(plan.info, "batched warmup")
+    stream = torch.cuda.current_stream()
+    launches0 = rs.kernel_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.run(Ap, seed)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = (rs.kernel_launch_count() - launches0) / args.steps
+    rs.check_info(plan.info, "batched steps")
+    ms_b = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    # the same problems through the single-problem FP32 path, one call each
+    for i in range(min(4, len(mats))):
+        rs.svd(mats[i], ks[i], p, q, seed)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    single = [rs.svd(mats[i], ks[i], p, q, seed, check=False) for i in range(len(mats))]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    errs_b, errs_s = [], []
+    for i, A in enumerate(mats):
+        U, S, V = plan.result(i)
+        errs_b.append(rel_err_device(rs, A, U, S, V))
+        errs_s.append(rel_err_device(rs, A, *single[i]))
+    flops = sum(2.0 * m * n * (k + p) * (2 * q + 2) for m, n, k in zip(ms, ns, ks))
+    a_bytes = sum(4.0 * m * n for m, n in zip(ms, ns))
+    gbs = (2 * q + 2) * a_bytes / (ms_b * 1e-3) / 1e9
+    eb, es = float(np.mean(errs_b)), float(np.mean(errs_s))
+    return {
+        "workload": "%s: %d FP32 problems, m in [%d, %d], n in [%d, %d], k in %s, p = %d, q = %d, "
+                    "sigma_j = exp(-j/k)" % (name, len(ms), min(ms), max(ms), min(ns), max(ns),
+                                             sorted(set(ks)), p, q),
+        "ms_per_step": ms_b, "unit": UNIT,
+        "value": world * flops / (ms_b * 1e-3) / 1e12,
+        "flops_definition": "sum over problems of 2 m n l (2q + 2) (the passes over A)",
+        "launches_per_step": launches,
+        "fp32_one_by_one_ms": ms_s,
+        "speedup_vs_fp32_one_by_one": ms_s / ms_b,
+        "rel_err_mean": eb, "rel_err_fp32_mean": es, "rel_err_ratio": eb / es,
+        "rel_err_max_ratio": float(np.max(np.array(errs_b) / np.array(errs_s))),
+        "rel_err_definition": "||A_i - U_i S_i V_i^T||_F / ||A_i||_F, mean over problems",
+        "a_pass_hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_kind + " STREAM-style copy",
+                       "work": "(2q + 2) reads of every A_i per step (4 B per entry), whole-step time"},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -407,6 +478,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the BF16-storage (mixed precision) measurement")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-workload (512 small problems) measurement")
     args = ap.parse_args()
 
     from synth import config as get_config
@@ -509,6 +582,10 @@ def main():
         mixed = mixed_precision_line(rs, A, plan, cfg, args, seed, world, dev, ms, peaks,
                                      peak_kind)
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_line(rs, args, world, dev, peaks, peak_kind)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -535,6 +612,7 @@ def main():
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "mixed": mixed,
+            "batched": batched,
         }
         print(json.dumps(line))
     if world > 1:
