@@ -1,9 +1,10 @@
 // Kernels of the batched path: many small, unevenly sized RSVD problems, each
 // step of Alg. 5 one launch over every problem of the batch.
 //
-// bgemm_kernel is a grouped fp32 GEMM: a task is (problem GEMM, 64-row block of
-// its output); the CTA computes the block's full width (N <= 128) over the
-// whole contraction, in 32-deep chunks staged in shared memory.  The sketch's
+// bgemm_kernel is a grouped fp32 GEMM: a task is (problem GEMM, block of 64, 128
+// or 256 output rows, by the width); the CTA computes the block's full width
+// (N <= 128) over the whole contraction, in 32-deep chunks staged in shared
+// memory.  The sketch's
 // Omega is generated in the chunk instead of read (Sec. 3.1: Gaussian test
 // matrix; the problem index is the counter's batch word).  Products are plain
 // fp32 FMAs: the problems are small, so the work is spread over many CTAs and
@@ -14,50 +15,82 @@
 namespace rsvd {
 
 namespace {
-constexpr int BG_T = 256;             // threads: 16 row groups of 4 rows x 16 column lanes
+constexpr int BG_T = 256;             // threads: 16 row groups x 16 column lanes
 constexpr int BG_TK = 32;             // contraction chunk
-constexpr int BG_AP = BGEMM_TM + 4;   // padded row of the staged A chunk (float4-aligned)
-constexpr int BG_WP = BATCH_LMAX + 4;
 }  // namespace
 
-__global__ void __launch_bounds__(BG_T) bgemm_kernel(const BGemm* __restrict__ gemms,
+// RPT rows per thread: the tile is TM = 16 RPT rows by NC * 16 columns, NC = 32 / RPT
+// (64 x 128, 128 x 64 or 256 x 32), so that every thread holds 32 accumulators
+// whatever the width.  The next chunk's A and W values are prefetched into
+// registers while the current chunk is multiplied from shared memory.
+template <int RPT>
+__global__ void __launch_bounds__(BG_T, 2) bgemm_kernel(const BGemm* __restrict__ gemms,
                                                      const int2* __restrict__ tasks,
                                                      uint64_t seed) {
-  __shared__ __align__(16) float As[BG_TK][BG_AP];   // As[kk][r] = op(A)(row0 + r, k0 + kk)
-  __shared__ __align__(16) float Ws[BG_TK][BG_WP];   // Ws[kk][c] = W(k0 + kk, c)
+  constexpr int TM = 16 * RPT;
+  constexpr int NC = 32 / RPT;
+  constexpr int NW = NC * 16;               // widest W handled
+  constexpr int PA = TM * BG_TK / BG_T;     // A values per thread and chunk
+  constexpr int PW = BG_TK * NW / BG_T;     // W values per thread and chunk (at most)
+  __shared__ __align__(16) float As[BG_TK][TM + 4];   // As[kk][r] = op(A)(row0 + r, k0 + kk)
+  __shared__ __align__(16) float Ws[BG_TK][NW + 4];   // Ws[kk][c] = W(k0 + kk, c)
   const int2 tk = tasks[blockIdx.x];
   const BGemm g = gemms[tk.x];
   const int row0 = tk.y;
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
   const int M = g.M, N = g.N, K = g.K;
-  const int nc = (N + 15) >> 4;             // column lanes per thread (<= 8)
-  float acc[4][8];
+  const int nc = (N + 15) >> 4;
+  float ra[PA], rw[PW];
+  auto load_chunk = [&](int k0) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[q][c] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += BG_TK) {
-    if (!g.transA) {   // A is M x K: rows of 32 contiguous values
-      for (int e = tid; e < BGEMM_TM * BG_TK; e += BG_T) {
-        const int r = e >> 5, kk = e & 31;
-        const int gr = row0 + r, gk = k0 + kk;
-        As[kk][r] = (gr < M && gk < K) ? g.A[(int64_t)gr * g.lda + gk] : 0.f;
+    for (int j = 0; j < PA; ++j) {
+      const int e = tid + j * BG_T;
+      int r, kk;
+      if (!g.transA) {
+        r = e >> 5;
+        kk = e & 31;
+      } else {
+        kk = e / TM;
+        r = e - kk * TM;
       }
-    } else {           // A is stored K x M: op(A)(r, kk) = A(kk, r), rows of 64 values
-      for (int e = tid; e < BGEMM_TM * BG_TK; e += BG_T) {
-        const int kk = e >> 6, r = e & 63;
-        const int gr = row0 + r, gk = k0 + kk;
-        As[kk][r] = (gr < M && gk < K) ? g.A[(int64_t)gk * g.lda + gr] : 0.f;
-      }
+      const int gr = row0 + r, gk = k0 + kk;
+      float v = 0.f;
+      if (gr < M && gk < K)
+        v = g.transA ? g.A[(int64_t)gk * g.lda + gr] : g.A[(int64_t)gr * g.lda + gk];
+      ra[j] = v;
     }
     if (g.W) {
-      for (int e = tid; e < BG_TK * N; e += BG_T) {
-        const int kk = e / N, c = e - (e / N) * N;
+#pragma unroll
+      for (int j = 0; j < PW; ++j) {
+        const int e = tid + j * BG_T;
+        const int kk = e / NW, c = e - (e / NW) * NW;
         const int gk = k0 + kk;
-        Ws[kk][c] = gk < K ? g.W[(int64_t)gk * g.ldw + c] : 0.f;
+        rw[j] = (c < N && gk < K) ? g.W[(int64_t)gk * g.ldw + c] : 0.f;
       }
-    } else {
+    }
+  };
+  auto store_chunk = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < PA; ++j) {
+      const int e = tid + j * BG_T;
+      int r, kk;
+      if (!g.transA) {
+        r = e >> 5;
+        kk = e & 31;
+      } else {
+        kk = e / TM;
+        r = e - kk * TM;
+      }
+      As[kk][r] = ra[j];
+    }
+    if (g.W) {
+#pragma unroll
+      for (int j = 0; j < PW; ++j) {
+        const int e = tid + j * BG_T;
+        Ws[e / NW][e - (e / NW) * NW] = rw[j];
+      }
+    } else {   // Omega rows k0 .. k0 + 31, generated
       const int nq = (N + 3) >> 2;
       for (int e = tid; e < BG_TK * nq; e += BG_T) {
         const int kk = e / nq, qd = e - (e / nq) * nq;
@@ -70,40 +103,66 @@ __global__ void __launch_bounds__(BG_T) bgemm_kernel(const BGemm* __restrict__ g
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if (4 * qd + t < N) Ws[kk][4 * qd + t] = z[t];
+          if (4 * qd + t < NW) Ws[kk][4 * qd + t] = (4 * qd + t < N) ? z[t] : 0.f;
       }
     }
+  };
+  float acc[RPT][NC];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[q][c] = 0.f;
+  load_chunk(0);
+  for (int k0 = 0; k0 < K; k0 += BG_TK) {
+    store_chunk(k0);
     __syncthreads();
+    if (k0 + BG_TK < K) load_chunk(k0 + BG_TK);
 #pragma unroll 4
     for (int kk = 0; kk < BG_TK; ++kk) {
-      const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
-      const float av[4] = {a4.x, a4.y, a4.z, a4.w};
-      float wv[8];
+      float av[RPT];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) wv[c] = (c < nc) ? Ws[kk][tx + 16 * c] : 0.f;
+      for (int q4 = 0; q4 < RPT / 4; ++q4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][RPT * ty + 4 * q4]);
+        av[4 * q4] = a4.x;
+        av[4 * q4 + 1] = a4.y;
+        av[4 * q4 + 2] = a4.z;
+        av[4 * q4 + 3] = a4.w;
+      }
+      float wv[NC];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int c = 0; c < NC; ++c) wv[c] = Ws[kk][tx + 16 * c];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[q][c] = fmaf(av[q], wv[c], acc[q][c]);
+      for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[q][c] = fmaf(av[q], wv[c], acc[q][c]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int gr = row0 + 4 * ty + q;
+  for (int q = 0; q < RPT; ++q) {
+    const int gr = row0 + RPT * ty + q;
     if (gr >= M) continue;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < NC; ++c) {
       const int col = tx + 16 * c;
       if (c < nc && col < g.ncol) g.C[(int64_t)gr * g.ldc + col] = acc[q][c];
     }
   }
 }
 
-cudaError_t launch_bgemm(const BGemm* gemms, const int2* tasks, int ntasks, uint64_t seed,
-                         cudaStream_t s) {
+int bgemm_rows(int N) { return N > 64 ? 64 : (N > 32 ? 128 : 256); }
+
+cudaError_t launch_bgemm(const BGemm* gemms, const int2* tasks, int ntasks, int rows,
+                         uint64_t seed, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
-  bgemm_kernel<<<ntasks, BG_T, 0, s>>>(gemms, tasks, seed);
+  if (rows == 64)
+    bgemm_kernel<4><<<ntasks, BG_T, 0, s>>>(gemms, tasks, seed);
+  else if (rows == 128)
+    bgemm_kernel<8><<<ntasks, BG_T, 0, s>>>(gemms, tasks, seed);
+  else if (rows == 256)
+    bgemm_kernel<16><<<ntasks, BG_T, 0, s>>>(gemms, tasks, seed);
+  else
+    return cudaErrorInvalidValue;
   count_launch();
   return cudaGetLastError();
 }

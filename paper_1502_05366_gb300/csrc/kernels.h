@@ -233,10 +233,11 @@ struct BGemm {
   int transA;
   int batch;
 };
-// tasks: (gemm index, first output row), one CTA each
-cudaError_t launch_bgemm(const BGemm* gemms, const int2* tasks, int ntasks, uint64_t seed,
-                         cudaStream_t s);
-constexpr int BGEMM_TM = 64;        // output rows per task
+// tasks: (gemm index, first output row), one CTA each, all of one block height
+// `rows` = bgemm_rows(N) of their GEMMs (64, 128 or 256)
+cudaError_t launch_bgemm(const BGemm* gemms, const int2* tasks, int ntasks, int rows,
+                         uint64_t seed, cudaStream_t s);
+int bgemm_rows(int N);
 constexpr int BATCH_LMAX = 128;     // largest sketch width of the batched path
 // Cholesky R^T R = G and R^-1 of one l x l Gram per CTA (the shifted CholeskyQR
 // factorisation of chol_kernel); R, Rinv l x l (ld l)

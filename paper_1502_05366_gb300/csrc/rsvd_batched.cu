@@ -38,6 +38,7 @@ enum StageKind { ST_GEMM, ST_CHOL, ST_TRMM, ST_SVD, ST_SIGN };
 struct Stage {
   int kind;
   int first, count;   // into the table of the kind (gemm: tasks; others: problems)
+  int rows;           // gemm: block height of the tasks
 };
 
 struct Plan {
@@ -63,16 +64,20 @@ bool items_ok(int batch, const rsvd_batch_item* it, int p, int q) {
   return true;
 }
 
-// One GEMM per problem, tasks over 64-row blocks of the output.
+// One GEMM per problem; tasks over blocks of output rows whose height follows
+// the width, one launch per height.
 void add_gemm_stage(Plan& P, const std::vector<BGemm>& gs) {
-  Stage st{ST_GEMM, (int)P.tasks.size(), 0};
-  for (const BGemm& g : gs) {
-    const int gi = (int)P.gemms.size();
-    P.gemms.push_back(g);
-    for (int r0 = 0; r0 < g.M; r0 += BGEMM_TM) P.tasks.push_back(make_int2(gi, r0));
+  const int g0 = (int)P.gemms.size();
+  for (const BGemm& g : gs) P.gemms.push_back(g);
+  for (int rows = 64; rows <= 256; rows *= 2) {
+    Stage st{ST_GEMM, (int)P.tasks.size(), 0, rows};
+    for (int i = 0; i < (int)gs.size(); ++i) {
+      if (bgemm_rows(gs[i].N) != rows) continue;
+      for (int r0 = 0; r0 < gs[i].M; r0 += rows) P.tasks.push_back(make_int2(g0 + i, r0));
+    }
+    st.count = (int)P.tasks.size() - st.first;
+    if (st.count > 0) P.stages.push_back(st);
   }
-  st.count = (int)P.tasks.size() - st.first;
-  P.stages.push_back(st);
 }
 
 BGemm gemm_of(const float* A, int64_t lda, int transA, const float* W, int64_t ldw, float* C,
@@ -99,7 +104,7 @@ void add_orth(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<
               bool on_z, bool want_R) {
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<BGemm> gram, apply;
-    Stage sc{ST_CHOL, (int)P.chols.size(), batch};
+    Stage sc{ST_CHOL, (int)P.chols.size(), batch, 0};
     for (int i = 0; i < batch; ++i) {
       const int l = it[i].k + p;
       const int64_t rows = on_z ? it[i].n : it[i].m;
@@ -121,7 +126,7 @@ void add_orth(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<
     add_gemm_stage(P, apply);
   }
   if (want_R) {
-    Stage st{ST_TRMM, (int)P.trmms.size(), batch};
+    Stage st{ST_TRMM, (int)P.trmms.size(), batch, 0};
     for (int i = 0; i < batch; ++i) {
       BTrmm t;
       t.R = b[i].R;
@@ -195,7 +200,7 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
   add_gemm_stage(P, gs);
   add_orth(P, batch, it, p, b, true, true);     // Bt = Qh Rh
   {
-    Stage st{ST_SVD, (int)P.svds.size(), batch};   // Rh = Uh diag(Sh) Vh^T
+    Stage st{ST_SVD, (int)P.svds.size(), batch, 0};   // Rh = Uh diag(Sh) Vh^T
     for (int i = 0; i < batch; ++i) {
       BSvd s;
       s.M = b[i].Racc;
@@ -218,7 +223,7 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
   }
   add_gemm_stage(P, gs);
   {
-    Stage st{ST_SIGN, (int)P.signs.size(), batch};
+    Stage st{ST_SIGN, (int)P.signs.size(), batch, 0};
     for (int i = 0; i < batch; ++i) {
       BSign s;
       s.U = U ? U + it[i].u_off : nullptr;
@@ -297,7 +302,7 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
   for (const Stage& st : P.stages) {
     cudaError_t e = cudaSuccess;
     switch (st.kind) {
-      case ST_GEMM: e = launch_bgemm(dg, dt + st.first, st.count, seed, s); break;
+      case ST_GEMM: e = launch_bgemm(dg, dt + st.first, st.count, st.rows, seed, s); break;
       case ST_CHOL: e = launch_chol_batched(dc + st.first, st.count, P.lmax, d_info, s); break;
       case ST_TRMM: e = launch_trmm_batched(dm + st.first, st.count, s); break;
       case ST_SVD:
