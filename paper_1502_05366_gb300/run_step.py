@@ -11,6 +11,8 @@ path without holding the full matrix A on the device:
   small_svd  SVD of an l x l upper-triangular factor           (Alg. 5)
   cpqr       k-step column-pivoted QR + T = S11^-1 S12 of r x n (Sec. 4, ID);
              float32: the double-float kernel of the FP32 path, float64: FP64
+  batched    one rsvd_svd_batched call on the 512-problem workload (uneven FP32
+             problems, sigma_j = exp(-j/k)); --batch limits the problem count
 
 Example:  python -m paper_1502_05366_gb300.run_step --step cpqr --r 220 --n 20000 --k 200
 
@@ -43,6 +45,13 @@ def _inputs(args, dev):
         M = torch.randn(args.l, args.l, generator=g, dtype=torch.float64)
         M = torch.triu(M) * (1.0 / torch.arange(1, args.l + 1, dtype=torch.float64))
         return M.to(dev, dt), None
+    if args.step == "batched":
+        from synth import BATCH_CONFIGS, batch_sizes, make_batch_torch
+        c = BATCH_CONFIGS["c4_f32_batched512"]
+        ms, ns, ks = batch_sizes("c4_f32_batched512", args.batch)
+        mats = make_batch_torch(ms, ns, ks, 0xA000 + c["index"], device=dev)
+        plan = rs.BatchPlan(ms, ns, ks, c["p"], c["q"], dev)
+        return plan, plan.pack(mats)
     if args.step == "cpqr":
         # rows scaled by 1/i like B = Q^T A of the same spectrum
         M = torch.randn(args.r, args.n, generator=g, dtype=torch.float64)
@@ -65,13 +74,16 @@ def _call(args, X0, X1):
         return rs.small_svd(X0, check=False)
     if s == "cpqr":
         return rs.cpqr_id(X0, args.k, check=False)
+    if s == "batched":
+        return X0.run(X1, args.seed)
     raise ValueError(s)
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--step", required=True,
-                    choices=["sample", "apply_n", "apply_t", "orth", "small_svd", "cpqr"])
+                    choices=["sample", "apply_n", "apply_t", "orth", "small_svd", "cpqr",
+                             "batched"])
     ap.add_argument("--m", type=int, default=50000)
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--l", type=int, default=220)
@@ -80,6 +92,7 @@ def main(argv=None):
     ap.add_argument("--dtype", default="float32", choices=["float32", "float64", "bfloat16"],
                     help="element type of A (bfloat16: the passes over A only)")
     ap.add_argument("--seed", type=int, default=0x5EED)
+    ap.add_argument("--batch", type=int, default=None, help="problems of --step batched")
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
     if not torch.cuda.is_available():

@@ -42,12 +42,19 @@ def make_batch_torch(ms, ns, ks, seed, device="cuda", tail=6):
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
+
+    def qr_q(X):
+        try:
+            return torch.linalg.qr(X)[0]
+        except RuntimeError:   # no device LAPACK in this process: factor on the host
+            return torch.linalg.qr(X.cpu())[0].to(X.device)
+
     out = []
     for m, n, k in zip(ms, ns, ks):
         r = int(min(n, tail * k))
         sig = torch.exp(-torch.arange(1, r + 1, device=device, dtype=torch.float64) / k)
-        U = torch.linalg.qr(torch.randn(m, r, generator=g, device=device, dtype=torch.float64))[0]
-        V = torch.linalg.qr(torch.randn(n, r, generator=g, device=device, dtype=torch.float64))[0]
+        U = qr_q(torch.randn(m, r, generator=g, device=device, dtype=torch.float64))
+        V = qr_q(torch.randn(n, r, generator=g, device=device, dtype=torch.float64))
         out.append(((U * sig[None, :]) @ V.T).to(torch.float32).contiguous())
     return out
 
