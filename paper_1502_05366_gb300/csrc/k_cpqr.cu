@@ -1059,24 +1059,26 @@ __global__ void __launch_bounds__(256) upper_solve_df_warp_kernel(
         xl[c] = __shfl_sync(0xffffffffu, x.y, owner);
       }
       const float2* ucol = U + (int64_t)i * kk;
+      // only the row slots t <= ti hold rows q <= i; ti is the same in every
+      // lane, so leaving the unrolled loop is a uniform branch and the empty
+      // slots cost no issue slots
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
+        if (t > ti) break;
         const int q = lane + 32 * t;
-        if (t <= ti) {
-          if (q < i) {
-            const float2 u = __ldg(ucol + q);
+        if (q < i) {
+          const float2 u = __ldg(ucol + q);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              const float2 r = df_fms2(make_float2(sh[c][t], sl[c][t]), make_float2(xh[c], xl[c]), u);
-              sh[c][t] = r.x;
-              sl[c][t] = r.y;
-            }
-          } else if (q == i) {
+          for (int c = 0; c < NC; ++c) {
+            const float2 r = df_fms2(make_float2(sh[c][t], sl[c][t]), make_float2(xh[c], xl[c]), u);
+            sh[c][t] = r.x;
+            sl[c][t] = r.y;
+          }
+        } else if (q == i) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              sh[c][t] = xh[c];
-              sl[c][t] = xl[c];
-            }
+          for (int c = 0; c < NC; ++c) {
+            sh[c][t] = xh[c];
+            sl[c][t] = xl[c];
           }
         }
       }
