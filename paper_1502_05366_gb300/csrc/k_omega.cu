@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
           for (int e = 0; e < 4; ++e) {
             const int64_t krow = kc * OBK + kk4 * 4 + e;
             float z[4] = {0.f, 0.f, 0.f, 0.f};
-            if (krow < P.K) OmegaGen<float>::quad(P.seed, (uint32_t)krow, (uint32_t)qd, z);
+            if (krow < P.K) OmegaGen<float>::quad(P.seed, (uint32_t)krow, (uint32_t)(qd + P.qoff), z);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
               // z is bf16-exact: its upper 16 bits are the bf16 encoding
@@ -731,7 +731,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(OTHREADS2, 1)
             for (int e = 0; e < 2; ++e) {
               const int64_t krow = kc * OBK + kk2 * 2 + e;
               float z[4] = {0.f, 0.f, 0.f, 0.f};
-              if (krow < P.K) OmegaGen<float>::quad(P.seed, (uint32_t)krow, (uint32_t)qd, z);
+              if (krow < P.K) OmegaGen<float>::quad(P.seed, (uint32_t)krow, (uint32_t)(qd + P.qoff), z);
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
                 const uint32_t b = (4 * qd + c < P.lvalid) ? (__float_as_uint(z[c]) >> 16) : 0u;
@@ -800,6 +800,7 @@ static cudaError_t launch_tc_omega2(const TcGemm& g, cudaStream_t s) {
   P.bm = OUNIT;
   P.L = g.L;
   P.lvalid = g.lvalid;
+  P.qoff = g.col0 / 4;
   P.seed = g.seed;
   P.tiles = sus;
   P.kiters = kiters;
@@ -860,6 +861,7 @@ cudaError_t launch_tc_omega(const TcGemm& g, cudaStream_t s) {
   P.wadd = 0;
   P.L = g.L;
   P.lvalid = g.lvalid;
+  P.qoff = g.col0 / 4;
   P.seed = g.seed;
   P.tiles = tiles;
   P.kiters = kiters;

@@ -35,6 +35,7 @@
 // RSVD_ERR_TIMEOUT, every role leaves its loop, the producer waits (bounded)
 // for its own copies in flight, TMEM is freed and the CTA returns.
 #include <cuda.h>
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -560,6 +561,32 @@ static cudaError_t launch_form(const CUtensorMap& ma, const CUtensorMap* mw, con
 }
 
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
+  if (g.L > 256 && g.L % 16 == 0 && g.L <= 1024) {
+    // wider outputs (the sketch width l > 256): column chunks of at most 256,
+    // one launch each over the whole of A.  Chunk c0 takes rows c0.. of the
+    // transposed bf16 operand and of the transposed output split, output
+    // columns c0.., and for Omega the columns c0.. of the Gaussian stream.
+    for (int c0 = 0; c0 < g.L; c0 += 256) {
+      const int Lc = std::min(256, g.L - c0);
+      TcGemm gc = g;
+      gc.L = Lc;
+      gc.col0 = g.col0 + c0;
+      gc.lvalid = std::max(0, std::min(g.lvalid - c0, Lc));
+      gc.ncols = std::max(0, std::min(g.ncols - c0, Lc));
+      gc.out = g.out + c0;
+      auto off16 = [&](const void* p, int64_t ld) -> const void* {
+        return p ? (const void*)((const __nv_bfloat16*)p + (int64_t)c0 * ld) : nullptr;
+      };
+      gc.Whi = off16(g.Whi, g.ldw);
+      gc.Wlo = off16(g.Wlo, g.ldw);
+      gc.Wlo2 = off16(g.Wlo2, g.ldw);
+      gc.out_hi = g.out_hi ? (void*)((__nv_bfloat16*)g.out_hi + (int64_t)c0 * g.ldt) : nullptr;
+      gc.out_lo = g.out_lo ? (void*)((__nv_bfloat16*)g.out_lo + (int64_t)c0 * g.ldt) : nullptr;
+      cudaError_t e = launch_tc_gemm(gc, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   if (!tc_supported(g.L)) return cudaErrorInvalidValue;
   if (g.form == 1 && g.omega) return cudaErrorInvalidValue;
   if (g.form == 0 && g.omega) return launch_tc_omega(g, s);

@@ -180,8 +180,11 @@ struct TcGemm {
   uint64_t seed;
   int64_t rows;         // output rows (M): rows of A (form 0) or columns of A (form 1)
   int64_t K;            // contraction length
-  int L;                // output columns (multiple of 16, <= 256)
+  int L;                // output columns (multiple of 16; above 256 launch_tc_gemm runs
+                        // column chunks of at most 256)
   int lvalid;           // Omega columns >= lvalid are zero
+  int col0;             // Omega: global index of output column 0 (a multiple of 4; the
+                        // column chunks of L > 256 start at 256, 512, ..)
   const float* A;       // source, row-major, 16-byte aligned rows: fp32 (lda % 4 == 0) or,
                         // with a_bf16, bf16 values (lda % 8 == 0) behind this pointer
   int64_t lda;          // elements

@@ -681,7 +681,7 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 static bool want_tc(int dtype, const Opts& o, int l, const void* A, int64_t lda) {
   if (dtype != RSVD_F32 && dtype != RSVD_BF16) return false;
   if (o.precision != RSVD_PREC_TC && o.precision != RSVD_PREC_MIXED) return false;
-  if (!tc_supported(padL(l))) return false;
+  if (padL(l) > 1024) return false;   // widths above 256 run in column chunks
   if (A && !aligned16(A)) return false;
   if (lda % (dtype == RSVD_BF16 ? 8 : 4) != 0) return false;
   return true;

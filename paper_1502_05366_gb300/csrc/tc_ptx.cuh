@@ -34,6 +34,7 @@ struct TcParams {
   // wmul c + wadd (ustride = bm, uoff = 0, wmul = 1, wadd = 0 for one CTA per worker)
   int64_t ustride;
   int uoff, wmul, wadd;
+  int qoff = 0;    // Omega: Philox quad index of the first output column (column / 4)
 };
 
 // Fixed-order sum of the stream-K partials of the tiles split between CTAs
