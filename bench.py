@@ -56,6 +56,9 @@ def a_pass_bytes(m, n, elem=4):
     return float(m) * n * elem
 
 
+ELEM = {"float32": 4, "float64": 8, "bfloat16": 2}   # bytes per entry of A
+
+
 # Algorithmic work of one launch of each kernel class at the bench workload:
 # HBM bytes for the passes over A (one read of the m x n fp32 matrix),
 # FP64-equivalent flops for the pivoted QR and the triangular solves.
@@ -100,7 +103,7 @@ def class_roofline(cls, trace, cfg, peaks, peak_kind, sm_mhz):
     base = {"kernel_class": cls, "avg_launch_ms": avg_ms, "launches": launches,
             "traffic": traffic}
     if cls in ("a_omega", "a_w", "at_w"):
-        achieved = a_pass_bytes(m, n) / (avg_ms * 1e-3) / 1e9
+        achieved = a_pass_bytes(m, n, ELEM[cfg["dtype"]]) / (avg_ms * 1e-3) / 1e9
         base.update({"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "peak_source": peak_kind + " STREAM-style copy",
@@ -141,7 +144,7 @@ def sketch_roofline(trace, cfg, peaks, peak_kind):
     nl = sum(trace[c][1] for c in cls)
     if nl <= 0 or ms <= 0:
         return None
-    achieved = nl * a_pass_bytes(m, n) / (ms * 1e-3) / 1e9
+    achieved = nl * a_pass_bytes(m, n, ELEM[cfg["dtype"]]) / (ms * 1e-3) / 1e9
     t = load_traffic()
     return {"kernels": "tc_omega2_kernel (A Omega), tc_unit_kernel (A W, A^T W)",
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -496,7 +499,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     m, n, k, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["q"]
-    tdt = {"float32": torch.float32, "float64": torch.float64}[cfg["dtype"]]
+    tdt = {"float32": torch.float32, "float64": torch.float64,
+           "bfloat16": torch.bfloat16}[cfg["dtype"]]
     A = make_matrix_torch(m, n, spectrum(cfg["spectrum"], cfg["r"]), noise=cfg["noise"],
                           seed=cfg["a_seed"] + rank, dtype=cfg["dtype"], device=dev)
     torch.cuda.synchronize()
@@ -594,12 +598,18 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": {"float32": "f32", "float64": "f64", "bfloat16": "bf16 A, f32"}[cfg["dtype"]],
+            "data": "synthetic",
             "config": {"workload": cfg["name"], "m": m, "n": n, "k": k, "p": p, "q": q,
                        "spectrum": "sigma_j = 1/j, r = %d, noise %g" % (cfg["r"], cfg["noise"]),
-                       "precision": "fp32 storage; split-bf16 tcgen05 products, fp32 accumulate",
+                       "precision": {"float32": "fp32 storage; split-bf16 tcgen05 products, "
+                                                 "fp32 accumulate",
+                                     "bfloat16": "bf16 storage; exact bf16 tcgen05 products, "
+                                                 "fp32 accumulate",
+                                     "float64": "fp64 storage; FP64 SIMT"}[cfg["dtype"]],
                        "step": "QB sketch + SVD + ID + CUR from one sketch",
-                       "l2": "A (%.1f GB) larger than L2 on every pass" % (4.0 * m * n / 1e9),
+                       "l2": "A (%.1f GB) larger than L2 on every pass"
+                             % (ELEM[cfg["dtype"]] * m * n / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "qb_sketch": {"a_pass_ms_per_step": pass_ms,
                           "a_pass_tflops": qb_flops / (pass_ms * 1e-3) / 1e12 if pass_ms else None,
