@@ -72,7 +72,7 @@ def test_calls_reject_invalid_arguments_without_launching(lib):
     st = lib.rsvd_qb(100, 50, 5, 5, 1, 1, rs.F64, fake, 49, fake, 10, fake, 10, fake, 1 << 20,
                      None, None, None)
     assert st == 1
-    # bf16 storage is not part of this build's paths
+    # bf16 A whose rows are not 16-byte aligned (lda % 8 != 0): not TMA-addressable
     st = lib.rsvd_qb(100, 50, 5, 5, 1, 1, rs.BF16, fake, 50, fake, 10, fake, 10, fake, 1 << 20,
                      None, None, None)
     assert st == 4
@@ -86,3 +86,76 @@ def test_calls_reject_invalid_arguments_without_launching(lib):
     st = lib.rsvd_qb(100, 50, 5, 5, 1, 1, rs.F64, fake, 50, fake, 10, fake, 10, fake, 1 << 20,
                      None, None, ctypes.byref(o))
     assert st == 1
+
+
+def test_bf16_and_mixed_workspace_queries(lib):
+    import paper_1502_05366_gb300 as rs
+    assert lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.BF16, None) > 0
+    simt = rs.make_opts(precision=rs.PREC_SIMT)
+    assert lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.BF16, ctypes.byref(simt)) == 0
+    mixed = rs.make_opts(precision=rs.PREC_MIXED)
+    assert lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.F32, ctypes.byref(mixed)) > 0
+    bad = rs.make_opts()
+    bad.precision = 3
+    assert lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.F32, ctypes.byref(bad)) == 0
+    # widths above 256 (column chunks) up to 1024 on the tensor-core path
+    assert lib.rsvd_svd_workspace_size(100000, 50000, 500, 50, 2, rs.BF16, None) > 0
+    assert lib.rsvd_svd_workspace_size(100000, 50000, 1000, 50, 2, rs.BF16, None) == 0
+
+
+def _items(rs, sizes):
+    items = (rs.BatchItem * len(sizes))()
+    a = u = v = s = 0
+    for i, (m, n, k) in enumerate(sizes):
+        items[i].m, items[i].n, items[i].k = m, n, k
+        items[i].a_off, items[i].u_off, items[i].v_off, items[i].s_off = a, u, v, s
+        a, u, v, s = a + m * n, u + m * k, v + n * k, s + k
+    return items
+
+
+def test_batched_workspace_and_validation(lib):
+    import paper_1502_05366_gb300 as rs
+    good = _items(rs, [(300, 150, 8), (1000, 700, 16), (96, 80, 64)])
+    w = lib.rsvd_svd_batched_workspace_size(3, good, 8, 1)
+    assert w > 0
+    # more problems or a wider sketch need more workspace
+    assert lib.rsvd_svd_batched_workspace_size(2, good, 8, 1) < w
+    assert lib.rsvd_svd_batched_workspace_size(3, good, 16, 1) > w
+    assert lib.rsvd_svd_batched_workspace_size(3, _items(rs, [(300, 150, 121)] * 3), 8, 1) == 0
+    assert lib.rsvd_svd_batched_workspace_size(1, _items(rs, [(100, 50, 45)]), 8, 1) == 0
+    assert lib.rsvd_svd_batched_workspace_size(1, _items(rs, [(100, 50, 0)]), 8, 1) == 0
+    assert lib.rsvd_svd_batched_workspace_size(0, good, 8, 1) == 0
+    assert lib.rsvd_svd_batched_workspace_size(3, good, 8, -1) == 0
+
+
+def test_batched_call_rejects_without_launching(lib):
+    import paper_1502_05366_gb300 as rs
+    vp = ctypes.c_void_p
+    fake = vp(0x100000)
+    good = _items(rs, [(300, 150, 8), (1000, 700, 16)])
+    w = lib.rsvd_svd_batched_workspace_size(2, good, 8, 1)
+    # null A
+    assert lib.rsvd_svd_batched(2, good, 8, 1, 5, vp(0), fake, fake, fake, fake, w, None,
+                                None) == 1
+    # work not 256-byte aligned
+    assert lib.rsvd_svd_batched(2, good, 8, 1, 5, fake, fake, fake, fake, vp(0x100010), w,
+                                None, None) == 1
+    # workspace too small
+    assert lib.rsvd_svd_batched(2, good, 8, 1, 5, fake, fake, fake, fake, fake, w - 4096,
+                                None, None) == 2
+    # a bad item
+    bad = _items(rs, [(300, 150, 8), (100, 50, 45)])
+    assert lib.rsvd_svd_batched(2, bad, 8, 1, 5, fake, fake, fake, fake, fake, w, None,
+                                None) == 1
+
+
+def test_batched_workload_sizes():
+    from synth import BATCH_CONFIGS, batch_sizes
+    c = BATCH_CONFIGS["c4_f32_batched512"]
+    ms, ns, ks = batch_sizes("c4_f32_batched512")
+    assert len(ms) == len(ns) == len(ks) == 512
+    assert batch_sizes("c4_f32_batched512") == (ms, ns, ks)      # seeded
+    for m, n, k in zip(ms, ns, ks):
+        assert c["m_range"][0] <= m <= c["m_range"][1]
+        assert k in c["ks"]
+        assert k + c["p"] <= n <= m
