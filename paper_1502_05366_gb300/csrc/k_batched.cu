@@ -167,6 +167,24 @@ cudaError_t launch_bgemm(const BGemm* gemms, const int2* tasks, int ntasks, int 
   return cudaGetLastError();
 }
 
+// Split-K partials of one problem summed in slice order (the Grams of tall
+// samples run as one GEMM task per 512-row slice).
+__global__ void __launch_bounds__(256) sum_batched_kernel(const BSum* __restrict__ tasks) {
+  const BSum tk = tasks[blockIdx.x];
+  for (int e = threadIdx.x; e < tk.count; e += blockDim.x) {
+    float acc = 0.f;
+    for (int sl = 0; sl < tk.nslice; ++sl) acc += tk.part[(int64_t)sl * tk.count + e];
+    tk.out[e] = acc;
+  }
+}
+
+cudaError_t launch_sum_batched(const BSum* tasks, int batch, cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  sum_batched_kernel<<<batch, 256, 0, s>>>(tasks);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // One CTA per problem: for each column j < k, the row of the largest |V(i, j)|
 // (lowest index on ties) decides the sign; U(:, j) and V(:, j) take it, and
 // S[j] = Sh[j].

@@ -252,6 +252,14 @@ struct BChol {
 };
 cudaError_t launch_chol_batched(const BChol* tasks, int batch, int lmax, int* d_info,
                                 cudaStream_t s);
+// out[e] = sum_{s < nslice} part[s * count + e] (fixed order), one CTA per problem
+struct BSum {
+  const float* part;
+  float* out;
+  int nslice;
+  int count;
+};
+cudaError_t launch_sum_batched(const BSum* tasks, int batch, cudaStream_t s);
 // Racc <- R Racc (upper triangular l x l) per problem, through tmp
 struct BTrmm {
   const float* R;

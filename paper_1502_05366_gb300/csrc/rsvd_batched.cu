@@ -30,11 +30,17 @@ struct Carve {   // workspace carving; dry when base is null
 };
 
 struct ProbBufs {
-  float *Y, *Yt, *Z, *Zt, *G, *R, *Rinv, *Racc, *tmp, *Uj, *Uh, *Vh;
+  float *Y, *Yt, *Z, *Zt, *G, *Gpart, *R, *Rinv, *Racc, *tmp, *Uj, *Uh, *Vh;
   double* Sh;
 };
 
-enum StageKind { ST_GEMM, ST_CHOL, ST_TRMM, ST_SVD, ST_SIGN };
+// A Gram of a tall sample runs as one GEMM per slice of this many rows (split
+// K), so that a stage has several tasks per problem; the slices are summed in
+// order.
+constexpr int GRAM_SLICE = 512;
+inline int gram_slices(int64_t rows) { return (int)((rows + GRAM_SLICE - 1) / GRAM_SLICE); }
+
+enum StageKind { ST_GEMM, ST_CHOL, ST_TRMM, ST_SVD, ST_SIGN, ST_SUM };
 struct Stage {
   int kind;
   int first, count;   // into the table of the kind (gemm: tasks; others: problems)
@@ -48,6 +54,7 @@ struct Plan {
   std::vector<BTrmm> trmms;
   std::vector<BSvd> svds;
   std::vector<BSign> signs;
+  std::vector<BSum> sums;
   std::vector<Stage> stages;
   int lmax = 0;
 };
@@ -105,6 +112,7 @@ void add_orth(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<BGemm> gram, apply;
     Stage sc{ST_CHOL, (int)P.chols.size(), batch, 0};
+    Stage ss{ST_SUM, (int)P.sums.size(), batch, 0};
     for (int i = 0; i < batch; ++i) {
       const int l = it[i].k + p;
       const int64_t rows = on_z ? it[i].n : it[i].m;
@@ -112,7 +120,21 @@ void add_orth(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<
       float* Xt = on_z ? b[i].Zt : b[i].Yt;
       const float* src = pass == 0 ? X : Xt;
       float* dst = pass == 0 ? Xt : X;
-      gram.push_back(gemm_of(src, l, 1, src, l, b[i].G, l, l, l, rows, l, i));
+      // G = sum over row slices of X_s^T X_s (split K)
+      const int ns = gram_slices(rows);
+      for (int sl = 0; sl < ns; ++sl) {
+        const int64_t r0 = (int64_t)sl * GRAM_SLICE;
+        const int64_t rs = std::min<int64_t>(GRAM_SLICE, rows - r0);
+        gram.push_back(gemm_of(src ? src + r0 * l : nullptr, l, 1, src ? src + r0 * l : nullptr, l,
+                               b[i].Gpart ? b[i].Gpart + (int64_t)sl * l * l : nullptr, l, l, l,
+                               rs, l, i));
+      }
+      BSum su;
+      su.part = b[i].Gpart;
+      su.out = b[i].G;
+      su.nslice = ns;
+      su.count = l * l;
+      P.sums.push_back(su);
       BChol c;
       c.G = b[i].G;
       c.R = (want_R && pass == 0) ? b[i].Racc : b[i].R;
@@ -122,6 +144,7 @@ void add_orth(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<
       apply.push_back(gemm_of(src, l, 0, b[i].Rinv, l, dst, l, rows, l, l, l, i));
     }
     add_gemm_stage(P, gram);
+    P.stages.push_back(ss);
     P.stages.push_back(sc);
     add_gemm_stage(P, apply);
   }
@@ -154,6 +177,7 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
     b[i].Z = cv.take<float>((size_t)n * l);
     b[i].Zt = cv.take<float>((size_t)n * l);
     b[i].G = cv.take<float>((size_t)l * l);
+    b[i].Gpart = cv.take<float>((size_t)gram_slices(std::max(m, n)) * l * l);
     b[i].R = cv.take<float>((size_t)l * l);
     b[i].Rinv = cv.take<float>((size_t)l * l);
     b[i].Racc = cv.take<float>((size_t)l * l);
@@ -245,6 +269,7 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
   cv.take<BTrmm>(P.trmms.size());
   cv.take<BSvd>(P.svds.size());
   cv.take<BSign>(P.signs.size());
+  cv.take<BSum>(P.sums.size());
   return cv.off + 256;
 }
 
@@ -288,6 +313,7 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
   BTrmm* dm = cv.take<BTrmm>(P.trmms.size());
   BSvd* dv = cv.take<BSvd>(P.svds.size());
   BSign* dsg = cv.take<BSign>(P.signs.size());
+  BSum* dsu = cv.take<BSum>(P.sums.size());
 #define UPLOAD(dst, vec)                                                                 \
   if (!vec.empty() && cudaMemcpyAsync(dst, vec.data(), vec.size() * sizeof(vec[0]),      \
                                       cudaMemcpyHostToDevice, s) != cudaSuccess)         \
@@ -298,6 +324,7 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
   UPLOAD(dm, P.trmms);
   UPLOAD(dv, P.svds);
   UPLOAD(dsg, P.signs);
+  UPLOAD(dsu, P.sums);
 #undef UPLOAD
   for (const Stage& st : P.stages) {
     cudaError_t e = cudaSuccess;
@@ -309,6 +336,7 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
         e = launch_small_svd_batched(dv + st.first, st.count, P.lmax, 30, d_info, s);
         break;
       case ST_SIGN: e = launch_sign_batched(dsg + st.first, st.count, s); break;
+      case ST_SUM: e = launch_sum_batched(dsu + st.first, st.count, s); break;
       default: break;
     }
     if (e != cudaSuccess) return RSVD_ERR_CUDA;
