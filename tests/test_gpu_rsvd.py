@@ -1,6 +1,7 @@
 """End-to-end GPU parity of rsvd_qb / rsvd_svd / rsvd_id / rsvd_cur against the oracle.
 
-Bars (from the workload statement, readings in the design doc):
+Bars (from the workload statement; "relative 1e-5" is per index i <= k, "within
+1 %" is on ||A - U S V^T||_F / ||A||_F in FP64):
 * top-k singular values: relative 1e-5 (FP32 paths), 1e-10 (FP64);
 * reconstruction error ||A - U S V^T||_F / ||A||_F within 1 % of the oracle's;
 * ID / CUR indices identical at every step before the first one whose pivot

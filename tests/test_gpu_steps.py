@@ -1,6 +1,6 @@
 """GPU parity of each step of the path against the FP64 oracle (through the C ABI).
 
-Tolerances (derived in the design doc): the FP32 tensor-core path splits each fp32
+Tolerances, from the arithmetic: the FP32 tensor-core path splits each fp32
 operand into two bf16 terms (16 significant bits, unit roundoff 2^-16 per
 term product) with fp32 accumulation, so a product entry carries a relative
 error of order 2^-16 / sqrt(terms) ~ 1e-5 in the worst case and ~1e-6 in the
