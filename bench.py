@@ -249,12 +249,20 @@ def max_over_ranks(x, world, device):
     return float(t.item())
 
 
+def whole_job(flops_per_step, ms_local, world, device):
+    """(slowest rank's ms per step, whole-job TFLOP/s).  Every rank runs its
+    own replica of the step, so the job processes world x flops_per_step per
+    step in the time of its slowest rank."""
+    ms = max_over_ranks(ms_local, world, device)
+    return ms, world * flops_per_step / (ms * 1e-3) / 1e12
+
+
 def _oracle_sample_setup(cfg, frac_rows=25, frac_cols=5):
     """A bounded sample of the same recipe (m/frac_rows x n/frac_cols) for the oracle."""
     from synth import make_matrix_np, spectrum
     m = max(cfg["m"] // frac_rows, cfg["k"] + cfg["p"] + 8)
     n = max(cfg["n"] // frac_cols, cfg["k"] + cfg["p"] + 8)
-    r = min(cfg["r"], n)
+    r = min(cfg["r"], m, n)
     A = make_matrix_np(m, n, spectrum(cfg["spectrum"], r), noise=cfg["noise"],
                        seed=cfg["a_seed"], dtype=cfg["dtype"]).astype(np.float64)
     try:
@@ -285,7 +293,7 @@ def cpu_oracle_sample(cfg, reps=3):
             "sample": desc + ", %.2f s per step (median of %d)" % (dt, reps)}
 
 
-def run_reference(args, cfg, world, rank):
+def run_reference(args, cfg, rank):
     """--impl reference: the oracle on the host cores (rank 0 only), W untimed
     warm-up steps then K timed steps of the bounded sample."""
     if rank != 0:
@@ -488,9 +496,11 @@ def main():
     from synth import config as get_config
     cfg = get_config(args.config)
     cfg["name"] = args.config
-    world, rank, local = dist_setup()
     if args.impl == "reference":
-        return run_reference(args, cfg, world, rank)
+        # host cores only, no exchange between ranks: rank 0 runs, the others
+        # exit without work (and without joining a process group)
+        return run_reference(args, cfg, int(os.environ.get("RANK", "0")))
+    world, rank, local = dist_setup()
 
     import torch
     import paper_1502_05366_gb300 as rs
@@ -535,10 +545,8 @@ def main():
     trace = rs.trace_read()
     rs.trace_enable(False)
     rs.check_info(plan.info, "timed steps")
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms = max_over_ranks(ms, world, dev)
     flops = step_flops(m, n, k, p, q)
-    value = world * flops / (ms * 1e-3) / 1e12
+    ms, value = whole_job(flops, ev0.elapsed_time(ev1) / args.steps, world, dev)
 
     # ---------------- roofline of the dominant kernel class ----------------
     peaks, peak_kind = load_peaks()
@@ -576,8 +584,8 @@ def main():
     torch.cuda.synchronize()
     rs.check_info(plan.info, "end-to-end steps")
     steps_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.e2e_steps)]
-    e2e_ms = max_over_ranks(float(np.median(steps_ms)), world, dev)
-    e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+    e2e_ms, e2e_value = whole_job(flops, float(np.median(steps_ms)), world, dev)
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
            "ms_steps": steps_ms, "statistic": "median of the steps"}
 
