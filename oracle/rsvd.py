@@ -105,6 +105,45 @@ def rsvd(A, k, p, q, seed, rounding="f64", s=1, Omega=None):
 
 
 # ---------------------------------------------------------------------------
+# Blocked adaptive QB to a tolerance (Alg. 7, "QB2"; Sec. 3.3)
+# ---------------------------------------------------------------------------
+def qb_blocked(A, b, M, q, eps, seed, rounding="f64", relative=False, s=1):
+    """Alg. 7: Q and B built block by block from the updated residual of A.
+
+    Block t (t = 0, 1, ...) draws its n x b Omega_t from the stream keyed by
+    seed + t (the paper's randn(n, b) per block).  Its Q_t comes from the range
+    finder with q power iterations applied to the CURRENT residual A, is
+    re-projected against the earlier blocks and orthonormalised again; then
+    B_t = Q_t^* A and A <- A - Q_t B_t.  The loop ends after the first block
+    whose residual has ||A||_F < tol (tol = eps, or eps * ||A_in||_F when
+    relative), or after M blocks.  The norm is the Frobenius norm (the paper
+    writes ||A|| without naming one).
+
+    Returns Q (m x b i), Bt = B^* (n x b i) and the residual norms
+    [||A_in||_F, ||A^(1)||_F, ..., ||A^(i)||_F].
+    """
+    A = np.array(A, dtype=np.float64)               # the algorithm overwrites A
+    n = A.shape[1]
+    resid = [float(np.linalg.norm(A))]
+    tol = eps * resid[0] if relative else eps
+    Qs, Bts = [], []
+    for t in range(M):
+        Om = philox.omega(n, b, (seed + t) % (1 << 64), rounding)   # Omega_t = randn(n, b)
+        Qt = range_finder(A, b, q, seed, rounding, s, Omega=Om)      # orth(A Omega_t), power scheme
+        if Qs:
+            Qbar = np.hstack(Qs)
+            Qt = orth(Qt - Qbar @ (Qbar.T @ Qt))    # Q_t - sum_j Q_j Q_j^* Q_t, re-orthonormalised
+        Bt = A.T @ Qt                               # B_t = Q_t^* A (stored transposed)
+        A = A - Qt @ Bt.T                           # A <- A - Q_t B_t
+        Qs.append(Qt)
+        Bts.append(Bt)
+        resid.append(float(np.linalg.norm(A)))
+        if resid[-1] < tol:
+            break
+    return np.hstack(Qs), np.hstack(Bts), resid
+
+
+# ---------------------------------------------------------------------------
 # Column-pivoted QR, k steps (Sec. 2.3; Alg. 1 first step)
 # ---------------------------------------------------------------------------
 def cpqr(M, ksteps):
