@@ -24,7 +24,7 @@
  * rsvd_svd_id_cur_host) and by rsvd_sample / rsvd_apply, on the tensor-core
  * path only: A 16-byte aligned with lda % 8 == 0, precision RSVD_PREC_TC or
  * RSVD_PREC_MIXED,
- * l + padding <= 256; otherwise RSVD_ERR_UNSUPPORTED.  The bf16 values of A are
+ * l rounded up to 16 <= 1024; otherwise RSVD_ERR_UNSUPPORTED.  The bf16 values of A are
  * exact tensor-core operands: each pass over A issues one product per term of
  * its right-hand operand and reads 2 bytes per entry.  All other arithmetic
  * (Gram, CholeskyQR, small SVD, pivoted QR, solves) is the FP32 path's.
@@ -210,6 +210,50 @@ rsvd_status rsvd_svd_id_cur_host(int64_t m, int64_t n, int k, int p, int q, uint
                                  int32_t* Jc, int32_t* Ir, void* Ucur, int64_t lducur,
                                  void* work, size_t work_bytes, int* d_info, void* stream,
                                  const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
+ * rsvd_qb_adaptive - blocked randomized QB to a tolerance (Alg. 7, "QB2";
+ * Sec. 3.3; the rank is not fixed in advance, Sec. 2.6 / Sec. 4 "TOL" mode).
+ *
+ * Block t = 0, 1, ... of b columns:
+ *   Omega_t (n x b) from the Philox stream keyed by seed + t (counters as for
+ *     Omega above);
+ *   Q_t = orth of the range finder with q power iterations (and the s of
+ *     opts) applied to the CURRENT A;
+ *   Q_t <- orth(Q_t - Qbar Qbar^* Q_t), Qbar = [Q_0 .. Q_{t-1}];
+ *   B_t = Q_t^* A, stored as Bt_t = A^* Q_t (n x b);
+ *   A <- A - Q_t B_t, then resid[t+1] = ||A||_F.
+ * The loop stops after the first block with resid[t+1] < tol, tol = eps
+ * (relative == 0) or eps * ||A_in||_F (relative != 0), or after M blocks, or
+ * when a device failure was recorded in *d_info.  The paper's ||A|| is read as
+ * the Frobenius norm.
+ *
+ * dtype: RSVD_F32 (tensor-core or SIMT path as for rsvd_qb; RSVD_PREC_MIXED
+ *        applies to the power scheme) or RSVD_F64; RSVD_BF16 gives
+ *        RSVD_ERR_UNSUPPORTED (A is updated in its own storage type).
+ * A:     m x n (lda >= n), device, READ AND OVERWRITTEN: on return it holds the
+ *        residual A_in - Q B of the blocks computed.  Pass a copy to keep A.
+ * Q:     m x (b M) capacity (ldq >= b M); columns [0, *rank) receive Qbar,
+ *        orthonormal.  Bt: n x (b M) capacity (ldbt >= b M); columns
+ *        [0, *rank) receive B^* = A_in^* Qbar.  Other columns are not written.
+ * resid: device double[M + 1]: resid[0] = ||A_in||_F, resid[t] = ||A||_F after
+ *        block t; entries past *rank / b are not written.
+ * rank:  HOST int, set to b times the number of blocks computed.
+ * Sizes: 1 <= b <= 1024, M >= 1, b M <= min(m, n), 0 <= q <= 64, eps >= 0.
+ * Errors: as the other calls (RSVD_ERR_INVALID_ARG, RSVD_ERR_WORKSPACE with
+ * nothing launched); device failures in *d_info.
+ * Unlike every other call, this one SYNCHRONISES the host with `stream` once
+ * per block (and once more for a relative tolerance): the stopping test reads
+ * the residual norm on the host, so the call cannot be captured in a CUDA
+ * graph.
+ * ------------------------------------------------------------------------- */
+size_t rsvd_qb_adaptive_workspace_size(int64_t m, int64_t n, int b, int M, int q, int dtype,
+                                       const rsvd_opts* opts);
+rsvd_status rsvd_qb_adaptive(int64_t m, int64_t n, int b, int M, int q, double eps,
+                             int relative, uint64_t seed, int dtype, void* A, int64_t lda,
+                             void* Q, int64_t ldq, void* Bt, int64_t ldbt, double* resid,
+                             int* rank, void* work, size_t work_bytes, int* d_info,
+                             void* stream, const rsvd_opts* opts);
 
 /* =========================================================================
  * Step-level entry points (one per step of the path; same conventions).

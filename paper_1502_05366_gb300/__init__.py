@@ -109,6 +109,11 @@ _SIGS = {
                                   _vp, _vp, _vp, _vp, _c_size, _vp, _vp]),
     "rsvd_cpqr_id_f32": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
                                   _vp, _c_size, _vp, _vp]),
+    "rsvd_qb_adaptive_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int,
+                                                  _OPTP]),
+    "rsvd_qb_adaptive": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, ctypes.c_double, _c_int,
+                                  _c_u64, _c_int, _vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _vp,
+                                  ctypes.POINTER(_c_int), _vp, _c_size, _vp, _vp, _OPTP]),
 }
 
 
@@ -249,6 +254,41 @@ def qb(A, k, p, q, seed, opts=None, check=True):
     if check:
         check_info(info, "rsvd_qb")
     return Q, Bt
+
+
+def qb_adaptive(A, b, M, q, eps, seed, relative=True, opts=None, overwrite=False, check=True):
+    """Blocked adaptive QB to a tolerance (Alg. 7): (Q, Bt, resid).
+
+    Q (m x r) orthonormal and Bt = A^T Q (n x r) with r = b times the number of
+    blocks taken; resid = [||A||_F, residual norm after each block].  The loop
+    stops at the first block whose residual is below eps (times ||A||_F when
+    relative) or after M blocks.  The library overwrites its A with the
+    residual: a copy is passed unless overwrite=True.
+    """
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    Aw = A if overwrite else A.clone()
+    cols = b * M
+    Q = torch.empty(m, cols, dtype=A.dtype, device=A.device)
+    Bt = torch.empty(n, cols, dtype=A.dtype, device=A.device)
+    resid = torch.zeros(M + 1, dtype=torch.float64, device=A.device)
+    ws = lib().rsvd_qb_adaptive_workspace_size(m, n, b, M, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_qb_adaptive_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    rank = ctypes.c_int(0)
+    st = lib().rsvd_qb_adaptive(m, n, b, M, q, float(eps), 1 if relative else 0, seed, dt,
+                                _ptr(Aw), Aw.stride(0), _ptr(Q), cols, _ptr(Bt), cols,
+                                _ptr(resid), ctypes.byref(rank), _ptr(W), W.numel(), _ptr(info),
+                                _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_qb_adaptive")
+    if check:
+        check_info(info, "rsvd_qb_adaptive")
+    r = rank.value
+    return Q[:, :r], Bt[:, :r], resid[:r // b + 1]
 
 
 def svd(A, k, p, q, seed, opts=None, check=True):

@@ -292,4 +292,18 @@ struct BSign {
 };
 cudaError_t launch_sign_batched(const BSign* tasks, int batch, cudaStream_t s);
 
+// ----- blocked adaptive QB (k_adaptive.cu) --------------------------------
+// X (rows x cols, ld ldx) <- X - Q Bt^T with Q rows x K (ld ldq) and Bt cols x K
+// (ld ldb); K = 0 leaves X unwritten.  With sumsq set, sumsq[t] (t <
+// rank_update_tiles(rows, cols)) receives the sum of squares of the updated
+// entries of tile t.
+int64_t rank_update_tiles(int64_t rows, int64_t cols);
+template <typename T>
+cudaError_t launch_rank_update(int64_t rows, int64_t cols, T* X, int64_t ldx, const T* Q,
+                               int64_t ldq, const T* Bt, int64_t ldb, int K, double* sumsq,
+                               cudaStream_t s);
+// *out = sqrt(sum_t parts[t]) in a fixed order; non-finite -> RSVD_ERR_NUMERIC.
+cudaError_t launch_sumsq_finish(int64_t nparts, const double* parts, double* out, int* d_info,
+                                cudaStream_t s);
+
 }  // namespace rsvd

@@ -341,10 +341,11 @@ struct Engine {
     return b;
   }
 
-  // On exit: b.Y holds Q (m x L, padded), b.Z holds Bt (n x L, padded); for
-  // the tensor-core path b.zs holds the split of Bt^T.
-  rsvd_status qb(QBBufs& b, int64_t m, int64_t n, int l, int q, uint64_t seed, const T* A,
-                 int64_t lda) {
+  // Range finder up to its last product (Alg. 5 first part): on exit b.Y holds
+  // Y = A Z (or A Omega when q = 0), not yet orthonormalised, with its split in
+  // b.ys on the tensor-core path.
+  rsvd_status power(QBBufs& b, int64_t m, int64_t n, int l, int q, uint64_t seed, const T* A,
+                    int64_t lda) {
     const int L = padL(l);
     rsvd_status st;
     if (!tc) LK(launch_fill<T>(m, L, b.Y, L, T(0), c.stream));
@@ -398,6 +399,16 @@ struct Engine {
                   &b.ys, b.part, nullptr, c.abf != 0);
       if (st != RSVD_OK) return st;
     }
+    return RSVD_OK;
+  }
+
+  // On exit: b.Y holds Q (m x L, padded), b.Z holds Bt (n x L, padded); for
+  // the tensor-core path b.zs holds the split of Bt^T.
+  rsvd_status qb(QBBufs& b, int64_t m, int64_t n, int l, int q, uint64_t seed, const T* A,
+                 int64_t lda) {
+    const int L = padL(l);
+    rsvd_status st = power(b, m, n, l, q, seed, A, lda);
+    if (st != RSVD_OK) return st;
     // Q = orth(Y)
     st = orth(m, l, L, b.Y, b.Ytmp, &b.ys, b.ob, b.part, b.slabs, false);
     if (st != RSVD_OK) return st;
@@ -406,6 +417,49 @@ struct Engine {
     st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr, false,
                 c.abf != 0);
     return st;
+  }
+
+  // ---------------- one block of the adaptive QB (Alg. 7) ----------------
+  // Q_t from the range finder on the current residual A (seed of this block),
+  // re-projected against the done = b t columns already in Qo and
+  // re-orthonormalised; Bt_t = A^* Q_t; both appended to the outputs at column
+  // `done`; then A <- A - Q_t Bt_t^T with the squared norms of the updated tiles
+  // in sq.  Ct (b x done) and cslabs are the re-projection's scratch.
+  rsvd_status qb2_block(QBBufs& b, int64_t m, int64_t n, int bs, int q, uint64_t seed, T* A,
+                        int64_t lda, T* Qo, int64_t ldq, T* Bto, int64_t ldbt, int64_t done,
+                        T* Ct, T* cslabs, double* sq) {
+    const int L = padL(bs);
+    rsvd_status st = power(b, m, n, bs, q, seed, A, lda);
+    if (st != RSVD_OK) return st;
+    st = orth(m, bs, L, b.Y, b.Ytmp, &b.ys, b.ob, b.part, b.slabs, false);
+    if (st != RSVD_OK) return st;
+    std::swap(b.Y, b.Ytmp);
+    if (done > 0) {
+      // Ct = Q_t^* Qbar (b x done): split-K partial products summed in a fixed order
+      int ns;
+      int64_t kc;
+      tn_split(bs, done, m, sms, &ns, &kc);
+      LK(launch_gemm_tn_partial<T>(bs, done, m, b.Y, L, Qo, ldq, cslabs, done, ns, kc,
+                                   c.stream));
+      LK(launch_reduce_slabs<T>(bs, done, ns, cslabs, done, Ct, done, c.stream));
+      // Q_t <- Q_t - Qbar Ct^T, then orth again
+      LK(launch_rank_update<T>(m, bs, b.Y, L, Qo, ldq, Ct, done, (int)done, nullptr, c.stream));
+      if (tc)
+        LK(launch_split_transpose(m, bs, L, (const float*)b.Y, L, b.ys.hi, b.ys.lo, b.ys.ld,
+                                  c.stream));
+      st = orth(m, bs, L, b.Y, b.Ytmp, &b.ys, b.ob, b.part, b.slabs, false);
+      if (st != RSVD_OK) return st;
+      std::swap(b.Y, b.Ytmp);
+    }
+    // Bt_t = A^* Q_t (B_t = Q_t^* A)
+    st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr,
+                false);
+    if (st != RSVD_OK) return st;
+    LK(launch_copy2d<T, T>(m, bs, b.Y, L, Qo + done, ldq, c.stream));
+    LK(launch_copy2d<T, T>(n, bs, b.Z, L, Bto + done, ldbt, c.stream));
+    // A <- A - Q_t B_t
+    LK(launch_rank_update<T>(m, n, A, lda, b.Y, L, b.Z, L, bs, sq, c.stream));
+    return RSVD_OK;
   }
 
   // ---------------- small SVD of R-hat and lift (Alg. 5 tail) ----------------
@@ -933,6 +987,85 @@ static rsvd_status dispatch(int64_t m, int64_t n, int k, int p, int q, uint64_t 
   return st;
 }
 
+// ------------------------------------------------------------------------
+// blocked adaptive QB to a tolerance (Alg. 7)
+// ------------------------------------------------------------------------
+// Reads a device value into host memory; the stream is synchronised.
+static bool read_back(Ctx& c, const void* src, void* dst, size_t bytes) {
+  if (!c.run(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c.stream))) return false;
+  return c.run(cudaStreamSynchronize(c.stream));
+}
+
+template <typename T>
+static rsvd_status run_qb_adaptive(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n, int bs,
+                                   int M, int q, double eps, int relative, uint64_t seed, T* A,
+                                   int64_t lda, T* Qo, int64_t ldq, T* Bto, int64_t ldbt,
+                                   double* resid, int* rank) {
+  Engine<T> e(c, o, tc);
+  const int L = padL(bs);
+  auto qbb = e.take_qb(m, n, L);
+  // re-projection scratch: Ct (b x b(M-1)) and the split-K slabs of its product
+  const int64_t cmax = (int64_t)bs * (M - 1);
+  size_t se = 0;
+  for (int t = 1; t < M; ++t) {
+    int ns;
+    int64_t kc;
+    tn_split(bs, (int64_t)bs * t, m, e.sms, &ns, &kc);
+    se = std::max(se, (size_t)ns * bs * bs * t);
+  }
+  T* Ct = cmax > 0 ? c.template take<T>((size_t)bs * cmax) : nullptr;
+  T* cslabs = se ? c.template take<T>(se) : nullptr;
+  const int64_t ntiles = rank_update_tiles(m, n);
+  double* sq = c.template take<double>((size_t)ntiles);
+  if (c.dry) return RSVD_OK;
+  if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
+
+  reset_info(c);
+  *rank = 0;
+  // resid[0] = ||A_in||_F (a read-only pass: K = 0)
+  LK(launch_rank_update<T>(m, n, A, lda, nullptr, 0, nullptr, 0, 0, sq, c.stream));
+  LK(launch_sumsq_finish(ntiles, sq, resid, c.d_info, c.stream));
+  double tol = eps;
+  if (relative) {
+    double a0 = 0.0;
+    if (!read_back(c, resid, &a0, sizeof(double))) return RSVD_ERR_CUDA;
+    tol = eps * a0;
+  }
+  for (int t = 0; t < M; ++t) {
+    const int64_t done = (int64_t)bs * t;
+    rsvd_status st = e.qb2_block(qbb, m, n, bs, q, seed + (uint64_t)t, A, lda, Qo, ldq, Bto,
+                                 ldbt, done, Ct, cslabs, sq);
+    if (st != RSVD_OK) return st;
+    LK(launch_sumsq_finish(ntiles, sq, resid + t + 1, c.d_info, c.stream));
+    *rank = (int)(done + bs);
+    // the stopping test of Alg. 7 needs the residual norm on the host
+    double r = 0.0;
+    int info = 0;
+    if (!read_back(c, resid + t + 1, &r, sizeof(double))) return RSVD_ERR_CUDA;
+    if (c.d_info && !read_back(c, c.d_info, &info, sizeof(int))) return RSVD_ERR_CUDA;
+    if (info != 0 || r < tol) break;
+  }
+  return RSVD_OK;
+}
+
+static bool qb_adaptive_args_ok(int64_t m, int64_t n, int bs, int M, int q, int dtype) {
+  if (dtype != RSVD_F32 && dtype != RSVD_F64) return false;
+  if (m < 1 || n < 1 || m > 0x7fffffffLL || n > 0x7fffffffLL) return false;
+  if (bs < 1 || bs > 1024 || M < 1 || q < 0 || q > 64) return false;
+  const int64_t cols = (int64_t)bs * M;
+  return cols <= m && cols <= n;
+}
+
+template <typename T>
+static size_t size_qb_adaptive(const Opts& o, bool tc, int64_t m, int64_t n, int bs, int M) {
+  Ctx c;
+  c.dry = true;
+  int rank = 0;
+  run_qb_adaptive<T>(c, o, tc, m, n, bs, M, 0, 0.0, 0, 0, nullptr, 0, nullptr, 0, nullptr, 0,
+                     nullptr, &rank);
+  return c.off + 256;
+}
+
 }  // namespace rsvd
 
 using namespace rsvd;
@@ -1053,6 +1186,54 @@ rsvd_status rsvd_svd_id_cur_host(int64_t m, int64_t n, int k, int p, int q, uint
   return dispatch(m, n, k, p, q, seed, dtype, A, lda, want, nullptr, 0, nullptr, 0, U, ldu, S, V,
                   ldv, J, T, ldt, Jc, Ir, Ucur, lducur, work, work_bytes, d_info, stream, opts,
                   A_host);
+}
+
+size_t rsvd_qb_adaptive_workspace_size(int64_t m, int64_t n, int b, int M, int q, int dtype,
+                                       const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o) || !qb_adaptive_args_ok(m, n, b, M, q, dtype)) return 0;
+  if (dtype == RSVD_F64) return size_qb_adaptive<double>(o, false, m, n, b, M);
+  const bool tc = want_tc(dtype, o, b, nullptr, 0);
+  size_t s1 = size_qb_adaptive<float>(o, false, m, n, b, M);
+  size_t s2 = tc ? size_qb_adaptive<float>(o, true, m, n, b, M) : 0;
+  return s1 > s2 ? s1 : s2;
+}
+
+rsvd_status rsvd_qb_adaptive(int64_t m, int64_t n, int b, int M, int q, double eps, int relative,
+                             uint64_t seed, int dtype, void* A, int64_t lda, void* Q, int64_t ldq,
+                             void* Bt, int64_t ldbt, double* resid, int* rank, void* work,
+                             size_t work_bytes, int* d_info, void* stream,
+                             const rsvd_opts* opts) {
+  Opts o;
+  if (!read_opts(opts, &o)) return RSVD_ERR_INVALID_ARG;
+  if (dtype == RSVD_BF16) return RSVD_ERR_UNSUPPORTED;
+  if (!qb_adaptive_args_ok(m, n, b, M, q, dtype)) return RSVD_ERR_INVALID_ARG;
+  if (!(eps >= 0.0) || eps > 1e300) return RSVD_ERR_INVALID_ARG;   // also rejects NaN
+  const int64_t cols = (int64_t)b * M;
+  if (!A || !Q || !Bt || !resid || !rank) return RSVD_ERR_INVALID_ARG;
+  if (lda < n || ldq < cols || ldbt < cols) return RSVD_ERR_INVALID_ARG;
+  if (!work && work_bytes) return RSVD_ERR_INVALID_ARG;
+  if (work && !aligned16(work)) return RSVD_ERR_INVALID_ARG;
+  Ctx c;
+  c.dry = false;
+  c.base = (char*)work;
+  c.cap = work_bytes;
+  c.stream = (cudaStream_t)stream;
+  c.d_info = d_info;
+  rsvd_status st;
+  if (dtype == RSVD_F64) {
+    if (size_qb_adaptive<double>(o, false, m, n, b, M) - 256 > work_bytes)
+      return RSVD_ERR_WORKSPACE;
+    st = run_qb_adaptive<double>(c, o, false, m, n, b, M, q, eps, relative, seed, (double*)A, lda,
+                                 (double*)Q, ldq, (double*)Bt, ldbt, resid, rank);
+  } else {
+    const bool tc = want_tc(dtype, o, b, A, lda);
+    if (size_qb_adaptive<float>(o, tc, m, n, b, M) - 256 > work_bytes) return RSVD_ERR_WORKSPACE;
+    st = run_qb_adaptive<float>(c, o, tc, m, n, b, M, q, eps, relative, seed, (float*)A, lda,
+                                (float*)Q, ldq, (float*)Bt, ldbt, resid, rank);
+  }
+  if (st == RSVD_OK && c.err != cudaSuccess) st = RSVD_ERR_CUDA;
+  return st;
 }
 
 }  // extern "C"

@@ -159,3 +159,44 @@ def test_batched_workload_sizes():
         assert c["m_range"][0] <= m <= c["m_range"][1]
         assert k in c["ks"]
         assert k + c["p"] <= n <= m
+
+
+def test_adaptive_qb_workspace_and_validation(lib):
+    import paper_1502_05366_gb300 as rs
+    ws = lib.rsvd_qb_adaptive_workspace_size
+    assert ws(3000, 2000, 32, 8, 1, rs.F32, None) > 0
+    assert ws(3000, 2000, 32, 8, 1, rs.F64, None) > 0
+    assert ws(3000, 2000, 32, 8, 1, rs.BF16, None) == 0          # A is updated in place
+    assert ws(300, 200, 64, 4, 1, rs.F32, None) == 0             # b M > min(m, n)
+    assert ws(300, 200, 0, 4, 1, rs.F32, None) == 0              # b = 0
+    assert ws(300, 200, 16, 0, 1, rs.F32, None) == 0             # M = 0
+    assert ws(3000, 2000, 1040, 1, 1, rs.F32, None) == 0         # b > 1024
+    # more blocks need more re-projection scratch
+    assert ws(3000, 2000, 32, 16, 1, rs.F32, None) > ws(3000, 2000, 32, 2, 1, rs.F32, None)
+    rank = ctypes.c_int(-1)
+    fake = ctypes.c_void_p(256)        # never dereferenced: every call below fails its checks
+    call = lib.rsvd_qb_adaptive
+
+    def st(**kw):
+        a = dict(m=300, n=200, b=16, M=4, q=1, eps=1e-3, rel=1, dt=rs.F32, A=fake, lda=200,
+                 Q=fake, ldq=64, Bt=fake, ldbt=64, resid=fake, rank=ctypes.byref(rank),
+                 work=None, wb=0)
+        a.update(kw)
+        return call(a["m"], a["n"], a["b"], a["M"], a["q"], a["eps"], a["rel"], 1, a["dt"],
+                    a["A"], a["lda"], a["Q"], a["ldq"], a["Bt"], a["ldbt"], a["resid"],
+                    a["rank"], a["work"], a["wb"], None, None, None)
+
+    assert st(eps=-1.0) == 1
+    assert st(eps=float("nan")) == 1
+    assert st(eps=float("inf")) == 1
+    assert st(A=None) == 1
+    assert st(resid=None) == 1
+    assert st(rank=None) == 1
+    assert st(lda=199) == 1
+    assert st(ldq=63) == 1
+    assert st(ldbt=63) == 1
+    assert st(b=64) == 1
+    assert st(dt=rs.BF16) == 4
+    assert st(q=65) == 1
+    assert st() == 2                   # no workspace
+    assert rank.value == -1            # nothing ran
