@@ -13,6 +13,9 @@ path without holding the full matrix A on the device:
              float32: the double-float kernel of the FP32 path, float64: FP64
   batched    one rsvd_svd_batched call on the 512-problem workload (uneven FP32
              problems, sigma_j = exp(-j/k)); --batch limits the problem count
+  adaptive   one rsvd_qb_adaptive call (Alg. 7) on a Gaussian m x n A with
+             eps = 0, so exactly --blocks blocks of --l columns with --q power
+             iterations each; A is overwritten (the residual), not copied
 
 Example:  python -m paper_1502_05366_gb300.run_step --step cpqr --r 220 --n 20000 --k 200
 
@@ -52,6 +55,9 @@ def _inputs(args, dev):
         mats = make_batch_torch(ms, ns, ks, 0xA000 + c["index"], device=dev)
         plan = rs.BatchPlan(ms, ns, ks, c["p"], c["q"], dev)
         return plan, plan.pack(mats)
+    if args.step == "adaptive":
+        gd = torch.Generator(device=dev).manual_seed(args.seed)
+        return torch.randn(args.m, args.n, generator=gd, device=dev, dtype=dt), None
     if args.step == "cpqr":
         # rows scaled by 1/i like B = Q^T A of the same spectrum
         M = torch.randn(args.r, args.n, generator=g, dtype=torch.float64)
@@ -76,6 +82,9 @@ def _call(args, X0, X1):
         return rs.cpqr_id(X0, args.k, check=False)
     if s == "batched":
         return X0.run(X1, args.seed)
+    if s == "adaptive":
+        return rs.qb_adaptive(X0, args.l, args.blocks, args.q, 0.0, args.seed, relative=False,
+                              overwrite=True, check=False)
     raise ValueError(s)
 
 
@@ -83,7 +92,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--step", required=True,
                     choices=["sample", "apply_n", "apply_t", "orth", "small_svd", "cpqr",
-                             "batched"])
+                             "batched", "adaptive"])
     ap.add_argument("--m", type=int, default=50000)
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--l", type=int, default=220)
@@ -93,6 +102,8 @@ def main(argv=None):
                     help="element type of A (bfloat16: the passes over A only)")
     ap.add_argument("--seed", type=int, default=0x5EED)
     ap.add_argument("--batch", type=int, default=None, help="problems of --step batched")
+    ap.add_argument("--blocks", type=int, default=4, help="blocks of --step adaptive")
+    ap.add_argument("--q", type=int, default=1, help="power iterations of --step adaptive")
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
     if not torch.cuda.is_available():
