@@ -12,7 +12,8 @@ philox   counter-based Philox4x32-10 stream and the Box-Muller Gaussian test
 rsvd     the algorithms of Voronin & Martinsson (RSVDPACK), step by step in
          FP64: orth (Householder QR), the range finder with power scheme,
          the QB step, Algorithm 5 (RSVD version II), k-step column-pivoted QR,
-         the QB-route randomized ID, the CUR of Algorithm 3 and the blocked
-         adaptive QB to a tolerance of Algorithm 7.
+         the QB-route randomized ID, the CUR of Algorithm 3, the blocked
+         adaptive QB to a tolerance of Algorithm 7, the parallel blocked QB of
+         Algorithm 8 and the randomized ID from the left sketch (Sec. 3.5).
 """
 from . import philox, rsvd  # noqa: F401

@@ -34,6 +34,7 @@ W1 = 0xBB67AE85
 MASK32 = np.uint64(0xFFFFFFFF)
 
 TAG_OMEGA = 0
+TAG_OMEGA_LEFT = 1      # the left test matrix Omega~ of the sketch Omega~ A (Sec. 3.5)
 
 
 def philox4x32_10(ctr, key):

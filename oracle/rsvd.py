@@ -143,6 +143,38 @@ def qb_blocked(A, b, M, q, eps, seed, rounding="f64", relative=False, s=1):
     return np.hstack(Qs), np.hstack(Bts), resid
 
 
+def qb_blocked_parallel(A, b, M, q, seed, rounding="f64"):
+    """Alg. 8: the approximate parallel blocked QB (fixed M blocks, A not updated).
+
+    Every block sketches the ORIGINAL A with its own Omega_t (stream keyed by
+    seed + t, as in qb_blocked) and runs its power scheme with orth between
+    products; the blocks are then orthonormalised, projected one after the
+    other against the blocks already accepted, orthonormalised again and
+    appended; finally B = Q^* A.
+
+    Returns Q (m x b M) and Bt = B^* (n x b M).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[1]
+    Ys = []
+    for t in range(M):                              # first loop: independent blocks
+        Om = philox.omega(n, b, (seed + t) % (1 << 64), rounding)
+        Y = A @ Om                                  # Y_t = A Omega_t
+        for _ in range(q):
+            Qt = orth(Y)
+            Y = A.T @ Qt                            # Y_t = A^* Q_t
+            Qt = orth(Y)
+            Y = A @ Qt                              # Y_t = A Q_t
+        Ys.append(Y)
+    Qs = [orth(Y) for Y in Ys]                      # second loop: Q_t = orth(Y_t)
+    Q = np.zeros((A.shape[0], 0))
+    for Qt in Qs:                                   # third loop: project, orth, append
+        Qt = Qt - Q @ (Q.T @ Qt)
+        Qt = orth(Qt)
+        Q = np.hstack([Q, Qt])
+    return Q, A.T @ Q                               # B = Q^* A
+
+
 # ---------------------------------------------------------------------------
 # Column-pivoted QR, k steps (Sec. 2.3; Alg. 1 first step)
 # ---------------------------------------------------------------------------
@@ -225,6 +257,28 @@ def rid(A, k, p, q, seed, rounding="f64", s=1, Omega=None):
 # ---------------------------------------------------------------------------
 # CUR through the two-sided ID (Sec. 2.5; Alg. 2, Alg. 3; Sec. 3.6)
 # ---------------------------------------------------------------------------
+def rid_left(A, k, p, q, seed, rounding="f64"):
+    """Randomized ID from the left sketch Y = Omega~ A (A^* A)^q (Sec. 3.5, Alg. 6).
+
+    Omega~ is (k + p) x m Gaussian: Omega~^* is the m x l stream of tag
+    TAG_OMEGA_LEFT.  Between products the sample is orthonormalised as in the
+    power scheme of Sec. 3.5: Y <- (A orth(Y^*))^*, then Y <- (A^* orth(Y^*))^*.
+    The ID is that of Y (k steps of CPQR, T = S11^{-1} S12).
+
+    Returns J (n,), T (k x (n-k)), pivot gaps, and Y (l x n).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m = A.shape[0]
+    l = k + p
+    OmT = philox.omega(m, l, seed, rounding, tag=philox.TAG_OMEGA_LEFT)   # Omega~^*
+    Y = (A.T @ OmT).T                               # Y = (A^* Omega~^*)^*, l x n
+    for _ in range(q):
+        Y = (A @ orth(Y.T)).T                       # l x m
+        Y = (A.T @ orth(Y.T)).T                     # l x n
+    J, T, gaps = id_from_matrix(Y, k)
+    return J, T, gaps, Y
+
+
 def cur_from_id(A, J, T, k):
     """Row ID of C = A(:, J[:k]) by k-step CPQR of C^*, then U = V^* R^dagger.
 
