@@ -14,6 +14,7 @@ rsvd     the algorithms of Voronin & Martinsson (RSVDPACK), step by step in
          the QB step, Algorithm 5 (RSVD version II), k-step column-pivoted QR,
          the QB-route randomized ID, the CUR of Algorithm 3, the blocked
          adaptive QB to a tolerance of Algorithm 7, the parallel blocked QB of
-         Algorithm 8 and the randomized ID from the left sketch (Sec. 3.5).
+         Algorithm 8, the randomized ID from the left sketch (Sec. 3.5) and
+         the reverse-mode derivative of Algorithm 5 with Omega fixed.
 """
 from . import philox, rsvd  # noqa: F401

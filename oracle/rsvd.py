@@ -176,6 +176,115 @@ def qb_blocked_parallel(A, b, M, q, seed, rounding="f64"):
 
 
 # ---------------------------------------------------------------------------
+# Reverse-mode derivative of Alg. 5 with Omega fixed (differentiable RSVD)
+# ---------------------------------------------------------------------------
+def qr_pos_vjp(Q, R, gQ, gR):
+    """Cotangent of X for X = Q R (thin QR, diag(R) > 0) given those of Q and R.
+
+    From dX = dQ R + Q dR with Q^* dQ skew and dR upper triangular:
+    g_X = (g_Q + Q sym(M)) R^{-*}, M = g_R R^* - Q^* g_Q, where sym(M) keeps
+    the upper triangle of M and mirrors its strictly upper part below.
+    """
+    M = gR @ R.T - Q.T @ gQ
+    symM = np.triu(M) + np.triu(M, 1).T
+    return sla.solve_triangular(R, (gQ + Q @ symM).T, lower=False).T   # (R^{-1} Y^*)^*
+
+
+def svd_square_vjp(Uh, S, Vh, gUh, gS, gVh):
+    """Cotangent of R for the square SVD R = Uh diag(S) Vh^* (distinct S).
+
+    With dC = Uh^* dR Vh: dS = diag(dC), and off the diagonal
+    (Uh^* dUh)_ij = F_ij (s_j dC_ij + s_i dC_ji), (Vh^* dVh)_ij = F_ij (s_i dC_ij + s_j dC_ji),
+    F_ij = 1 / (s_j^2 - s_i^2).  Collecting the coefficients of dC:
+    g_R = Uh [diag(g_S) + (F o (Gu - Gu^*)) S + S (F o (Gv - Gv^*))] Vh^*,
+    Gu = Uh^* g_Uh, Gv = Vh^* g_Vh.
+    """
+    s2 = S ** 2
+    D = s2[None, :] - s2[:, None]                  # D_ij = s_j^2 - s_i^2
+    np.fill_diagonal(D, 1.0)
+    F = 1.0 / D
+    np.fill_diagonal(F, 0.0)
+    Gu = Uh.T @ gUh
+    Gv = Vh.T @ gVh
+    X = np.diag(gS) + (F * (Gu - Gu.T)) * S[None, :] + S[:, None] * (F * (Gv - Gv.T))
+    return Uh @ X @ Vh.T
+
+
+def rsvd_vjp(A, k, p, q, seed, gU, gS, gV, rounding="f64", Omega=None):
+    """g_A for the map A -> (U, S, V) of Alg. 5 (s = 1) with Omega held fixed,
+    given the cotangents of its outputs; the sign rule is treated as constant.
+
+    The forward steps are those of rsvd(); the backward replays them in reverse
+    with the adjoints of matmul, of orth (qr_pos_vjp with g_R = 0), of the QR of
+    Bt and of the square SVD of R-hat (svd_square_vjp).
+
+    Returns g_A (m x n) and the forward outputs (U, S, V).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[1]
+    l = k + p
+    if Omega is None:
+        Omega = philox.omega(n, l, seed, rounding)
+    # ---- forward, keeping what the backward needs ----
+    tape = []                                      # ("orth", X, Q, R) | ("mulA", W) | ("mulAt", W)
+    Y = A @ Omega
+    tape.append(("mulA", Omega))
+    for _ in range(q):
+        Qy, Ry = qr_pos(Y)
+        tape.append(("orth", Qy, Ry))
+        Z = A.T @ Qy
+        tape.append(("mulAt", Qy))
+        Qz, Rz = qr_pos(Z)
+        tape.append(("orth", Qz, Rz))
+        Y = A @ Qz
+        tape.append(("mulA", Qz))
+    Q, Rq = qr_pos(Y)
+    Bt = A.T @ Q
+    Qh, Rh = qr_pos(Bt)
+    Uh, S, VhT = np.linalg.svd(Rh)
+    Vh = VhT.T
+    U = Q @ Vh[:, :k]
+    V = Qh @ Uh[:, :k]
+    signs = np.ones(k)
+    for j in range(k):
+        i = int(np.argmax(np.abs(V[:, j])))
+        if V[i, j] < 0:
+            signs[j] = -1.0
+    U = U * signs[None, :]
+    V = V * signs[None, :]
+    # ---- backward ----
+    gU = np.asarray(gU, dtype=np.float64) * signs[None, :]
+    gV = np.asarray(gV, dtype=np.float64) * signs[None, :]
+    gA = np.zeros_like(A)
+    gVh = np.zeros((l, l))
+    gUh = np.zeros((l, l))
+    gVh[:, :k] = Q.T @ gU                          # U = Q Vh(:, :k)
+    gQ = gU @ Vh[:, :k].T
+    gUh[:, :k] = Qh.T @ gV                         # V = Qh Uh(:, :k)
+    gQh = gV @ Uh[:, :k].T
+    gSfull = np.zeros(l)
+    gSfull[:k] = gS
+    gRh = svd_square_vjp(Uh, S, Vh, gUh, gSfull, gVh)
+    gBt = qr_pos_vjp(Qh, Rh, gQh, gRh)             # [Qh, Rh] = qr(Bt)
+    gA += Q @ gBt.T                                # Bt = A^* Q
+    gQ += A @ gBt
+    gY = qr_pos_vjp(Q, Rq, gQ, np.zeros_like(Rq))  # Q = orth(Y)
+    for entry in reversed(tape):
+        if entry[0] == "mulA":                     # Y = A W
+            W = entry[1]
+            gA += gY @ W.T
+            gY = A.T @ gY                          # cotangent of W
+        elif entry[0] == "mulAt":                  # Z = A^* W
+            W = entry[1]
+            gA += W @ gY.T
+            gY = A @ gY
+        else:                                      # Q_ = orth(X)
+            _, Qo, Ro = entry
+            gY = qr_pos_vjp(Qo, Ro, gY, np.zeros_like(Ro))
+    return gA, (U, S[:k].copy(), V)
+
+
+# ---------------------------------------------------------------------------
 # Column-pivoted QR, k steps (Sec. 2.3; Alg. 1 first step)
 # ---------------------------------------------------------------------------
 def cpqr(M, ksteps):
