@@ -4,8 +4,9 @@ The no-allocation entry point serves callers that cannot allocate device
 memory or hand over a workspace (cudaMalloc / cudaFree synchronise the device;
 some host frameworks own the whole device-memory budget).  It must give the
 same small SVD as the workspace entry point, twice in a row on the shared
-static scratch, in a fresh process or after every other test.  Collected last
-(file name) so that a first-failure run has already run everything else.
+static scratch, in a fresh process or after the other tests.  Collected after
+the per-step and whole-path files (file name), so that a first-failure run
+has already run them; only the full-size file comes later.
 """
 import ctypes
 

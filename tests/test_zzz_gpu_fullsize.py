@@ -17,6 +17,9 @@ computes one by one:
 * The plan's ID pivots against the oracle's CPQR fed the library's own B: the
   same at every step before the first whose oracle gap is <= 1e-6; where all
   k match, T against the oracle's T (fp32 output: bar 1e-5).
+
+Collected last (file name): it builds the 4 GB matrix, the slowest setup of
+the suite.
 """
 import numpy as np
 import pytest
