@@ -344,6 +344,34 @@ def id_from_matrix(M, k):
     return perm, T, gaps
 
 
+def id_tol(M, tol):
+    """Column ID of M to a tolerance (Sec. 2.6; Sec. 4, TOL mode): the fewest
+    pivoted-QR steps k >= 1 after which ||S22||_F < tol (all min(r, n) steps
+    when none does).  The paper's ||S22|| is read as the Frobenius norm, the
+    root of the sum of the residual column norms that the pivoting tracks.
+
+    The pivots of the first k steps do not depend on later steps, so one full
+    factorization gives every ||S22(k)||_F = ||S[k:, k:]||_F; the ID itself is
+    then the k-step one (later steps would reorder J[k:] and the columns of T).
+
+    Returns J (n,), T (k x (n-k)), k and the norms ||S22(j)||_F, j = 0..min(r, n).
+    """
+    M = np.asarray(M, dtype=np.float64)
+    kmax = min(M.shape)
+    _, S, _, _ = cpqr(M, kmax)
+    norms = np.array([np.linalg.norm(S[j:, j:]) for j in range(kmax)] + [0.0])
+    k = next((j for j in range(1, kmax + 1) if norms[j] < tol), kmax)
+    J, T, _ = id_from_matrix(M, k)
+    return J, T, k, norms
+
+
+def svd_rank_tol(S, tol):
+    """Rank of the SVD to a tolerance (Sec. 2.6): the k with sigma_{k+1} <= tol,
+    i.e. the number of singular values above tol (at least 1)."""
+    S = np.asarray(S, dtype=np.float64)
+    return max(1, int(np.sum(S > tol)))
+
+
 def interpolation_matrix_t(J, T, k):
     """V^* = [I_k  T] P^T as a dense k x n array (Eq. for V in Sec. 2.4)."""
     n = J.size

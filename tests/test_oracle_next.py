@@ -15,6 +15,13 @@ Left-sketch ID
 * no rank-k ID beats sigma_{k+1} (spectral norm);
 * the orthonormalisations between products do not change the row space of
   Omega~ A (A^* A)^q.
+
+Tolerance modes (Sec. 2.6)
+* the ID's residual A(:, J[k:]) - A(:, J[:k]) T equals Q2 S22, so its Frobenius
+  norm is ||S22||_F, and k is the first step that brings it below TOL;
+* an exactly rank-r matrix needs r steps;
+* the SVD truncated at sigma_{k+1} <= TOL on a QB with ||A - Q B|| < eps errs
+  by at most eps + TOL (spectral norm; triangle inequality and Eckart-Young).
 """
 import numpy as np
 import pytest
@@ -104,3 +111,45 @@ def test_left_omega_is_its_own_stream():
     wa = philox.omega_words(64, 8, 3, tag=philox.TAG_OMEGA_LEFT)
     wb = philox.omega_words(64, 8, 3)
     assert np.all(np.any(wa != wb, axis=2))
+
+
+# ---------------------------------------------------------------------------
+# Tolerance mode of the ID and of the SVD (Sec. 2.6)
+# ---------------------------------------------------------------------------
+def test_id_tol_residual_is_s22_and_k_is_minimal():
+    A = make_matrix_np(120, 90, spectrum("logspace4", 90), noise=0.0, seed=27, dtype="float64")
+    for tol in (1e-1, 1e-2, 1e-3):
+        J, T, k, norms = orc.id_tol(A, tol * np.linalg.norm(A))
+        # the ID's residual equals ||S22||_F: A(:, J[k:]) - A(:, J[:k]) T = Q2 S22
+        E = A[:, J[k:]] - A[:, J[:k]] @ T
+        assert np.linalg.norm(E) == pytest.approx(norms[k], rel=1e-8, abs=1e-13)
+        assert norms[k] < tol * np.linalg.norm(A) <= norms[k - 1]
+        # the first k pivots of the full factorization (which gave the norms)
+        # are those of the k-step ID
+        Jfull = orc.cpqr(A, min(A.shape))[0]
+        assert np.array_equal(J[:k], Jfull[:k])
+    assert norms[0] == pytest.approx(np.linalg.norm(A), rel=1e-14)
+
+
+def test_id_tol_exact_rank():
+    rng = np.random.default_rng(28)
+    A = rng.standard_normal((80, 7)) @ rng.standard_normal((7, 60))
+    J, T, k, norms = orc.id_tol(A, 1e-9 * np.linalg.norm(A))
+    assert k == 7 and norms[6] > 1e-3 * norms[0]
+
+
+def test_svd_to_tolerance_on_an_adaptive_qb():
+    # ||A - U_k S_k V_k^*||_2 <= ||A - Q B||_2 + sigma_{k+1}(B) <= eps + tol
+    A = make_matrix_np(200, 150, spectrum("logspace3", 150), noise=0.0, seed=29,
+                       dtype="float64")
+    eps, tol = 1e-2, 3e-2
+    Q, Bt, resid = orc.qb_blocked(A, 10, 15, 1, eps, 4)
+    Qh, Rh = orc.qr_pos(Bt)
+    Uh, S, VhT = np.linalg.svd(Rh)
+    k = orc.svd_rank_tol(S, tol)
+    assert S[k - 1] > tol >= (S[k] if k < S.size else 0.0)
+    U = Q @ VhT.T[:, :k]
+    V = Qh @ Uh[:, :k]
+    err = np.linalg.norm(A - U @ np.diag(S[:k]) @ V.T, 2)
+    assert err <= eps + tol
+    assert err >= np.linalg.svd(A, compute_uv=False)[k] * (1 - 1e-12)
