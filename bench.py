@@ -10,13 +10,15 @@ n = 20000, r = 2000, k = 200, p = 20, q = 2 (4 GB row-major, larger than L2).
 
 JSON line fields: value = algorithmic TFLOP/s of the step (flop count of every
 step of the path, dominated by the 2q+2 passes over A at 2 m n l flops each)
-divided by the measured step time; roofline = the dominant tensor-core kernel
-class (CUDA events recorded by the library on its own stream) against the
-measured HBM copy bandwidth; e2e = the same metric through the host-input
+divided by the measured step time; roofline = the dominant kernel class (CUDA
+events recorded by the library on its own stream) against its hardware bound
+(HBM copy bandwidth for the passes over A, the FP64 pipe for the pivoted QR);
+qb_sketch = rsvd_qb (Y = A Omega through Bt = A^T Q) timed as one unit against
+2q + 2 reads of A at the HBM bandwidth; e2e = the same metric through the host-input
 entry point (A in pinned host memory, copied by the library in row chunks that
 the sketch consumes as they land) with the outputs copied back, all inside the
 timed region;
-cpu_baseline = the FP64 oracle on a bounded sample of the same recipe.
+cpu_baseline = the FP64 oracle, one step on the GPU step's own matrix.
 With --impl reference the oracle itself is the timed arm (host cores).
 """
 import argparse
@@ -110,29 +112,28 @@ def class_roofline(cls, trace, cfg, peaks, peak_kind, sm_mhz):
                      "work_per_launch": "m n 4 bytes (one read of A)"})
         return base
     mhz = sm_mhz or peaks.get("sm_max_mhz", 2070.0)
+    # The pivoted QR and the solves compute FP64-accurate results (double-float
+    # pairs on the FP32 pipe); their roofline is the hardware FP64 rate they
+    # stand in for: 152 SMs x 4 FP64 flops per clock (2 DFMA) x the SM clock
+    # sampled during the timed region.  Two launches per step in both classes;
+    # flops averaged over the pair.
     fp64_peak = SM_COUNT * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
-    # two launches per step in both classes; flops averaged over the pair.
-    # Both run in double-float on the FP32 pipe: the peak is the FP32 issue
-    # rate times FP64-equivalent flops per FP32 instruction of the kernel's
-    # inner operation (CPQR: 4 flops per entry-step in 27 instructions; solve:
-    # 2 flops per multiply-add in 16 instructions).
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     if cls == "cpqr":
         flops = cpqr_flops(l, n, k) + cpqr_flops(k, m, k)    # ID of B, row ID of C^T
-        per_instr = 4.0 / 27.0
     elif cls == "solve":
         flops = solve_flops(k, n - k) + solve_flops(k, k)      # T = S11^-1 S12, U_cur
-        per_instr = 2.0 / 16.0
     else:
         return dict(base, bound=None, note="no work model for this class")
-    df_peak = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 * per_instr / 1e12
     achieved = (flops / 2.0) / (avg_ms * 1e-3) / 1e12
-    base.update({"bound": "alu", "achieved": achieved, "peak": df_peak,
-                 "unit": "TFLOP/s (FP64-equivalent, double-float)",
-                 "frac": achieved / df_peak,
-                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (measured) x "
-                                "%.3f FP64-equivalent flops per FP32 instruction" % (mhz, per_instr),
-                 "fp64_pipe_peak": fp64_peak,
-                 "work_per_launch": "FP64-equivalent flops of the launch (both launches averaged)"})
+    base.update({"bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                 "unit": "TFLOP/s (FP64 flops of the algorithm)",
+                 "frac": achieved / fp64_peak,
+                 "peak_source": "hardware FP64 pipe: 152 SMs x 4 flops/clk x %.0f MHz "
+                                "(clock sampled under load)" % mhz,
+                 "fp32_pipe_peak": fp32_peak,
+                 "arithmetic": "double-float (hi + lo fp32 pairs) on the FP32 pipe, ~48-bit",
+                 "work_per_launch": "FP64 flops of the launch (both launches averaged)"})
     return base
 
 
@@ -152,6 +153,56 @@ def sketch_roofline(trace, cfg, peaks, peak_kind):
             "per_class_ms": {c: trace[c][0] / trace[c][1] for c in cls},
             "traffic": {c: t.get((c, cfg["name"])) for c in cls},
             "peak_source": peak_kind + " STREAM-style copy"}
+
+
+def qb_sketch_unit(rs, A, cfg, args, seed, world, dev, peaks, peak_kind):
+    """The QB sketch (Y = A Omega through Bt = A^T Q: the range finder, its q
+    power iterations with their CholeskyQR orthonormalisations, the final orth
+    and the QB step) timed as one stream-ordered unit: rsvd_qb, W untimed then K
+    timed calls bracketed by CUDA events on the library's stream.  Roofline:
+    its algorithmic bytes, 2q + 2 reads of A, against the measured HBM copy
+    bandwidth; flops 2 m n l (2q + 2) plus the CholeskyQR Grams and applies."""
+    import torch
+    m, n, k, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["q"]
+    l = k + p
+    plan = rs.QbPlan(m, n, k, p, q, A.dtype, dev)
+    for _ in range(args.warmup):
+        plan.run(A, seed)
+    torch.cuda.synchronize()
+    rs.check_info(plan.info, "qb warmup")
+    stream = torch.cuda.current_stream()
+    rs.trace_enable(True)
+    rs.trace_read()
+    launches0 = rs.kernel_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.run(A, seed)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = (rs.kernel_launch_count() - launches0) / args.steps
+    trace = rs.trace_read()
+    rs.trace_enable(False)
+    rs.check_info(plan.info, "qb steps")
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    bytes_ = (2 * q + 2) * a_pass_bytes(m, n, ELEM[cfg["dtype"]])
+    flops = 2.0 * m * n * l * (2 * q + 2) + (q + 1) * 4.0 * (m + n) * l * l
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    del plan
+    return {"what": "rsvd_qb: Y = A Omega, q power iterations with CholeskyQR, Q = orth(Y), "
+                    "Bt = A^T Q (one stream-ordered unit)",
+            "ms": ms, "tflops": world * flops / (ms * 1e-3) / 1e12,
+            "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"],
+            "peak_source": peak_kind + " STREAM-style copy",
+            "work": "%d reads of A (%.1f GB each) per call" % (2 * q + 2, bytes_ / (2 * q + 2) / 1e9),
+            "launches_per_call": launches,
+            "kernels": {c: {"ms_per_call": v[0] / args.steps, "launches_per_call": v[1] / args.steps}
+                        for c, v in trace.items() if v[1] > 0}}
 
 
 def load_peaks():
@@ -293,13 +344,32 @@ def cpu_oracle_sample(cfg, reps=3):
             "sample": desc + ", %.2f s per step (median of %d)" % (dt, reps)}
 
 
+def cpu_oracle_full(A_host, cfg):
+    """The FP64 oracle, as it stands, timed for one step (RSVD, then ID + CUR) on
+    the very matrix the GPU step used (copied to the host and promoted to
+    float64), with OpenBLAS threads on every affinity core."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    A64 = A_host.numpy().astype(np.float64)
+    dt = _oracle_step(A64, cfg)
+    del A64
+    m, n = cfg["m"], cfg["n"]
+    fl = step_flops(m, n, cfg["k"], cfg["p"], cfg["q"])
+    return {"value": fl / dt / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "the full workload (m=%d n=%d k=%d p=%d q=%d, the GPU step's own A in "
+                      "FP64): one step of oracle.rsvd + oracle.rcur, %.1f s"
+                      % (m, n, cfg["k"], cfg["p"], cfg["q"], dt)}
+
+
 def run_reference(args, cfg, rank):
     """--impl reference: the oracle on the host cores (rank 0 only), W untimed
     warm-up steps then K timed steps of the bounded sample."""
     if rank != 0:
         return 0
     A, m, n, cores, desc = _oracle_sample_setup(cfg)
-    for _ in range(min(args.warmup, 3)):
+    for _ in range(args.warmup):
         _oracle_step(A, cfg)
     times = [_oracle_step(A, cfg) for _ in range(args.steps)]
     tot = float(sum(times))
@@ -308,7 +378,7 @@ def run_reference(args, cfg, rank):
     ms = 1e3 * tot / len(times)
     sample = desc + ", %.2f s per step" % (tot / len(times))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": len(times), "warmup": min(args.warmup, 3), "ms_per_step": ms,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": cfg["name"], "sample": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -487,6 +557,8 @@ def main():
     ap.add_argument("--config", default="c2_f32_50000x20000")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-sample", action="store_true",
+                    help="time the oracle on a bounded sample instead of the full workload")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the BF16-storage (mixed precision) measurement")
     ap.add_argument("--no-batched", action="store_true",
@@ -589,6 +661,8 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
            "ms_steps": steps_ms, "statistic": "median of the steps"}
 
+    qb_unit = qb_sketch_unit(rs, A, cfg, args, seed, world, dev, peaks, peak_kind)
+
     mixed = None
     if not args.no_mixed and tdt == torch.float32:
         mixed = mixed_precision_line(rs, A, plan, cfg, args, seed, world, dev, ms, peaks,
@@ -601,7 +675,8 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_oracle_sample(cfg)
+            cpu = (cpu_oracle_sample(cfg) if args.cpu_baseline_sample
+                   else cpu_oracle_full(A_host, cfg))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -619,9 +694,9 @@ def main():
                        "l2": "A (%.1f GB) larger than L2 on every pass"
                              % (ELEM[cfg["dtype"]] * m * n / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "qb_sketch": {"a_pass_ms_per_step": pass_ms,
-                          "a_pass_tflops": qb_flops / (pass_ms * 1e-3) / 1e12 if pass_ms else None,
-                          "a_passes_per_step": 2 * q + 2},
+            "qb_sketch": dict(qb_unit, a_pass_ms_per_step=pass_ms,
+                              a_pass_tflops=qb_flops / (pass_ms * 1e-3) / 1e12 if pass_ms else None,
+                              a_passes_per_step=2 * q + 2),
             "roofline": roof,
             "roofline_sketch": roof_sketch,
             "kernels": breakdown,

@@ -156,9 +156,12 @@ rsvd_status rsvd_svd(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, i
 
 /* -------------------------------------------------------------------------
  * rsvd_id - rank-k column interpolative decomposition through the QB step
- * (Sec. 3.5, last part): k steps of column-pivoted QR (FP64 Householder, pivot
- * = largest residual column norm, ties to the lowest column index, LAPACK-style
- * exchanges) of B = Bt^T (l x n), T = S11^{-1} S12 by back substitution.
+ * (Sec. 3.5, last part): k steps of column-pivoted Householder QR (pivot =
+ * largest residual column norm, ties to the lowest column index, LAPACK-style
+ * exchanges) of B = Bt^T (l x n), T = S11^{-1} S12 by back substitution.  The
+ * arithmetic is FP64 for RSVD_F64 A and double-float (hi + lo float pairs,
+ * about 48 significant bits, compensated dot products) for RSVD_F32 and
+ * RSVD_BF16 A, with the reflector scalars in FP64.
  * Out: J  n int32, the column permutation; J[0:k] is the skeleton;
  *      T  k x (n-k) (ldt >= n-k): A(:, J[k+c]) ~ sum_i A(:, J[i]) T[i][c].
  * ------------------------------------------------------------------------- */
@@ -336,7 +339,9 @@ rsvd_status rsvd_cpqr_id_f32(int r, int64_t n, int k, const float* M, int64_t ld
  * scratch is one static device array of RSVD_NOALLOC_SCRATCH_BYTES per GPU
  * (held until the process exits), shared by all calls: calls that overlap on
  * the GPU race and must be serialised by the caller.  The first call on a
- * device looks up the array's address (make it before any stream capture).
+ * device looks up the array's address (make it before any stream capture);
+ * the address is kept for the life of the process, so the entry point must not
+ * be called on a device after a cudaDeviceReset of that device.
  * Sizes whose scratch need exceeds the array (l above 512 in FP64, about 720
  * in FP32) return RSVD_ERR_WORKSPACE; nothing is allocated.
  * ------------------------------------------------------------------------- */
@@ -376,6 +381,18 @@ int rsvd_trace_read(double* ms, int64_t* launches, int nclass);
 
 /* Number of kernels the library has launched since it was loaded. */
 int64_t rsvd_kernel_launch_count(void);
+
+/* Test aid for the failure path of the bounded waits (host only; not part of
+ * the paper's method).  While `cycles` > 0, every grid-barrier wait of the
+ * pivoted-QR kernels (rsvd_id, rsvd_cur, rsvd_cpqr_id, rsvd_cpqr_id_f32 and the
+ * combined calls) gives up after `cycles` SM clock cycles instead of about
+ * 2 s; with `withhold` non-zero, CTA 0 also withholds its arrival at the first
+ * barrier, so that every CTA's wait runs out: each records RSVD_ERR_TIMEOUT in
+ * *d_info and returns, nothing is left running and the context stays usable.
+ * cycles = 0 restores the defaults (withhold is then ignored).  Affects the
+ * launches enqueued after it by any thread.  RSVD_ERR_INVALID_ARG when
+ * cycles < 0. */
+rsvd_status rsvd_test_set_barrier_wait(long long cycles, int withhold);
 
 /* ------------------------------------------------------------------------
  * Batched RSVD of many small FP32 matrices of different sizes (Alg. 5 for each

@@ -96,6 +96,7 @@ _SIGS = {
     "rsvd_trace_enable": (_c_int, [_c_int]),
     "rsvd_trace_read": (_c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_i64), _c_int]),
     "rsvd_kernel_launch_count": (_c_i64, []),
+    "rsvd_test_set_barrier_wait": (_c_int, [ctypes.c_longlong, _c_int]),
     "rsvd_cpqr_id": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp, _vp,
                               _c_size, _vp, _vp]),
     "rsvd_svd_id_cur_host": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int,
@@ -156,6 +157,14 @@ def trace_read():
 
 def kernel_launch_count():
     return int(lib().rsvd_kernel_launch_count())
+
+
+def test_set_barrier_wait(cycles, withhold=False):
+    """Test aid: bound the pivoted-QR grid-barrier waits to `cycles` SM clocks
+    (0 restores the default) and optionally withhold CTA 0's first arrival
+    (rsvd_test_set_barrier_wait)."""
+    _raise(lib().rsvd_test_set_barrier_wait(int(cycles), 1 if withhold else 0),
+           "rsvd_test_set_barrier_wait")
 
 
 def make_opts(s=1, max_sweeps=30, precision=PREC_TC):
@@ -405,6 +414,34 @@ class Plan:
             self.n - k, _ptr(self.Jc), _ptr(self.Ir), _ptr(self.Ucur), k, _ptr(self.work),
             self.work.numel(), _ptr(self.info), _stream(), _opts_ptr(self.opts))
         _raise(st, "rsvd_svd_id_cur")
+
+
+class QbPlan:
+    """Pre-allocated Q, Bt and workspace for repeated rsvd_qb calls (the range
+    finder with the power scheme and Bt = A^T Q, Alg. 5 up to the QB step)."""
+
+    def __init__(self, m, n, k, p, q, dtype, device, opts=None):
+        torch = _torch()
+        self.m, self.n, self.k, self.p, self.q = m, n, k, p, q
+        self.dt = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16}[dtype]
+        self.opts = opts
+        dev = torch.device(device)
+        l = k + p
+        self.Q = torch.empty(m, l, dtype=_out_dtype(dtype), device=dev)
+        self.Bt = torch.empty(n, l, dtype=_out_dtype(dtype), device=dev)
+        ws = lib().rsvd_qb_workspace_size(m, n, k, p, q, self.dt, _opts_ptr(opts))
+        if ws == 0:
+            raise RsvdError(1, "rsvd_qb_workspace_size")
+        self.work = _work(ws, dev)
+        self.info = _info(dev)
+
+    def run(self, A, seed):
+        _check_matrix(A, "A")
+        l = self.k + self.p
+        st = lib().rsvd_qb(self.m, self.n, self.k, self.p, self.q, seed, self.dt, _ptr(A),
+                           A.stride(0), _ptr(self.Q), l, _ptr(self.Bt), l, _ptr(self.work),
+                           self.work.numel(), _ptr(self.info), _stream(), _opts_ptr(self.opts))
+        _raise(st, "rsvd_qb")
 
 
 def svd_id_cur(A, k, p, q, seed, opts=None, check=True):

@@ -19,6 +19,19 @@ namespace rsvd {
 namespace {
 constexpr int PT = 1024;
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;
+// Test aid (rsvd_test_set_barrier_wait): a shorter bound on the grid-barrier
+// waits and, optionally, CTA 0 withholding its arrival at the first barrier so
+// that every wait runs out.  0 / 0 = the defaults.
+long long g_test_spin_limit = 0;
+int g_test_withhold = 0;
+}
+
+extern "C" rsvd_status rsvd_test_set_barrier_wait(long long cycles, int withhold) {
+  if (cycles < 0) return RSVD_ERR_INVALID_ARG;
+  if (cycles == 0) withhold = 0;
+  g_test_spin_limit = cycles;
+  g_test_withhold = withhold ? 1 : 0;
+  return RSVD_OK;
 }
 
 // Proposal slots: 2 x 1024 CTAs x (2 doubles) and 2 x 1024 x int64.
@@ -33,19 +46,21 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Returns false when the wait ran out.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int* d_info) {
+// Returns false when the wait ran out.  `limit` bounds the wait in SM clock
+// cycles; `arrive` false withholds this CTA's arrival (test aid only).
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int* d_info, long long limit,
+                             bool arrive) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(bar, 1u);
+    if (arrive) atomicAdd(bar, 1u);
     const long long t0 = clock64();
     int ok = 1;
     unsigned it = 0;
     while (ld_acquire_u32(bar) < target) {
       __nanosleep(100);
-      if (((++it) & 255u) == 0 && clock64() - t0 > SPIN_LIMIT_CYCLES) {
+      if (((++it) & 255u) == 0 && clock64() - t0 > limit) {
         set_info(d_info, RSVD_ERR_TIMEOUT);
         ok = 0;
         break;
@@ -166,7 +181,9 @@ __global__ void __launch_bounds__(PT) cpqr_kernel(CpqrArgs a) {
       a.pval[(size_t)slot * 2 * G + 2 * blockIdx.x + 1] = loc.b2;
       a.pidx[(size_t)slot * G + blockIdx.x] = loc.i1;
     }
-    if (!grid_barrier(a.bar, (unsigned)(j + 1) * (unsigned)G, a.d_info)) return;
+    if (!grid_barrier(a.bar, (unsigned)(j + 1) * (unsigned)G, a.d_info, a.spin_limit,
+                      !(a.withhold && j == 0 && blockIdx.x == 0)))
+      return;
     Top2 g{-1.0, 0x7fffffffffffffffLL, -1.0};
     for (int b = tid; b < G; b += PT)
       g = merge_top2(g, Top2{__ldcg(a.pval + (size_t)slot * 2 * G + 2 * b),
@@ -287,8 +304,8 @@ cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel, PT, dyn);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  // one SM is left to a single-CTA kernel running beside the CPQR on another
-  // stream (the Jacobi SVD of the combined SVD + ID/CUR call)
+  // one SM is left to the one-CTA FP64 Jacobi SVD that runs beside the CPQR
+  // on another stream in the combined SVD + ID/CUR call
   int64_t G = sms > 1 ? sms - 1 : 1;
   const int64_t byn = ceil_div(a.n, 32);
   if (G > byn) G = byn;
@@ -303,6 +320,8 @@ cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   CpqrArgs b = a;
   b.tpc = tpc;
+  b.spin_limit = g_test_spin_limit > 0 ? g_test_spin_limit : SPIN_LIMIT_CYCLES;
+  b.withhold = g_test_withhold;
   void* args[] = {(void*)&b};
   count_launch();
   const int tr = trace_begin(RSVD_TRACE_CPQR, s);
@@ -645,14 +664,15 @@ __device__ __forceinline__ Top2F warp_top2f(Top2F v) {
 // CTA's proposal, written by the same thread before it, is visible to whoever
 // acquires the count); the poll is an acquire load, which orders the reads of
 // other CTAs' proposals.
-__device__ __forceinline__ bool grid_barrier_warp(unsigned* bar, unsigned target, int* d_info) {
+__device__ __forceinline__ bool grid_barrier_warp(unsigned* bar, unsigned target, int* d_info,
+                                                  long long limit, bool arrive) {
   int ok = 1;
   if ((threadIdx.x & 31) == 0) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     const long long t0 = clock64();
     unsigned it = 0;
     while (ld_acquire_u32(bar) < target) {
-      if (((++it) & 1023u) == 0 && clock64() - t0 > SPIN_LIMIT_CYCLES) {
+      if (((++it) & 1023u) == 0 && clock64() - t0 > limit) {
         set_info(d_info, RSVD_ERR_TIMEOUT);
         ok = 0;
         break;
@@ -759,7 +779,8 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
         pv[(size_t)slot * G + blockIdx.x] = make_float4(v.b1.h, v.b1.l, v.b2.h, v.b2.l);
         a.pidx[(size_t)slot * G + blockIdx.x] = v.i1;
       }
-      if (!grid_barrier_warp(a.bar, (unsigned)(j + 1) * (unsigned)G, a.d_info)) {
+      if (!grid_barrier_warp(a.bar, (unsigned)(j + 1) * (unsigned)G, a.d_info, a.spin_limit,
+                             !(a.withhold && j == 0 && blockIdx.x == 0))) {
         if (lane == 0) s_abort = 1;
       } else {
         Top2F g{none, 0x7fffffffffffffffLL, none};
@@ -920,6 +941,8 @@ static cudaError_t launch_cpqr_df_t(const CpqrArgs& a, int sms, cudaStream_t s) 
   if (e != cudaSuccess) return e;
   CpqrArgs b = a;
   b.nrm_local = nrm_local ? 1 : 0;
+  b.spin_limit = g_test_spin_limit > 0 ? g_test_spin_limit : SPIN_LIMIT_CYCLES;
+  b.withhold = g_test_withhold;
   void* args[] = {(void*)&b};
   count_launch();
   const int tr = trace_begin(RSVD_TRACE_CPQR, s);

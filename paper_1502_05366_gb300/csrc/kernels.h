@@ -136,6 +136,8 @@ struct CpqrArgs {
   int* d_info;
   int tpc;          // set by the launcher: threads per column (FP64 kernel)
   int nrm_local;    // set by the launcher: residual norms in shared memory (double-float kernel)
+  long long spin_limit;  // set by the launcher: bound of each grid-barrier wait (SM clocks)
+  int withhold;     // set by the launcher: CTA 0 skips its first arrival (test aid)
 };
 cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s);
 // Double-float arithmetic on the same working area reinterpreted as two float

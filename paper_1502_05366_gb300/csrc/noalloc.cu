@@ -13,7 +13,10 @@
 // The array's name is only a host-side stand-in in host code; its device
 // address is looked up once per device with cudaGetSymbolAddress, with that
 // device current, on the first call made on that device (do that first call
-// before any stream capture).  All calls share the one array and it keeps the
+// before any stream capture).  The address is cached for the life of the
+// process: after a cudaDeviceReset the module, and with it the array, is
+// reloaded elsewhere, so the entry point must not be called on that device
+// again.  All calls share the one array and it keeps the
 // last call's contents; calls that overlap on the GPU (different streams, or
 // host threads racing) race on it and must be serialised by the caller.
 #include <mutex>

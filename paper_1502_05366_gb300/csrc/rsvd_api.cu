@@ -4,9 +4,12 @@
 // with a bump allocator (the same code computes the *_workspace_size values
 // by running without launching), and enqueues kernels on the caller's stream.
 // No device memory is allocated and the host never waits for the device.  The
-// combined SVD + ID/CUR call forks one kernel (the single-CTA Jacobi SVD) onto
-// an auxiliary stream and joins it back with events; that stream and its two
-// events are created once per device on first use.
+// combined SVD + ID/CUR call forks one kernel (the Jacobi SVD: an 8-CTA
+// cluster for FP32 cores of 32 <= l <= 256, one CTA otherwise) onto an
+// auxiliary stream and joins it back with events; that stream and its two
+// events are created once per device on first use and kept until the process
+// exits (a cudaDeviceReset invalidates them: do not call the library on that
+// device afterwards).
 #include <cstring>
 #include <mutex>
 
@@ -859,11 +862,15 @@ static rsvd_status run_all(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t n,
       LK(launch_transpose<T, double>(n, l, qbb.Z, L, idb.W, n, c.stream));
     }
   }
-  // With the ID/CUR requested too, the single-CTA Jacobi sweeps of the SVD run
-  // on the auxiliary stream, beside the CPQR and solves (which leave one SM
-  // free); the SVD is finished on the caller's stream after the join.  The
-  // two branches share no buffer: the Jacobi reads Rh and writes the SVD
-  // buffers only.
+  // With the ID/CUR requested too, the Jacobi sweeps of the SVD run on the
+  // auxiliary stream, beside the CPQR and solves; the SVD is finished on the
+  // caller's stream after the join.  The double-float CPQR grid leaves eight
+  // SMs free and the FP64 one one SM, room for the 8-CTA cluster or the
+  // one-CTA Jacobi; whether the cluster is placed beside the running
+  // cooperative grid is the hardware scheduler's choice (it needs eight free
+  // SMs of one GPC), so the overlap is partial and the results do not depend
+  // on it.  The two branches share no buffer: the Jacobi reads Rh and writes
+  // the SVD buffers only.
   SideStream* ss = nullptr;
   std::unique_lock<std::mutex> side_lock;
   if (want & W_SVD) {

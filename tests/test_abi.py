@@ -200,3 +200,21 @@ def test_adaptive_qb_workspace_and_validation(lib):
     assert st(q=65) == 1
     assert st() == 2                   # no workspace
     assert rank.value == -1            # nothing ran
+
+
+def test_noalloc_scratch_limits(lib):
+    """The 16 MiB static scratch of rsvd_small_svd_noalloc holds the small-SVD
+    workspace up to l = 512 (FP64) and l = 720 (FP32), and no further: the
+    documented limits follow the workspace layout."""
+    import paper_1502_05366_gb300 as rs
+    cap = 16 << 20
+    assert lib.rsvd_small_svd_workspace_size(512, rs.F64, None) <= cap
+    assert lib.rsvd_small_svd_workspace_size(513, rs.F64, None) > cap
+    assert lib.rsvd_small_svd_workspace_size(720, rs.F32, None) <= cap
+    assert lib.rsvd_small_svd_workspace_size(721, rs.F32, None) > cap
+
+
+def test_barrier_wait_test_aid_arguments(lib):
+    assert lib.rsvd_test_set_barrier_wait(-1, 0) == 1        # RSVD_ERR_INVALID_ARG
+    assert lib.rsvd_test_set_barrier_wait(1000, 1) == 0
+    assert lib.rsvd_test_set_barrier_wait(0, 1) == 0          # defaults restored

@@ -36,14 +36,14 @@ def test_alu_roofline_of_the_pivoted_qr():
     trace = {"cpqr": (8.0, 2)}
     r = bench.class_roofline("cpqr", trace, CFG, PEAKS, "measured", 1500.0)
     assert r["bound"] == "alu"
-    # peak = SMs x FP32 lanes x clock x (4 FP64-equivalent flops / 27 instructions)
-    assert r["peak"] == pytest.approx(152 * 128 * 1500e6 * 4 / 27 / 1e12, rel=1e-12)
+    # peak = the hardware FP64 pipe: SMs x 4 flops per clock x the sampled clock
+    assert r["peak"] == pytest.approx(152 * 4 * 1500e6 / 1e12, rel=1e-12)
     # the two launches of a step (ID of B: l x n; row ID of C^T: k x m), averaged
     l, k, m, n = 220, 200, 50000, 20000
     work = sum(4.0 * (l - j) * (n - j - 1) for j in range(k)) + \
         sum(4.0 * (k - j) * (m - j - 1) for j in range(k))
     assert r["achieved"] == pytest.approx(work / 2 / 4e-3 / 1e12, rel=1e-12)
-    assert 0 < r["frac"] < 1
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-12)
 
 
 def test_cpqr_flops_closed_form():

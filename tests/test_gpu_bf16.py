@@ -34,7 +34,19 @@ def _bf16(x):
     return t.to(DEV), t.double().numpy()
 
 
-SHAPES = [(1000, 800, 60), (4096, 2048, 220), (1001, 776, 13), (257, 296, 64)]  # lda % 8 == 0
+def _elem_err(Y, ref, absprod):
+    """max over entries of |Y - ref| / (|A| |W|): each entry against the error
+    bound of its own dot product; entries whose bound is zero must be zero."""
+    d = np.abs(np.asarray(Y, dtype=np.float64) - ref)
+    den = np.asarray(absprod, dtype=np.float64)
+    assert np.all(d[den == 0] == 0)
+    nz = den > 0
+    return float(np.max(d[nz] / den[nz])) if nz.any() else 0.0
+
+
+# lda % 8 == 0; the last shape is ragged against the 512- and 256-row units
+SHAPES = [(1000, 800, 60), (4096, 2048, 220), (1001, 776, 13), (257, 296, 64),
+          (16411, 4104, 220)]
 
 
 @pytest.mark.parametrize("m,n,l", SHAPES)
@@ -46,6 +58,9 @@ def test_sample_bf16(m, n, l):
     # against the kernels' own Omega: only fp32 accumulation error
     Om_gpu = rs.omega(n, l, seed, torch.float32, DEV).double().cpu().numpy()
     assert _rel(Y, A64 @ Om_gpu) <= 1e-5
+    # element-wise: exact products, fp32 accumulation only
+    e = _elem_err(Y, A64 @ Om_gpu, np.abs(A64) @ np.abs(Om_gpu))
+    assert e <= 1e-5, e
     # against the oracle's Omega (rare bf16 rounding flips of a Gaussian)
     assert _rel(Y, A64 @ philox.omega(n, l, seed, "bf16")) <= 1e-4
 
@@ -60,6 +75,10 @@ def test_apply_bf16(m, n, l, trans):
     X64 = X.astype(np.float64)
     ref = (A64.T @ X64) if trans else (A64 @ X64)
     assert _rel(Y, ref) <= 3e-5, _rel(Y, ref)
+    # element-wise: two bf16 terms of X (2^-16 per product) and fp32 accumulation
+    a, x = np.abs(A64), np.abs(X64)
+    e = _elem_err(Y, ref, (a.T @ x) if trans else (a @ x))
+    assert e <= 5e-5, e
 
 
 def _matched_prefix(J, Jo, gaps):

@@ -34,6 +34,26 @@ def _dev(x, dtype):
     return torch.from_numpy(np.ascontiguousarray(x)).to(DEV, dtype)
 
 
+def _elem_err(Y, ref, absprod):
+    """max over entries of |Y - ref| / (|A| |W|): every entry against the error
+    bound of its own dot product.  The split products and the fp32 sums err in
+    proportion to the sum of the absolute term products, so a wrong tile, a
+    stale padded column or a dropped stream-K contribution shows up at full
+    size however small the entry is.  Entries whose bound is zero must be
+    exactly zero."""
+    d = np.abs(np.asarray(Y, dtype=np.float64) - ref)
+    den = np.asarray(absprod, dtype=np.float64)
+    assert np.all(d[den == 0] == 0)
+    nz = den > 0
+    return float(np.max(d[nz] / den[nz])) if nz.any() else 0.0
+
+
+# Element-wise bars relative to |A| |W| (worst case of the arithmetic):
+# Omega is bf16-exact and A carries two bf16 terms (2^-16 per product) plus fp32
+# accumulation: 2e-5; a stored operand adds its own dropped terms: 5e-5; FP64: 1e-12.
+ELEM_TC_SAMPLE, ELEM_TC_APPLY, ELEM_F64 = 2e-5, 5e-5, 1e-12
+
+
 # ---------------------------------------------------------------------------
 # Philox / Omega: integer words bit-exact, Gaussians within rounding
 # ---------------------------------------------------------------------------
@@ -89,7 +109,10 @@ def test_omega_f32_distribution():
 # ---------------------------------------------------------------------------
 # sample Y = A Omega and the power half steps
 # ---------------------------------------------------------------------------
-SHAPES = [(300, 200, 24), (1000, 777, 60), (517, 1290, 17), (129, 33, 16), (2048, 4096, 220)]
+# the last shape: m and n not multiples of the 512-row super-unit or the 256-row
+# unit, and long enough contractions that stream-K splits them across CTAs
+SHAPES = [(300, 200, 24), (1000, 777, 60), (517, 1290, 17), (129, 33, 16), (2048, 4096, 220),
+          (16411, 4099, 220)]
 
 
 @pytest.mark.parametrize("m,n,l", SHAPES)
@@ -100,8 +123,10 @@ def test_sample(m, n, l, mode):
     seed = 1234 + l
     if mode == "f64":
         Y = rs.sample(_dev(A, torch.float64), l, seed).cpu().numpy()
-        ref = A @ philox.omega(n, l, seed, "f64")
+        Om = philox.omega(n, l, seed, "f64")
+        ref = A @ Om
         assert _rel(Y, ref) <= 1e-13
+        assert _elem_err(Y, ref, np.abs(A) @ np.abs(Om)) <= ELEM_F64
     else:
         A32 = A.astype(np.float32)
         opts = _simt() if mode == "simt" else None
@@ -111,6 +136,9 @@ def test_sample(m, n, l, mode):
         ref = A32.astype(np.float64) @ Om_gpu
         tol = 2e-5 if mode == "tc" else 2e-6
         assert _rel(Y, ref) <= tol, _rel(Y, ref)
+        if mode == "tc":
+            e = _elem_err(Y, ref, np.abs(A32.astype(np.float64)) @ np.abs(Om_gpu))
+            assert e <= ELEM_TC_SAMPLE, e
         # ... and against the oracle's Omega, which differs by rare bf16 flips
         ref_o = A32.astype(np.float64) @ philox.omega(n, l, seed, "bf16")
         assert _rel(Y, ref_o) <= 1e-4, _rel(Y, ref_o)
@@ -127,6 +155,8 @@ def test_apply(m, n, l, trans, mode):
     if mode == "f64":
         Y = rs.apply(_dev(A, torch.float64), _dev(X, torch.float64), trans).cpu().numpy()
         assert _rel(Y, ref) <= 1e-13
+        absprod = (np.abs(A).T @ np.abs(X)) if trans else (np.abs(A) @ np.abs(X))
+        assert _elem_err(Y, ref, absprod) <= ELEM_F64
     else:
         opts = _simt() if mode == "simt" else None
         A32, X32 = A.astype(np.float32), X.astype(np.float32)
@@ -134,6 +164,10 @@ def test_apply(m, n, l, trans, mode):
         Y = rs.apply(_dev(A32, torch.float32), _dev(X32, torch.float32), trans, opts).cpu().numpy()
         tol = 3e-5 if mode == "tc" else 2e-6
         assert _rel(Y, ref) <= tol, _rel(Y, ref)
+        if mode == "tc":
+            a, x = np.abs(A32.astype(np.float64)), np.abs(X32.astype(np.float64))
+            e = _elem_err(Y, ref, (a.T @ x) if trans else (a @ x))
+            assert e <= ELEM_TC_APPLY, e
 
 
 # ---------------------------------------------------------------------------

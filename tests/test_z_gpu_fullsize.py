@@ -18,8 +18,15 @@ computes one by one:
   same at every step before the first whose oracle gap is <= 1e-6; where all
   k match, T against the oracle's T (fp32 output: bar 1e-5).
 
-Collected last (file name): it builds the 4 GB matrix, the slowest setup of
-the suite.
+* The whole path against the FP64 oracle itself (oracle.rsvd and oracle.rcur on
+  the same stored A promoted to float64, the same seed and the bf16 rounding of
+  Omega): singular values per index (1e-5 above the noise edge, where sigma_i
+  exceeds twice the noise's spectral norm; a documented looser bar in the
+  noise bulk), reconstruction errors within 1 %, ID and CUR indices identical
+  before the first oracle step whose pivot gap is <= 1e-6, CUR error within 1 %.
+
+Collected after the other parity files (file name): it builds the 4 GB matrix,
+the slowest setup of the suite.
 """
 import numpy as np
 import pytest
@@ -101,3 +108,64 @@ def test_fullsize_plan_against_its_own_sketch(c2):
         # indexed by the same order of J[k:]
         assert np.array_equal(J, Jo)
         assert _rel(plan.T.double().cpu().numpy(), To) <= 1e-5
+
+
+def _rel_err_cur_blocked(A64, Jc, Ir, U, block=5000):
+    """||A - A(:, Jc) U A(Ir, :)||_F / ||A||_F in FP64, row block by row block."""
+    CU = A64[:, Jc] @ U
+    R = A64[Ir, :]
+    num = den = 0.0
+    for i0 in range(0, A64.shape[0], block):
+        Ab = A64[i0:i0 + block]
+        D = Ab - CU[i0:i0 + block] @ R
+        num += float(np.sum(D * D))
+        den += float(np.sum(Ab * Ab))
+    return np.sqrt(num / den)
+
+
+def test_fullsize_whole_path_against_the_oracle(c2):
+    """The bench's call (one Plan: SVD, ID and CUR from one sketch) against the
+    oracle's Alg. 5, ID and CUR run in FP64 on the same matrix and Omega."""
+    cfg, A = c2
+    m, n, k, p, q, seed = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["q"], cfg["omega_seed"]
+    plan = rs.Plan(m, n, k, p, q, torch.float32, DEV)
+    plan.run(A, seed)
+    torch.cuda.synchronize()
+    rs.check_info(plan.info, "plan")
+    A64 = A.cpu().numpy().astype(np.float64)
+    Uo, So, Vo, _ = orc.rsvd(A64, k, p, q, seed, rounding="bf16")
+    Jco, Iro, Ucuro, Jo, To, cgaps, rgaps = orc.rcur(A64, k, p, q, seed, rounding="bf16")
+    S = plan.S.cpu().numpy()
+    rel = np.abs(S - So) / So
+    # noise edge: the 1e-4 N(0,1) noise has spectral norm ~1e-4 (sqrt(m) + sqrt(n))
+    edge = 2.0 * cfg["noise"] * (np.sqrt(m) + np.sqrt(n))
+    top = So > edge
+    assert top[:20].all()
+    print("sigma rel err: above edge (%d) max %.2e; bulk max %.2e median %.2e"
+          % (top.sum(), rel[top].max(), rel[~top].max(), np.median(rel[~top])))
+    assert rel[top].max() <= 1e-5, rel[top].max()
+    assert rel.max() <= 1e-4, rel.max()
+    e_gpu = orc.rel_err_svd(A64, plan.U.double().cpu().numpy(), S, plan.V.double().cpu().numpy())
+    e_orc = orc.rel_err_svd(A64, Uo, So, Vo)
+    assert abs(e_gpu - e_orc) <= 0.01 * e_orc, (e_gpu, e_orc)
+    # ID pivots: identical before the first oracle gap <= 1e-6
+    J = plan.J.cpu().numpy()
+    t = 0
+    while t < k and J[t] == Jo[t]:
+        t += 1
+    first_small = next((i for i, g in enumerate(cgaps) if g <= 1e-6), k)
+    print("ID pivots: %d of %d match; first oracle gap <= 1e-6 at %d" % (t, k, first_small))
+    assert t >= min(first_small, k), (t, first_small)
+    # CUR: row pivots by the same rule (when every column pivot matched), error within 1 %
+    Ir = plan.Ir.cpu().numpy()
+    if t >= k:
+        tr = 0
+        while tr < k and Ir[tr] == Iro[tr]:
+            tr += 1
+        first_small_r = next((i for i, g in enumerate(rgaps) if g <= 1e-6), k)
+        print("CUR row pivots: %d of %d match; first oracle gap <= 1e-6 at %d"
+              % (tr, k, first_small_r))
+        assert tr >= min(first_small_r, k), (tr, first_small_r)
+    c_gpu = _rel_err_cur_blocked(A64, plan.Jc.cpu().numpy(), Ir, plan.Ucur.double().cpu().numpy())
+    c_orc = _rel_err_cur_blocked(A64, Jco, Iro, Ucuro)
+    assert abs(c_gpu - c_orc) <= 0.01 * c_orc, (c_gpu, c_orc)
