@@ -171,6 +171,67 @@ rsvd_status rsvd_id(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, in
                     const rsvd_opts* opts);
 
 /* -------------------------------------------------------------------------
+ * Tolerance mode (Sec. 2.6; Sec. 4, "TOL"): the rank is chosen from the
+ * result instead of fixed in advance.  The sketch is built with
+ * l = kmax + p columns; the host learns the rank through one synchronisation
+ * with `stream`, so these three calls cannot be captured in a CUDA graph.
+ * `rank` is HOST memory.  tol must be positive and finite.
+ *
+ * rsvd_svd_tol - rsvd_svd with k = kmax, then *rank = the number of computed
+ *   singular values above tol (at least 1): sigma_{rank+1} <= tol.  U, S, V
+ *   are written for all kmax columns; the first *rank form the result.
+ *   Workspace: rsvd_svd_workspace_size(m, n, kmax, p, q, dtype, opts).
+ *
+ * rsvd_id_tol - rsvd_id whose pivoted QR of B (l x n) stops before step
+ *   j >= 1 as soon as ||S22(j)||_F < tol (the Frobenius norm of the
+ *   residual block, i.e. the root of the sum of the residual column norms^2
+ *   that the pivoting tracks), at the latest after kmax steps; *rank = the
+ *   number of steps taken, and J, T are the ID of that rank (T is
+ *   rank x (n - rank), ldt >= n - 1).  1 <= kmax < n.
+ *
+ * rsvd_cur_tol - rsvd_cur on the column ID of rsvd_id_tol: the row ID of
+ *   C = A(:, Jc) takes *rank steps.  Jc, Ir hold kmax entries and U kmax x kmax
+ *   (ldu >= kmax); the first *rank (rows and columns) are written.
+ *   kmax < min(m, n).
+ *
+ * Errors as rsvd_id / rsvd_cur; a device failure recorded in *d_info (the
+ * call has synchronised, so it can be read at once) leaves *rank = 0 for the
+ * ID and CUR calls.
+ * ------------------------------------------------------------------------- */
+size_t rsvd_id_tol_workspace_size(int64_t m, int64_t n, int kmax, int p, int q, int dtype,
+                                  const rsvd_opts* opts);
+size_t rsvd_cur_tol_workspace_size(int64_t m, int64_t n, int kmax, int p, int q, int dtype,
+                                   const rsvd_opts* opts);
+rsvd_status rsvd_svd_tol(int64_t m, int64_t n, int kmax, int p, int q, double tol, uint64_t seed,
+                         int dtype, const void* A, int64_t lda, void* U, int64_t ldu, double* S,
+                         void* V, int64_t ldv, int* rank, void* work, size_t work_bytes,
+                         int* d_info, void* stream, const rsvd_opts* opts);
+rsvd_status rsvd_id_tol(int64_t m, int64_t n, int kmax, int p, int q, double tol, uint64_t seed,
+                        int dtype, const void* A, int64_t lda, int32_t* J, void* T, int64_t ldt,
+                        int* rank, void* work, size_t work_bytes, int* d_info, void* stream,
+                        const rsvd_opts* opts);
+rsvd_status rsvd_cur_tol(int64_t m, int64_t n, int kmax, int p, int q, double tol, uint64_t seed,
+                         int dtype, const void* A, int64_t lda, int32_t* Jc, int32_t* Ir, void* U,
+                         int64_t ldu, int* rank, void* work, size_t work_bytes, int* d_info,
+                         void* stream, const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
+ * rsvd_id_left - rank-k column ID from the LEFT sketch (Sec. 3.5, Alg. 6):
+ *   Y = Omega~ A (A^* A)^q, Omega~ l x m Gaussian (l = k + p), orthonormalised
+ *   before every product (Y <- (A orth(Y^*))^*, then (A^* orth(Y^*))^*; the
+ *   s option is not used), then k steps of the pivoted QR of Y (l x n) as in
+ *   rsvd_id and T = S11^{-1} S12.  Omega~^* is the Philox stream of `seed`
+ *   with counter (row i < m, column j / 4, tag 1, 0), values as for Omega.
+ *   It is generated once into the workspace (m x l), not re-drawn per tile.
+ * Out: J n int32 (J[0:k] skeleton); T k x (n-k) (ldt >= n-k).
+ * ------------------------------------------------------------------------- */
+size_t rsvd_id_left_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                                   const rsvd_opts* opts);
+rsvd_status rsvd_id_left(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                         const void* A, int64_t lda, int32_t* J, void* T, int64_t ldt, void* work,
+                         size_t work_bytes, int* d_info, void* stream, const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
  * rsvd_cur - rank-k CUR A ~ A(:, Jc) U A(Ir, :) (Sec. 3.6; Alg. 2, 3): the
  * randomized ID above, then a k-step pivoted QR of C^* with C = A(:, Jc)
  * (row ID), R = A(Ir, :), and U = V^* R^dagger with R^dagger = Q_R R_R^{-T}
@@ -257,6 +318,31 @@ rsvd_status rsvd_qb_adaptive(int64_t m, int64_t n, int b, int M, int q, double e
                              void* Q, int64_t ldq, void* Bt, int64_t ldbt, double* resid,
                              int* rank, void* work, size_t work_bytes, int* d_info,
                              void* stream, const rsvd_opts* opts);
+
+/* -------------------------------------------------------------------------
+ * rsvd_svd_vjp - reverse-mode derivative of rsvd_svd (Alg. 5 with the orth of
+ * every power step, s = 1) with Omega held fixed and the sign rule treated as
+ * constant: given the cotangents gU (m x k), gS (k doubles) and gV (n x k) of
+ * the outputs U, S, V, writes gA (m x n, ldga >= n) = the cotangent of A.
+ * Nothing needs to be kept from the forward call: this call replays the
+ * forward path from A and `seed` (every orthonormalisation a full CholeskyQR,
+ * so each Q is orthonormal to working precision) and keeps its factors in the
+ * workspace, then applies the adjoints in reverse order: of the products with
+ * A and A^*, of the thin QR X = Q R (diag(R) > 0), and of the square SVD of
+ * R-hat with its 1 / (s_j^2 - s_i^2) coupling (distinct singular values; equal
+ * ones contribute nothing).  U (m x k), S (k) and V (n x k) receive the
+ * replayed forward outputs when non-NULL.
+ * dtype: RSVD_F32 (tensor-core or SIMT path as rsvd_svd) or RSVD_F64;
+ * RSVD_BF16 gives RSVD_ERR_UNSUPPORTED.  gU, gS, gV must be non-NULL (pass
+ * zeros for an output the loss does not use).
+ * ------------------------------------------------------------------------- */
+size_t rsvd_svd_vjp_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
+                                   const rsvd_opts* opts);
+rsvd_status rsvd_svd_vjp(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
+                         const void* A, int64_t lda, const void* gU, int64_t ldgu,
+                         const double* gS, const void* gV, int64_t ldgv, void* gA, int64_t ldga,
+                         void* U, int64_t ldu, double* S, void* V, int64_t ldv, void* work,
+                         size_t work_bytes, int* d_info, void* stream, const rsvd_opts* opts);
 
 /* =========================================================================
  * Step-level entry points (one per step of the path; same conventions).

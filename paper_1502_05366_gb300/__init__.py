@@ -9,6 +9,10 @@ when librsvd.so has not been built.
 
 Functions (names follow the C ABI):
   qb, svd, id, cur, svd_id_cur       - the routines of the paper's Alg. 5 / Sec. 3.5-3.6
+  svd_tol, id_tol, cur_tol           - the same to a tolerance (Sec. 2.6, Sec. 4 TOL mode)
+  id_left                            - the ID from the left sketch (Sec. 3.5, Alg. 6)
+  svd_vjp, svd_autograd              - the adjoint of Alg. 5 (rsvd_svd_vjp) and a
+                                       torch.autograd.Function around it
   omega, omega_words                 - the Philox Gaussian test matrix (checking aid)
   sample, apply, orth, small_svd     - the individual steps of the path
   cpqr_id                            - column ID of an explicit FP64 matrix (Alg. 1)
@@ -110,6 +114,28 @@ _SIGS = {
                                   _vp, _vp, _vp, _vp, _c_size, _vp, _vp]),
     "rsvd_cpqr_id_f32": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
                                   _vp, _c_size, _vp, _vp]),
+    "rsvd_id_tol_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int,
+                                             _OPTP]),
+    "rsvd_cur_tol_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int,
+                                              _OPTP]),
+    "rsvd_id_left_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int,
+                                              _OPTP]),
+    "rsvd_svd_tol": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, ctypes.c_double, _c_u64,
+                              _c_int, _vp, _c_i64, _vp, _c_i64, _vp, _vp, _c_i64,
+                              ctypes.POINTER(_c_int), _vp, _c_size, _vp, _vp, _OPTP]),
+    "rsvd_id_tol": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, ctypes.c_double, _c_u64,
+                             _c_int, _vp, _c_i64, _vp, _vp, _c_i64, ctypes.POINTER(_c_int), _vp,
+                             _c_size, _vp, _vp, _OPTP]),
+    "rsvd_cur_tol": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, ctypes.c_double, _c_u64,
+                              _c_int, _vp, _c_i64, _vp, _vp, _vp, _c_i64, ctypes.POINTER(_c_int),
+                              _vp, _c_size, _vp, _vp, _OPTP]),
+    "rsvd_id_left": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int, _vp, _c_i64,
+                              _vp, _vp, _c_i64, _vp, _c_size, _vp, _vp, _OPTP]),
+    "rsvd_svd_vjp_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int,
+                                              _OPTP]),
+    "rsvd_svd_vjp": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64, _c_int, _vp, _c_i64,
+                              _vp, _c_i64, _vp, _vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _vp, _vp,
+                              _c_i64, _vp, _c_size, _vp, _vp, _OPTP]),
     "rsvd_qb_adaptive_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int,
                                                   _OPTP]),
     "rsvd_qb_adaptive": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, ctypes.c_double, _c_int,
@@ -363,6 +389,178 @@ def cur(A, k, p, q, seed, opts=None, check=True):
     if check:
         check_info(info, "rsvd_cur")
     return Jc, Ir, U
+
+
+def svd_tol(A, kmax, p, q, tol, seed, opts=None, check=True):
+    """SVD to a tolerance (Sec. 2.6): (U, S, V) of rank r, the number of
+    singular values above tol (at least 1), from a sketch of kmax + p columns."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    U = torch.empty(m, kmax, dtype=_out_dtype(A.dtype), device=A.device)
+    V = torch.empty(n, kmax, dtype=_out_dtype(A.dtype), device=A.device)
+    S = torch.empty(kmax, dtype=torch.float64, device=A.device)
+    ws = lib().rsvd_svd_workspace_size(m, n, kmax, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_svd_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    rank = ctypes.c_int(0)
+    st = lib().rsvd_svd_tol(m, n, kmax, p, q, float(tol), seed, dt, _ptr(A), A.stride(0), _ptr(U),
+                            kmax, _ptr(S), _ptr(V), kmax, ctypes.byref(rank), _ptr(W), W.numel(),
+                            _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_svd_tol")
+    if check:
+        check_info(info, "rsvd_svd_tol")
+    r = rank.value
+    return U[:, :r], S[:r], V[:, :r]
+
+
+def id_tol(A, kmax, p, q, tol, seed, opts=None, check=True):
+    """Column ID to a tolerance (Sec. 2.6): (J, T, k) with ||S22||_F < tol after
+    k <= kmax pivoted-QR steps of the sketch B (l = kmax + p)."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    J = torch.empty(n, dtype=torch.int32, device=A.device)
+    T = torch.empty(kmax, n - 1, dtype=_out_dtype(A.dtype), device=A.device)
+    ws = lib().rsvd_id_tol_workspace_size(m, n, kmax, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_id_tol_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    rank = ctypes.c_int(0)
+    st = lib().rsvd_id_tol(m, n, kmax, p, q, float(tol), seed, dt, _ptr(A), A.stride(0), _ptr(J),
+                           _ptr(T), T.stride(0), ctypes.byref(rank), _ptr(W), W.numel(),
+                           _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_id_tol")
+    if check:
+        check_info(info, "rsvd_id_tol")
+    k = rank.value
+    return J, T[:k, : n - k], k
+
+
+def cur_tol(A, kmax, p, q, tol, seed, opts=None, check=True):
+    """CUR to a tolerance: (Jc, Ir, U, k) on the column ID of id_tol."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    Jc = torch.empty(kmax, dtype=torch.int32, device=A.device)
+    Ir = torch.empty(kmax, dtype=torch.int32, device=A.device)
+    U = torch.empty(kmax, kmax, dtype=_out_dtype(A.dtype), device=A.device)
+    ws = lib().rsvd_cur_tol_workspace_size(m, n, kmax, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_cur_tol_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    rank = ctypes.c_int(0)
+    st = lib().rsvd_cur_tol(m, n, kmax, p, q, float(tol), seed, dt, _ptr(A), A.stride(0),
+                            _ptr(Jc), _ptr(Ir), _ptr(U), kmax, ctypes.byref(rank), _ptr(W),
+                            W.numel(), _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_cur_tol")
+    if check:
+        check_info(info, "rsvd_cur_tol")
+    k = rank.value
+    return Jc[:k], Ir[:k], U[:k, :k], k
+
+
+def id_left(A, k, p, q, seed, opts=None, check=True):
+    """Column ID from the left sketch Omega~ A (A^T A)^q (Sec. 3.5, Alg. 6): (J, T)."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    J = torch.empty(n, dtype=torch.int32, device=A.device)
+    T = torch.empty(k, max(n - k, 1), dtype=_out_dtype(A.dtype), device=A.device)
+    ws = lib().rsvd_id_left_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_id_left_workspace_size")
+    W = _work(ws, A.device)
+    info = _info(A.device)
+    st = lib().rsvd_id_left(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(J), _ptr(T),
+                            T.stride(0), _ptr(W), W.numel(), _ptr(info), _stream(),
+                            _opts_ptr(opts))
+    _raise(st, "rsvd_id_left")
+    if check:
+        check_info(info, "rsvd_id_left")
+    return J, T[:, : n - k]
+
+
+def svd_vjp(A, k, p, q, seed, gU, gS, gV, opts=None, check=True, with_outputs=False):
+    """Cotangent of A for (U, S, V) = svd(A, k, p, q, seed) given the cotangents
+    of U, S and V (rsvd_svd_vjp; Omega fixed, the forward replayed from A and
+    the seed).  gU, gS, gV may be None (zero).  Returns gA, or (gA, U, S, V)."""
+    torch = _torch()
+    _check_matrix(A, "A")
+    m, n = A.shape
+    dt = _dtype_code(A)
+    dev = A.device
+    gU = torch.zeros(m, k, dtype=A.dtype, device=dev) if gU is None else \
+        gU.to(A.dtype).contiguous()
+    gV = torch.zeros(n, k, dtype=A.dtype, device=dev) if gV is None else \
+        gV.to(A.dtype).contiguous()
+    gS = torch.zeros(k, dtype=torch.float64, device=dev) if gS is None else \
+        gS.to(torch.float64).contiguous()
+    gA = torch.empty(m, n, dtype=A.dtype, device=dev)
+    U = V = S = None
+    if with_outputs:
+        U = torch.empty(m, k, dtype=A.dtype, device=dev)
+        V = torch.empty(n, k, dtype=A.dtype, device=dev)
+        S = torch.empty(k, dtype=torch.float64, device=dev)
+    ws = lib().rsvd_svd_vjp_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
+    if ws == 0:
+        raise RsvdError(1, "rsvd_svd_vjp_workspace_size")
+    W = _work(ws, dev)
+    info = _info(dev)
+    st = lib().rsvd_svd_vjp(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(gU), k, _ptr(gS),
+                            _ptr(gV), k, _ptr(gA), n, _ptr(U), k, _ptr(S), _ptr(V), k, _ptr(W),
+                            W.numel(), _ptr(info), _stream(), _opts_ptr(opts))
+    _raise(st, "rsvd_svd_vjp")
+    if check:
+        check_info(info, "rsvd_svd_vjp")
+    return (gA, U, S, V) if with_outputs else gA
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class RSVD(torch.autograd.Function):
+        """(U, S, V) = rsvd_svd(A) as a differentiable function of A (Omega fixed).
+
+        The forward runs rsvd_svd and keeps only A; the backward calls
+        rsvd_svd_vjp, which replays the forward from A and the seed instead of
+        storing the power iteration's intermediates."""
+
+        @staticmethod
+        def forward(ctx, A, k, p, q, seed, opts):
+            U, S, V = svd(A, k, p, q, seed, opts)
+            ctx.save_for_backward(A)
+            ctx.args = (k, p, q, seed, opts)
+            return U, S, V
+
+        @staticmethod
+        def backward(ctx, gU, gS, gV):
+            (A,) = ctx.saved_tensors
+            k, p, q, seed, opts = ctx.args
+            gA = svd_vjp(A.detach().contiguous(), k, p, q, seed, gU, gS, gV, opts)
+            return gA, None, None, None, None, None
+
+    return RSVD
+
+
+_RSVD = None
+
+
+def svd_autograd(A, k, p, q, seed, opts=None):
+    """Differentiable randomized SVD: (U, S, V) whose backward is the library's
+    adjoint of Alg. 5 (rsvd_svd_vjp)."""
+    global _RSVD
+    if _RSVD is None:
+        _RSVD = _make_autograd()
+    return _RSVD.apply(A, k, p, q, seed, opts)
 
 
 class Plan:

@@ -147,8 +147,8 @@ struct OmegaGen;
 template <>
 struct OmegaGen<float> {
   __device__ __forceinline__ static void quad(uint64_t seed, uint32_t row, uint32_t quad,
-                                              float z[4]) {
-    gauss4_f(omega_words(seed, row, quad), z);
+                                              float z[4], uint32_t tag = 0) {
+    gauss4_f(omega_words(seed, row, quad, tag), z);
 #pragma unroll
     for (int t = 0; t < 4; ++t) z[t] = round_bf16(z[t]);
   }
@@ -157,8 +157,8 @@ struct OmegaGen<float> {
 template <>
 struct OmegaGen<double> {
   __device__ __forceinline__ static void quad(uint64_t seed, uint32_t row, uint32_t quad,
-                                              double z[4]) {
-    gauss4_d(omega_words(seed, row, quad), z);
+                                              double z[4], uint32_t tag = 0) {
+    gauss4_d(omega_words(seed, row, quad, tag), z);
   }
 };
 

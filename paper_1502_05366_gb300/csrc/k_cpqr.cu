@@ -168,14 +168,32 @@ __global__ void __launch_bounds__(PT) cpqr_kernel(CpqrArgs a) {
     }
   __syncthreads();
 
+  const bool tolmode = a.tol2 > 0.0;
+  __shared__ double s_wsum[PT / 32];
+  __shared__ double s_tot;
+  int steps = a.k;
   for (int j = 0; j < a.k; ++j) {
     Top2 loc{-1.0, 0x7fffffffffffffffLL, -1.0};
+    double cs = 0.0;
     for (int64_t c = c0 + tid; c < c1; c += PT) {
       const double x = nrm[c];
-      if (x >= 0.0) loc = merge_top2(loc, Top2{x, c, -1.0});
+      if (x >= 0.0) {
+        loc = merge_top2(loc, Top2{x, c, -1.0});
+        cs += x;
+      }
     }
     loc = block_top2(loc);
     const int slot = j & 1;
+    if (tolmode) {   // the CTA's sum of residual norms^2, in a fixed order
+      cs = warp_sum(cs);
+      if (lane == 0) s_wsum[warp] = cs;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nwarp; ++w) t += s_wsum[w];
+        a.psum[(size_t)slot * G + blockIdx.x] = t;
+      }
+    }
     if (tid == 0) {
       a.pval[(size_t)slot * 2 * G + 2 * blockIdx.x] = loc.b1;
       a.pval[(size_t)slot * 2 * G + 2 * blockIdx.x + 1] = loc.b2;
@@ -191,6 +209,20 @@ __global__ void __launch_bounds__(PT) cpqr_kernel(CpqrArgs a) {
                                     (size_t)slot * G + b),
                              __ldcg(a.pval + (size_t)slot * 2 * G + 2 * b + 1)});
     g = block_top2(g);
+    if (tolmode && j >= 1) {
+      // ||S22(j)||_F^2: every CTA adds the G partials in the same order
+      if (warp == 0) {
+        double t = 0.0;
+        for (int b = lane; b < G; b += 32) t += __ldcg(a.psum + (size_t)slot * G + b);
+        t = warp_sum(t);
+        if (lane == 0) s_tot = t;
+      }
+      __syncthreads();
+      if (s_tot < a.tol2) {
+        steps = j;
+        break;
+      }
+    }
     const int64_t p = g.i1;
     if (p < 0 || p >= n) {  // no active column left (cannot happen for k <= min(r, n))
       set_info(a.d_info, RSVD_ERR_NUMERIC);
@@ -288,6 +320,7 @@ __global__ void __launch_bounds__(PT) cpqr_kernel(CpqrArgs a) {
     }
     __syncthreads();
   }
+  if (a.k_out && blockIdx.x == 0 && tid == 0) *a.k_out = steps;
 }
 
 cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
@@ -507,9 +540,10 @@ struct CpqrDfCol {
   bool zero;
   int lane, warp;
 
-  // Returns (on lane 0) the warp's best two residual norms after the step.
+  // Returns (on lane 0) the warp's best two residual norms after the step and
+  // adds them all, as doubles, to `acc` (lane 0; read in tolerance mode only).
   template <int S, int NWARP>
-  __device__ __forceinline__ Top2F run() const {
+  __device__ __forceinline__ Top2F run(double& acc) const {
     const DF none{-1.f, 0.f};
     Top2F best{none, 0x7fffffffffffffffLL, none};
     const float tol3z = 1.4901161193847656e-08f;   // sqrt(eps_fp64), as in the FP64 kernel
@@ -623,6 +657,7 @@ struct CpqrDfCol {
         const float2 nv = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
         nrm2[c - cbase] = nv;
         best = merge_top2f(best, Top2F{DF{nv.x, nv.y}, c, none});
+        acc += (double)nv.x + (double)nv.y;
       }
     }
     // the warp's first column of the next step into L1 (stored rows j + 1 ..)
@@ -733,11 +768,15 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
   __shared__ int64_t s_p;                   // this step's pivot column
   __shared__ float s_g[4];                  // the step's best two norms (for the gaps)
   __shared__ int s_abort;
+  __shared__ int s_stop;                    // tolerance mode: ||S22(j)||_F below tol
+  __shared__ double s_wsum[NWARP];          // per-warp sums of residual norms^2
+  const bool tolmode = a.tol2 > 0.0;
   const DF none{-1.f, 0.f};
 
   // exact initial squared norms, one warp per column; each warp keeps its best two
   {
     Top2F best{none, 0x7fffffffffffffffLL, none};
+    double acc = 0.0;
     for (int64_t c = c0 + warp; c < c1; c += NWARP) {
       float sh = 0.f, se = 0.f;
       for (int i = lane; i < r; i += 32) df_acc_sqr(Wh[c * r + i], Wl[c * r + i], sh, se);
@@ -748,9 +787,11 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
         nrm2[c - cbase] = make_float2(h, l);
         nref[c - cbase] = h;
         best = merge_top2f(best, Top2F{DF{h, l}, c, none});
+        acc += (double)h + (double)l;
       }
     }
     if (lane == 0) {
+      s_wsum[warp] = acc;
       s_wt[warp][0] = best.b1.h;
       s_wt[warp][1] = best.b1.l;
       s_wt[warp][2] = best.b2.h;
@@ -763,9 +804,13 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
       a.J[c] = (int32_t)c;
       a.where[c] = c;
     }
-  if (tid == 0) s_abort = 0;
+  if (tid == 0) {
+    s_abort = 0;
+    s_stop = 0;
+  }
   __syncthreads();
 
+  int steps = a.k;
   for (int j = 0; j < a.k; ++j) {
     const int len = r - j;
     // ---- warp 0: CTA proposal, grid barrier, global pivot, Householder vector ----
@@ -775,6 +820,12 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
         v = Top2F{DF{s_wt[lane][0], s_wt[lane][1]}, s_wi[lane], DF{s_wt[lane][2], s_wt[lane][3]}};
       v = warp_top2f(v);
       const int slot = j & 1;
+      if (tolmode) {
+        // the CTA's sum of residual norms^2 (warps in a fixed order)
+        double ws = lane < NWARP ? s_wsum[lane] : 0.0;
+        ws = warp_sum(ws);
+        if (lane == 0) a.psum[(size_t)slot * G + blockIdx.x] = ws;
+      }
       if (lane == 0) {
         pv[(size_t)slot * G + blockIdx.x] = make_float4(v.b1.h, v.b1.l, v.b2.h, v.b2.l);
         a.pidx[(size_t)slot * G + blockIdx.x] = v.i1;
@@ -802,7 +853,18 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
         }
         g = warp_top2f(g);
         const int64_t p = g.i1;
-        if (p < 0 || p >= n) {
+        bool stop = false;
+        if (tolmode && j >= 1) {
+          // ||S22(j)||_F^2 = the sum of all residual norms^2: every CTA adds
+          // the G partials in the same order, so all take the same decision
+          double t = 0.0;
+          for (int b = lane; b < G; b += 32) t += __ldcg(a.psum + (size_t)slot * G + b);
+          t = __shfl_sync(0xffffffffu, warp_sum(t), 0);
+          stop = t < a.tol2;
+        }
+        if (stop) {
+          if (lane == 0) s_stop = 1;
+        } else if (p < 0 || p >= n) {
           if (lane == 0) {
             set_info(a.d_info, RSVD_ERR_NUMERIC);
             s_abort = 1;
@@ -863,6 +925,10 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
     }
     __syncthreads();
     if (s_abort) return;
+    if (s_stop) {
+      steps = j;
+      break;
+    }
     const int64_t p = s_p;
     const float tauh = s_th, taul = s_tl;
     const bool zero = s_zero != 0;
@@ -888,17 +954,19 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
     CpqrDfCol cp{Wh, Wl, nrm2, nref, cbase, svh, svl, r, j, len, p, c0, c1, tauh, taul, zero,
                  lane, warp};
     Top2F best;
+    double acc = 0.0;
     switch ((nt + SLOT_STEP<RPL>() - 1) / SLOT_STEP<RPL>()) {
-      case 1: best = cp.template run<1 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 2: best = cp.template run<2 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 3: best = cp.template run<3 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 4: best = cp.template run<4 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 5: best = cp.template run<5 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 6: best = cp.template run<6 * SLOT_STEP<RPL>(), NWARP>(); break;
-      case 7: best = cp.template run<7 * SLOT_STEP<RPL>(), NWARP>(); break;
-      default: best = cp.template run<8 * SLOT_STEP<RPL>(), NWARP>(); break;
+      case 1: best = cp.template run<1 * SLOT_STEP<RPL>(), NWARP>(acc); break;
+      case 2: best = cp.template run<2 * SLOT_STEP<RPL>(), NWARP>(acc); break;
+      case 3: best = cp.template run<3 * SLOT_STEP<RPL>(), NWARP>(acc); break;
+      case 4: best = cp.template run<4 * SLOT_STEP<RPL>(), NWARP>(acc); break;
+      case 5: best = cp.template run<5 * SLOT_STEP<RPL>(), NWARP>(acc); break;
+      case 6: best = cp.template run<6 * SLOT_STEP<RPL>(), NWARP>(acc); break;
+      case 7: best = cp.template run<7 * SLOT_STEP<RPL>(), NWARP>(acc); break;
+      default: best = cp.template run<8 * SLOT_STEP<RPL>(), NWARP>(acc); break;
     }
     if (lane == 0) {
+      s_wsum[warp] = acc;
       s_wt[warp][0] = best.b1.h;
       s_wt[warp][1] = best.b1.l;
       s_wt[warp][2] = best.b2.h;
@@ -908,6 +976,7 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
     if (p >= c0 && p < c1 && tid == 0) nrm2[p - cbase] = make_float2(-1.f, 0.f);
     __syncthreads();
   }
+  if (a.k_out && blockIdx.x == 0 && tid == 0) *a.k_out = steps;
 }
 
 template <int RPL, int NT>

@@ -7,8 +7,11 @@
 namespace rsvd {
 
 // ----- Philox / Omega (k_philox.cu) ----------------------------------------
+// tag: the counter's third word (0 = Omega of the right sketch, 1 = the left
+// test matrix Omega~ of Sec. 3.5, stored transposed: n here is its column count m)
 template <typename T>
-cudaError_t launch_omega(int64_t n, int l, uint64_t seed, T* Om, int64_t ldo, cudaStream_t s);
+cudaError_t launch_omega(int64_t n, int l, uint64_t seed, T* Om, int64_t ldo, cudaStream_t s,
+                         uint32_t tag = 0);
 cudaError_t launch_omega_words(int64_t n, int l, uint64_t seed, uint32_t* out, cudaStream_t s);
 
 // ----- SIMT GEMMs (k_simt.cu) ----------------------------------------------
@@ -138,6 +141,13 @@ struct CpqrArgs {
   int nrm_local;    // set by the launcher: residual norms in shared memory (double-float kernel)
   long long spin_limit;  // set by the launcher: bound of each grid-barrier wait (SM clocks)
   int withhold;     // set by the launcher: CTA 0 skips its first arrival (test aid)
+  // Tolerance mode (Sec. 2.6): with tol2 > 0 the factorisation stops before
+  // step j >= 1 once the sum of the residual column norms^2, ||S22(j)||_F^2,
+  // is below tol2 (at the latest after k steps); *k_out (device) receives the
+  // number of steps taken.  psum: 2 * 1024 doubles of per-CTA partial sums.
+  double tol2;
+  int* k_out;
+  double* psum;
 };
 cudaError_t launch_cpqr(const CpqrArgs& a, int* grid_out, cudaStream_t s);
 // Double-float arithmetic on the same working area reinterpreted as two float
@@ -293,6 +303,25 @@ struct BSign {
   int k;
 };
 cudaError_t launch_sign_batched(const BSign* tasks, int batch, cudaStream_t s);
+
+// ----- adjoint of Alg. 5 (k_vjp.cu) ---------------------------------------
+// X (L x L) = diag(gs) + (F o (Gu - Gu^T)) diag(s) + diag(s) (F o (Gv - Gv^T)),
+// F_ij = 1 / (s_j^2 - s_i^2), on the leading l x l block (gs: k entries, may
+// be null); zero padding.
+template <typename T>
+cudaError_t launch_svd_vjp_core(int l, int L, int k, const double* s, const double* gs,
+                                const T* Gu, const T* Gv, int64_t ldg, T* X, int64_t ldx,
+                                cudaStream_t st);
+// out (L x L) = sym(P1 - P2): upper triangle of M = P1 - P2 mirrored below
+// (P1 may be null); zero padding.
+template <typename T>
+cudaError_t launch_sym_upper(int l, int L, const T* P1, const T* P2, int64_t ldp, T* out,
+                             int64_t ldo, cudaStream_t st);
+// dst(:, 0:cols) = scale * src(:, 0:cols), columns with signs[j] < 0 negated
+// once more (signs may be null).
+template <typename T>
+cudaError_t launch_pack_cols(int64_t rows, int cols, const T* src, int64_t lds, T* dst,
+                             int64_t ldd, T scale, const int* signs, cudaStream_t st);
 
 // ----- blocked adaptive QB (k_adaptive.cu) --------------------------------
 // X (rows x cols, ld ldx) <- X - Q Bt^T with Q rows x K (ld ldq) and Bt cols x K

@@ -94,11 +94,13 @@ def _orthonormal_np(rng, rows, cols):
     return Q * np.sign(np.diag(R))[None, :]
 
 
-def make_matrix_np(m, n, sigma, noise=0.0, seed=0, dtype="float64"):
+def make_matrix_np(m, n, sigma, noise=0.0, seed=0, dtype="float64", factors=False):
     """A = U diag(sigma) V^T (+ noise * N(0,1)) built in float64, stored as dtype.
 
     dtype "bfloat16" returns a float32 array holding bf16-representable values
     (round to nearest even), i.e. the stored bf16 matrix promoted to fp32.
+    With factors=True the result is (A, U, V): the orthonormal factors the
+    matrix was built from (float64).
     """
     sigma = np.asarray(sigma, dtype=np.float64)
     r = sigma.size
@@ -109,15 +111,16 @@ def make_matrix_np(m, n, sigma, noise=0.0, seed=0, dtype="float64"):
     if noise:
         A += noise * rng.standard_normal((m, n))
     if dtype in ("float64", np.float64):
-        return A
+        return (A, U, V) if factors else A
     A32 = A.astype(np.float32)
     if dtype in ("float32", np.float32):
-        return A32
+        return (A32, U, V) if factors else A32
     if dtype == "bfloat16":
         b = A32.view(np.uint32).astype(np.uint64)
         b = ((b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1)))
              >> np.uint64(16)) << np.uint64(16)
-        return b.astype(np.uint32).view(np.float32)
+        Ab = b.astype(np.uint32).view(np.float32)
+        return (Ab, U, V) if factors else Ab
     raise ValueError(dtype)
 
 
