@@ -548,6 +548,47 @@ def batched_line(rs, args, world, dev, peaks, peak_kind, name="c4_f32_batched512
     }
 
 
+def adaptive_line(rs, A, cfg, args, world, dev, peaks, peak_kind, b=64, M=4, q=1):
+    """The blocked adaptive QB (Alg. 7) on the workload's matrix: M blocks of b
+    columns (tolerance 0, so all M blocks run), q power steps per block.  Each
+    call gets a fresh copy of A (the algorithm overwrites A with its residual),
+    made outside the timed region; CUDA events around the call, which
+    synchronises with the host once per block to test the tolerance."""
+    import torch
+    m, n = cfg["m"], cfg["n"]
+    seed = cfg["omega_seed"]
+    reps = max(1, min(args.steps, 3))
+    times = []
+    for r in range(reps + 1):
+        Aw = A.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Q, Bt, resid = rs.qb_adaptive(Aw, b, M, q, 0.0, seed, relative=False, overwrite=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if r > 0:                      # the first call is an untimed warm-up
+            times.append(e0.elapsed_time(e1))
+        del Aw
+    ms = max_over_ranks(float(np.median(times)), world, dev)
+    es = ELEM[cfg["dtype"]]
+    # per block: sketch, q power steps (2 passes each), Bt: 2q + 2 reads of A;
+    # the update reads and writes A; plus the norm of A_in
+    bytes_ = M * ((2 * q + 2) + 2) * a_pass_bytes(m, n, es) + a_pass_bytes(m, n, es)
+    flops = M * (2.0 * m * n * b * (2 * q + 2) + 2.0 * m * n * b)
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    r = resid.cpu().numpy()
+    return {"what": "rsvd_qb_adaptive (Alg. 7): %d blocks of b = %d, q = %d, tolerance 0" % (M, b, q),
+            "ms_per_call": ms, "calls_timed": len(times),
+            "tflops": world * flops / (ms * 1e-3) / 1e12,
+            "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_kind + " STREAM-style copy",
+                    "work": "per block 2q + 2 reads of A and the update's read + write, plus "
+                            "the first norm read"},
+            "residual_norms": [float(x) for x in r]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -563,6 +604,8 @@ def main():
                     help="skip the BF16-storage (mixed precision) measurement")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-workload (512 small problems) measurement")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip the blocked adaptive QB (Alg. 7) measurement")
     args = ap.parse_args()
 
     from synth import config as get_config
@@ -672,6 +715,10 @@ def main():
     if not args.no_batched:
         batched = batched_line(rs, args, world, dev, peaks, peak_kind)
 
+    adaptive = None
+    if not args.no_adaptive and tdt == torch.float32:
+        adaptive = adaptive_line(rs, A, cfg, args, world, dev, peaks, peak_kind)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -706,6 +753,7 @@ def main():
             "cpu_baseline": cpu,
             "mixed": mixed,
             "batched": batched,
+            "adaptive_qb": adaptive,
         }
         print(json.dumps(line))
     if world > 1:

@@ -76,6 +76,9 @@ struct Ctx {
   } while (0)
 
 static inline int padL(int l) { return (int)round_up(l, 16); }
+// K-chunks (of 32) per tensor-core accumulation run in the products whose scale
+// matters (Bt = A^* Q): 2048 terms keep the accumulation's drift near 3e-6.
+constexpr int kDrainQB = 64;
 static inline int64_t pad8(int64_t r) { return round_up(r, 8); }
 
 // ------------------------------------------------------------------------
@@ -151,13 +154,17 @@ struct Engine {
   }
 
   // Z (rows x L) = A^T W with A (K x rows).
+  // drain > 0: the tensor-core accumulation runs hold at most `drain` K-chunks
+  // of 32 (see tc_unit_kernel); used where the result's scale matters, not
+  // only its span (the QB projection Bt = A^* Q).
   rsvd_status gemm_t(int64_t rows, int64_t K, int L, const T* A, int64_t lda, const Split* w,
                      const T* Wsimt, int64_t ldws, T* out, int64_t ldo, int ncols,
                      Split* out_split, float* part, T* slabs, const int* skip, bool gram = false,
-                     bool a_bf16 = false) {
+                     bool a_bf16 = false, int drain = 0) {
     if (tc) {
       TcGemm g{};
       g.form = 1;
+      g.drain = drain;
       g.a_bf16 = a_bf16 ? 1 : 0;
       g.rows = rows;
       g.K = K;
@@ -413,9 +420,10 @@ struct Engine {
     st = orth(m, l, L, b.Y, b.Ytmp, &b.ys, b.ob, b.part, b.slabs, false);
     if (st != RSVD_OK) return st;
     std::swap(b.Y, b.Ytmp);
-    // Bt = A^* Q (Alg. 5)
+    // Bt = A^* Q (Alg. 5); its scale sets the singular values: bounded
+    // accumulation runs
     st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr, false,
-                c.abf != 0);
+                c.abf != 0, kDrainQB);
     return st;
   }
 
@@ -496,7 +504,7 @@ struct Engine {
     }
     // Bt_t = A^* Q_t (B_t = Q_t^* A)
     st = gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr,
-                false);
+                false, false, kDrainQB);
     if (st != RSVD_OK) return st;
     LK(launch_copy2d<T, T>(m, bs, b.Y, L, Qo + done, ldq, c.stream));
     LK(launch_copy2d<T, T>(n, bs, b.Z, L, Bto + done, ldbt, c.stream));

@@ -594,7 +594,18 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   if (tc_unit_supported(g)) return launch_tc_unit(g, s);
   int64_t tiles, kiters, total, G;
   int maxseg;
-  sk_plan(g.rows, g.K, BM, BK, device_sm_count(), &tiles, &kiters, &total, &G, &maxseg);
+  const int sms = device_sm_count();
+  sk_plan(g.rows, g.K, BM, BK, sms, &tiles, &kiters, &total, &G, &maxseg);
+  // Short contractions (the R^-1 apply of CholeskyQR, K = L): one CTA per
+  // output tile instead of stream-K, so that no tile is split and the reduce
+  // launch disappears (a few waves of short CTAs cost less than the split
+  // tiles' partial writes and the extra launch)
+  bool whole_tiles = false;
+  if (kiters <= 8 && tiles > sms && tiles <= 4 * (int64_t)sms) {
+    G = tiles;
+    maxseg = 1;
+    whole_tiles = true;
+  }
   TcParams P;
   P.rows = g.rows;
   P.K = g.K;
@@ -672,8 +683,10 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
     return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
   // fixed-order reduction of the tiles split between CTAs
-  e = launch_tc_reduce(P, (int)G, s);
-  if (e != cudaSuccess) return e;
+  if (!whole_tiles) {
+    e = launch_tc_reduce(P, (int)G, s);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

@@ -22,6 +22,14 @@
 //               K-major 64-byte-swizzled tiles in shared memory; then the
 //               epilogue of their tile (t = (warp - 4) / 4, TMEM lane quadrant
 //               warp % 4) into the output or a stream-K partial
+// Bounded accumulation runs (P.drain > 0): the tensor cores' fp32 accumulation
+// into TMEM is not rounded to nearest, and over a long contraction its error
+// drifts one way (over the 50000-row contraction of Bt = A^* Q a TMEM
+// accumulator holding ~800 K-chunks came out ~6.5e-5 small in relative
+// terms).  With drain = D the accumulator holds at most D K-chunks; the
+// epilogue then adds it into the CTA's partial tile in fp32 with round to
+// nearest, and the MMAs restart on a fresh accumulator.
+//
 // Every mbarrier wait is bounded: on expiry the kernel records
 // RSVD_ERR_TIMEOUT, the roles leave their loops, the producers wait (bounded)
 // for their copies in flight, TMEM is freed and the CTA returns.
@@ -193,15 +201,16 @@ __global__ void __launch_bounds__(U_THREADS, 1)
     // ------------------------------- MMA issuer -------------------------------
     if (lane == 0) {
       const uint32_t idesc = make_idesc(U_BM, L);
-      int64_t seg = -1;
+      int64_t run = -1;   // accumulation runs: one per segment, or `drain` K-chunks each
+      int rc = 0;         // K-chunks in the current run
       int64_t kc = it0 % P.kiters;
       int bs = 0;
       uint32_t bph = 0;
       for (int64_t it = it0; it < it1; ++it) {
-        const bool seg_start = (it == it0) || (kc == 0);
-        if (seg_start) {
-          ++seg;
-          if (seg > 0 && !mbar_wait(acc_empty, (uint32_t)((seg - 1) & 1), abort_flag, P.d_info))
+        if (it == it0 || kc == 0) rc = 0;
+        if (rc == 0) {
+          ++run;
+          if (run > 0 && !mbar_wait(acc_empty, (uint32_t)((run - 1) & 1), abort_flag, P.d_info))
             break;
         }
         if (!mbar_wait(&aready[bs], bph, abort_flag, P.d_info)) break;
@@ -213,7 +222,7 @@ __global__ void __launch_bounds__(U_THREADS, 1)
         for (int kk = 0; kk < U_BK / 16; ++kk) {
           const uint64_t bw0 = sw64_desc(wbase + 32u * kk);
           const uint64_t bw1 = sw64_desc(wbase + (uint32_t)WT + 32u * kk);
-          const uint32_t acc0 = (seg_start && kk == 0) ? 0u : 1u;
+          const uint32_t acc0 = (rc == 0 && kk == 0) ? 0u : 1u;
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
             const uint32_t d = tmem + U_ACC2 * (uint32_t)t;
@@ -225,8 +234,12 @@ __global__ void __launch_bounds__(U_THREADS, 1)
           }
         }
         mma_commit(&bdone[bs]);
+        ++rc;
         const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
-        if (seg_end) mma_commit(acc_full);
+        if (seg_end || (P.drain > 0 && rc == P.drain)) {
+          mma_commit(acc_full);
+          rc = 0;
+        }
         if (++kc == P.kiters) kc = 0;
         if (++bs == U_BST) {
           bs = 0;
@@ -242,7 +255,8 @@ __global__ void __launch_bounds__(U_THREADS, 1)
     const int rr = t * U_BM + r;            // row within the unit
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const uint32_t acc = tmem + U_ACC2 * (uint32_t)t;
-    int64_t seg = -1;
+    int64_t run = -1;     // accumulation runs, counted as the MMA issuer counts them
+    int rc = 0, rin = 0;  // K-chunks in the run; runs of this segment already drained
     int64_t unit = it0 / P.kiters, kc = it0 - unit * P.kiters;
     const int64_t unit0 = unit;
     bool whole = false;
@@ -250,9 +264,11 @@ __global__ void __launch_bounds__(U_THREADS, 1)
     uint32_t fph = 0, bph = 0;
     for (int64_t it = it0; it < it1; ++it) {
       if (it == it0 || kc == 0) {
-        ++seg;
         whole = (kc == 0);
+        rc = 0;
+        rin = 0;
       }
+      if (rc == 0) ++run;
       if (!mbar_wait(&ffull[fs], fph, abort_flag, P.d_info)) break;
       const unsigned char* st = fring + fs * U_FBYTES;
       uint32_t hi[16], lo[16];
@@ -307,17 +323,29 @@ __global__ void __launch_bounds__(U_THREADS, 1)
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&aready[bs]);
+      ++rc;
       const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
-      if (seg_end) {
-        if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag, P.d_info)) break;
+      if (seg_end || (P.drain > 0 && rc == P.drain)) {
+        if (!mbar_wait(acc_full, (uint32_t)(run & 1), abort_flag, P.d_info)) break;
         tc_fence_after();
         const int64_t gr = unit * U_ROWS + rr;
-        if (whole && kc + 1 == P.kiters) {
-          // this CTA holds the whole unit: final rows (+ transposed bf16 split)
+        // the CTA's partial tile of this segment (column-major, 256 rows): it
+        // receives every run but the last of a whole unit; rows are thread-owned
+        float* slot =
+            P.part + ((int64_t)blockIdx.x * P.maxseg + (unit - unit0)) * (int64_t)U_ROWS * L;
+        if (seg_end && whole && kc + 1 == P.kiters) {
+          // this CTA holds the whole unit: final rows (+ transposed bf16 split),
+          // the earlier runs' sum added from the partial tile
           for (int c0 = 0; c0 < L; c0 += 16) {
             uint32_t v[16];
             tmem_ld16(lane_base + acc + (uint32_t)c0, v);
             tmem_wait_ld();
+            if (rin > 0) {
+#pragma unroll
+              for (int c = 0; c < 16; ++c)
+                v[c] = __float_as_uint(slot[(int64_t)(c0 + c) * U_ROWS + rr] +
+                                       __uint_as_float(v[c]));
+            }
             if (gr < P.rows) {
               float* orow = P.out + gr * P.ldo + c0;
               const bool vec =
@@ -345,20 +373,25 @@ __global__ void __launch_bounds__(U_THREADS, 1)
             }
           }
         } else {
-          float* dst =
-              P.part + ((int64_t)blockIdx.x * P.maxseg + (unit - unit0)) * (int64_t)U_ROWS * L;
+          // a partial segment's sum for the fixed-order reduce, or a bounded run
+          // drained mid-segment: the first run writes, later runs add (fp32,
+          // round to nearest, in run order)
           for (int c0 = 0; c0 < L; c0 += 16) {
             uint32_t v[16];
             tmem_ld16(lane_base + acc + (uint32_t)c0, v);
             tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-              dst[(int64_t)(c0 + c) * U_ROWS + rr] = __uint_as_float(v[c]);
+            for (int c = 0; c < 16; ++c) {
+              float* d = slot + (int64_t)(c0 + c) * U_ROWS + rr;
+              *d = rin > 0 ? *d + __uint_as_float(v[c]) : __uint_as_float(v[c]);
+            }
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty);
+        ++rin;
+        rc = 0;
       }
       if (++kc == P.kiters) {
         kc = 0;
@@ -438,6 +471,7 @@ cudaError_t launch_tc_unit(const TcGemm& g, cudaStream_t s) {
   P.ldt = g.ldt;
   P.skip = g.skip;
   P.d_info = g.d_info;
+  P.drain = g.drain;
 
   CUtensorMap ma, mw0, mw1;
   memset(&ma, 0, sizeof(ma));

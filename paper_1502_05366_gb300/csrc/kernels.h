@@ -218,6 +218,8 @@ struct TcGemm {
   int64_t ldt;
   const int* skip;      // when non-null and *skip == 1 the launch does nothing
   int* d_info;
+  int drain;            // stored-operand passes: K-chunks per TMEM accumulation run
+                        // (0 = one run per stream-K segment); see tc_unit_kernel
 };
 size_t tc_part_bytes(int64_t rows, int64_t K, int L);
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s);

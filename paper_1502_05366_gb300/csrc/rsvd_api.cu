@@ -751,8 +751,9 @@ static rsvd_status apply_impl(Ctx& c, const Opts& o, bool tc, int64_t m, int64_t
   if (!trans)
     return e.gemm_n(rows, K, L, A, lda, m, n, false, 0, L, &w, X, ldx, Y, ldy, l, nullptr, part,
                     nullptr, c.abf != 0);
+  // bounded accumulation runs: the result is returned to the caller as is
   return e.gemm_t(rows, K, L, A, lda, &w, X, ldx, Y, ldy, l, nullptr, part, slabs, nullptr, false,
-                  c.abf != 0);
+                  c.abf != 0, kDrainQB);
 }
 
 template <typename T>

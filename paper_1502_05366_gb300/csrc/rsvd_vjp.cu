@@ -192,7 +192,7 @@ static rsvd_status run_svd_vjp(Ctx& c, const Opts& o, bool tc, int64_t m, int64_
   std::swap(b.Y, b.Ytmp);                         // b.Y = Q
   LK(launch_copy2d<T, T>(L, L, b.ob.Racc, L, Rq, L, st));
   RUN(e.gemm_t(n, m, L, A, lda, &b.ys, b.Y, L, b.Z, L, L, &b.zs, b.part, b.slabs, nullptr,
-               false, abf));                      // b.Z = Bt
+               false, abf, kDrainQB));            // b.Z = Bt
   RUN(e.svd_prep(b, sb, n, l));                   // b.Ztmp = Qh, Racc = Rh
   LK(launch_copy2d<T, T>(L, L, b.ob.Racc, L, Rh, L, st));
   RUN(e.small_svd_jacobi(l, b.ob.Racc, L, sb, st));

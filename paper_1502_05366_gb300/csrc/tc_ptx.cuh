@@ -35,6 +35,10 @@ struct TcParams {
   int64_t ustride;
   int uoff, wmul, wadd;
   int qoff = 0;    // Omega: Philox quad index of the first output column (column / 4)
+  // bounded accumulation runs (tc_unit_kernel): when > 0, a TMEM accumulator
+  // takes at most `drain` K-chunks; the epilogue then adds it into the CTA's
+  // partial tile in fp32 (round to nearest) and the next run starts afresh
+  int drain = 0;
 };
 
 // Fixed-order sum of the stream-K partials of the tiles split between CTAs
