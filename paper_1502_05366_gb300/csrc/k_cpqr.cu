@@ -539,6 +539,7 @@ struct CpqrDfCol {
   float tauh, taul;
   bool zero;
   int lane, warp;
+  bool tol;           // tolerance mode: sum the residual norms^2 (lane 0)
 
   // Returns (on lane 0) the warp's best two residual norms after the step and
   // adds them all, as doubles, to `acc` (lane 0; read in tolerance mode only).
@@ -657,7 +658,7 @@ struct CpqrDfCol {
         const float2 nv = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
         nrm2[c - cbase] = nv;
         best = merge_top2f(best, Top2F{DF{nv.x, nv.y}, c, none});
-        acc += (double)nv.x + (double)nv.y;
+        if (tol) acc += (double)nv.x + (double)nv.y;
       }
     }
     // the warp's first column of the next step into L1 (stored rows j + 1 ..)
@@ -787,7 +788,7 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
         nrm2[c - cbase] = make_float2(h, l);
         nref[c - cbase] = h;
         best = merge_top2f(best, Top2F{DF{h, l}, c, none});
-        acc += (double)h + (double)l;
+        if (tolmode) acc += (double)h + (double)l;
       }
     }
     if (lane == 0) {
@@ -952,7 +953,7 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
     // instruction is spent on slots beyond the active rows
     const int nt = (len + 31) >> 5;
     CpqrDfCol cp{Wh, Wl, nrm2, nref, cbase, svh, svl, r, j, len, p, c0, c1, tauh, taul, zero,
-                 lane, warp};
+                 lane, warp, tolmode};
     Top2F best;
     double acc = 0.0;
     switch ((nt + SLOT_STEP<RPL>() - 1) / SLOT_STEP<RPL>()) {

@@ -13,6 +13,8 @@
 // (global memory beyond the limit).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -26,16 +28,28 @@ template <> __device__ __forceinline__ float jeps<float>() { return 5.9604645e-8
 template <> __device__ __forceinline__ double jeps<double>() { return 1.1102230246251565e-16; }
 }  // namespace
 
-// Cluster variant (fp32, 32 <= l <= 256): 8 CTAs of one thread-block cluster.
-constexpr int JC = 8;           // CTAs per cluster
-constexpr int JCT = 512;        // threads per CTA (16 warps: one per pair of a sub-round)
-static inline bool jacobi_use_cluster(int l, int elem) { return elem == 4 && l >= 32 && l <= 256; }
-__host__ __device__ inline int jc_width(int l) { return (l + 2 * JC - 1) / (2 * JC); }
+// Cluster variant (fp32): a thread-block cluster of JC CTAs, each holding two
+// blocks of w = ceil(l / 2 JC) columns and two inbox blocks in shared memory
+// (4 w l floats).  8 CTAs of 512 threads for 32 <= l <= 256; 16 CTAs (the
+// opt-in cluster size) of 1024 threads for 256 < l <= 672, where 4 w l floats
+// still fit a CTA's shared memory.  One warp per pair of a sub-round (w <= 21).
+constexpr int JC_MAX = 16;
+constexpr int JC_LMAX = 672;
+static inline int jacobi_cluster_size(int l, int elem) {
+  if (elem != 4 || l < 32 || l > JC_LMAX) return 0;
+  return l <= 256 ? 8 : 16;
+}
+static inline bool jacobi_use_cluster(int l, int elem) { return jacobi_cluster_size(l, elem) > 0; }
+__host__ __device__ inline int jc_width(int l, int jc) { return (l + 2 * jc - 1) / (2 * jc); }
 
 size_t jacobi_scratch_bytes(int l, int elem) {
-  if (jacobi_use_cluster(l, elem)) return (size_t)2 * JC * jc_width(l) * sizeof(double);
+  const int jc = jacobi_cluster_size(l, elem);
+  // the cluster kernel's sigma exchange, and the one-CTA kernel's fallback
+  // storage when the cluster cannot be placed
   const size_t b = (size_t)l * l * elem;
-  return b <= JSMEM_LIMIT ? 0 : b;
+  const size_t one = b <= JSMEM_LIMIT ? 0 : b;
+  if (jc) return std::max((size_t)2 * jc * jc_width(l, jc) * sizeof(double), one);
+  return one;
 }
 
 __device__ __forceinline__ void rr_pair(int r, int p, int N, int* a, int* b) {
@@ -266,7 +280,8 @@ __device__ __forceinline__ bool jc_rotate(float* xa, float* xb, int l, float tol
   return true;
 }
 
-__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JCT)
+template <int JC, int JCT>
+__global__ void __launch_bounds__(JCT)
     jacobi_cluster_kernel(int l, const float* __restrict__ M, int64_t ldm, float* __restrict__ Uh,
                           int64_t lduh, double* __restrict__ Sh, double* __restrict__ sig,
                           int max_sweeps, int* d_info) {
@@ -278,7 +293,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JCT)
   __shared__ int s_in[2];                    // this CTA's current inbox buffers (top, bottom)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NWARP = JCT / 32;
-  const int w = jc_width(l);
+  const int w = jc_width(l, JC);
   const int bsz = w * l;                     // floats per block, column-major X[a*l + i]
   // buffer roles (indices into the four block buffers)
   int iT = 0, iB = 1, inT = 2, inB = 3;
@@ -569,6 +584,52 @@ cudaError_t launch_small_svd_batched(const BSvd* tasks, int batch, int lmax, int
   return cudaGetLastError();
 }
 
+// The cluster kernel through cudaLaunchKernelEx (cluster size set at launch;
+// 16 needs the non-portable size opt-in).  *placed = false, and nothing is
+// launched, when the device cannot hold one such cluster.
+static cudaError_t launch_jacobi_cluster(int jc, int l, const float* M, int64_t ldm, float* Uh,
+                                         int64_t lduh, double* Sh, double* sig, int max_sweeps,
+                                         int* d_info, cudaStream_t s, bool* placed) {
+  *placed = false;
+  const size_t dyn = (size_t)4 * jc_width(l, jc) * l * sizeof(float);
+  const void* kern = jc == 8 ? (const void*)jacobi_cluster_kernel<8, 512>
+                             : (const void*)jacobi_cluster_kernel<16, 1024>;
+  const int threads = jc == 8 ? 512 : 1024;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
+  if (jc > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)jc);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)jc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  if (e != cudaSuccess) return e;
+  if (nclusters < 1) return cudaSuccess;
+  *placed = true;
+  const int tr_ = trace_begin(RSVD_TRACE_JACOBI, s);
+  if (jc == 8)
+    e = cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<8, 512>, l, M, ldm, Uh, lduh, Sh, sig,
+                           max_sweeps, d_info);
+  else
+    e = cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<16, 1024>, l, M, ldm, Uh, lduh, Sh, sig,
+                           max_sweeps, d_info);
+  count_launch();
+  trace_end(tr_, s);
+  return e;
+}
+
 template <typename T>
 cudaError_t launch_jacobi(int l, const T* M, int64_t ldm, T* Uh, int64_t lduh, double* Sh,
                           T* Vh, int64_t ldvh, T* scratch, int max_sweeps, int* d_info,
@@ -576,20 +637,14 @@ cudaError_t launch_jacobi(int l, const T* M, int64_t ldm, T* Uh, int64_t lduh, d
   (void)Vh;
   (void)ldvh;
   if (l > 1024) return cudaErrorInvalidValue;
-  if (jacobi_use_cluster(l, (int)sizeof(T))) {
+  const int jc = jacobi_cluster_size(l, (int)sizeof(T));
+  if (jc) {
     if (!scratch) return cudaErrorInvalidValue;
-    const size_t dyn = (size_t)4 * jc_width(l) * l * sizeof(float);
-    if (dyn > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-      if (e != cudaSuccess) return e;
-    }
-    const int tr_ = trace_begin(RSVD_TRACE_JACOBI, s);
-    jacobi_cluster_kernel<<<JC, JCT, dyn, s>>>(l, (const float*)M, ldm, (float*)Uh, lduh, Sh,
-                                               (double*)scratch, max_sweeps, d_info);
-    count_launch();
-    trace_end(tr_, s);
-    return cudaGetLastError();
+    bool placed = false;
+    const cudaError_t e = launch_jacobi_cluster(jc, l, (const float*)M, ldm, (float*)Uh, lduh, Sh,
+                                                (double*)scratch, max_sweeps, d_info, s, &placed);
+    // a cluster that cannot be placed falls through to the one-CTA kernel
+    if (e != cudaSuccess || placed) return e;
   }
   const size_t bytes = (size_t)l * l * sizeof(T);
   size_t dyn = 0;
