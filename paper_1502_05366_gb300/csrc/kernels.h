@@ -1,6 +1,7 @@
 // Host-side launchers of the library's kernels (internal; not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -305,6 +306,51 @@ struct BSign {
   int k;
 };
 cudaError_t launch_sign_batched(const BSign* tasks, int batch, cudaStream_t s);
+
+// ----- grouped tensor-core passes of the batched path (k_tc_group.cu) -----
+constexpr int TG_NMAX = 128;      // widest MMA N: round_up(l, 16) <= BATCH_LMAX
+// One problem of a grouped pass: C (M x ncol, ld ldc) = A W (form 0) or A^T W
+// (form 1); A and the bf16 terms of W^T through the launch's tensor maps.
+struct TgProb {
+  float* C;
+  int64_t ldc;
+  int M;          // output rows
+  int K;          // contraction length
+  int ncol;       // output columns (l)
+  int N;          // MMA width, round_up(l, 16) <= TG_NMAX
+};
+struct TgTask {   // one 128-row output tile of one problem
+  int prob, r0;
+};
+struct TgPad {    // rows x cols fp32 copied from pitch lds to pitch ldd
+  const float* src;
+  float* dst;
+  int64_t rows, cols, lds, ldd;
+};
+struct TgSplit {  // W (rows x l, ld ldw) -> bf16 hi / lo of W^T (N x ldt); Omega^T: W = null
+  const float* W;
+  int64_t ldw;
+  uint16_t* hi;
+  uint16_t* lo;
+  int64_t rows, ldt;
+  int l, N, batch;
+};
+// Tensor maps of one problem (A, W^T hi, W^T lo) for form 0 / 1; A padded to
+// pitch ldap (a multiple of 4), W^T with pitch ldt (a multiple of 8).
+bool tg_encode_maps(int form, int nwt, const float* Ap, int64_t m, int64_t n, int64_t ldap,
+                    const void* whi, const void* wlo, int64_t K, int N, int64_t ldt,
+                    CUtensorMap out[3]);
+// nwt: 1 = one bf16 term of W (Omega, bf16-exact), 2 = hi and lo terms.
+// maps: 3 per problem, 64-byte aligned, in device memory.
+cudaError_t launch_tc_group(int form, int nwt, const TgProb* probs, const TgTask* tasks,
+                            int ntasks, const CUtensorMap* maps, int* d_info, cudaStream_t s);
+// chunks: (job, first row), 32 rows each
+cudaError_t launch_pad_rows_batched(const TgPad* jobs, const int2* chunks, int nchunks,
+                                    cudaStream_t s);
+cudaError_t launch_split_t_batched(const TgSplit* jobs, const int2* chunks, int nchunks,
+                                   cudaStream_t s);
+cudaError_t launch_omega_t_batched(const TgSplit* jobs, const int2* chunks, int nchunks,
+                                   uint64_t seed, cudaStream_t s);
 
 // ----- adjoint of Alg. 5 (k_vjp.cu) ---------------------------------------
 // X (L x L) = diag(gs) + (F o (Gu - Gu^T)) diag(s) + diag(s) (F o (Gv - Gv^T)),

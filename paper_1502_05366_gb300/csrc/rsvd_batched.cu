@@ -32,6 +32,9 @@ struct Carve {   // workspace carving; dry when base is null
 struct ProbBufs {
   float *Y, *Yt, *Z, *Zt, *G, *Gpart, *R, *Rinv, *Racc, *tmp, *Uj, *Uh, *Vh;
   double* Sh;
+  // grouped tensor-core passes: A at a 16-byte pitch, the bf16 operands
+  float* Ap;
+  uint16_t *Oh, *Yh, *Yl, *Zh, *Zl;   // Omega^T; hi / lo of Y^T and of Z^T
 };
 
 // A Gram of a tall sample runs as one GEMM per slice of this many rows (split
@@ -40,11 +43,15 @@ struct ProbBufs {
 constexpr int GRAM_SLICE = 512;
 inline int gram_slices(int64_t rows) { return (int)((rows + GRAM_SLICE - 1) / GRAM_SLICE); }
 
-enum StageKind { ST_GEMM, ST_CHOL, ST_TRMM, ST_SVD, ST_SIGN, ST_SUM };
+enum StageKind { ST_GEMM, ST_CHOL, ST_TRMM, ST_SVD, ST_SIGN, ST_SUM, ST_TCG, ST_PAD, ST_SPLIT,
+                 ST_OMT };
 struct Stage {
   int kind;
-  int first, count;   // into the table of the kind (gemm: tasks; others: problems)
+  int first, count;   // into the table of the kind (gemm: tasks; others: problems; pad /
+                      // split / omega: chunks; grouped tensor-core pass: tasks)
   int rows;           // gemm: block height of the tasks
+  int first2 = 0;     // grouped pass: first problem record (and its 3 tensor maps)
+  int form = 0, nwt = 0;
 };
 
 struct Plan {
@@ -57,6 +64,14 @@ struct Plan {
   std::vector<BSum> sums;
   std::vector<Stage> stages;
   int lmax = 0;
+  // grouped tensor-core passes
+  std::vector<TgProb> tgp;
+  std::vector<TgTask> tgt;
+  std::vector<CUtensorMap> tgm;
+  std::vector<TgPad> pads;
+  std::vector<TgSplit> splits;
+  std::vector<int2> chunks;   // pad, split and omega chunks: (job, first row)
+  bool map_fail = false;      // a tensor map could not be encoded
 };
 
 bool items_ok(int batch, const rsvd_batch_item* it, int p, int q) {
@@ -103,6 +118,90 @@ BGemm gemm_of(const float* A, int64_t lda, int transA, const float* W, int64_t l
   g.transA = transA;
   g.batch = batch;
   return g;
+}
+
+inline int tg_n(int l) { return (l + 15) & ~15; }
+inline int64_t pad4(int64_t x) { return (x + 3) & ~(int64_t)3; }
+inline int64_t pad8(int64_t x) { return (x + 7) & ~(int64_t)7; }
+
+// Chunks of 32 rows of each job (rows[i]) appended to P.chunks; returns the
+// stage's (first, count).
+void add_chunks(Plan& P, int first_job, const std::vector<int64_t>& rows, int kind) {
+  Stage st{kind, (int)P.chunks.size(), 0, 0};
+  for (size_t i = 0; i < rows.size(); ++i)
+    for (int64_t r0 = 0; r0 < rows[i]; r0 += 32) P.chunks.push_back(make_int2(first_job + (int)i, (int)r0));
+  st.count = (int)P.chunks.size() - st.first;
+  if (st.count > 0) P.stages.push_back(st);
+}
+
+// W^T split (hi, lo) of every problem's X (rows x l, ld l): Y (rows m) or Z (rows n).
+void add_split(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<ProbBufs>& b,
+               bool on_z) {
+  const int j0 = (int)P.splits.size();
+  std::vector<int64_t> rows;
+  for (int i = 0; i < batch; ++i) {
+    const int l = it[i].k + p;
+    const int64_t rr = on_z ? it[i].n : it[i].m;
+    TgSplit sp;
+    sp.W = on_z ? b[i].Z : b[i].Y;
+    sp.ldw = l;
+    sp.hi = on_z ? b[i].Zh : b[i].Yh;
+    sp.lo = on_z ? b[i].Zl : b[i].Yl;
+    sp.rows = rr;
+    sp.ldt = pad8(rr);
+    sp.l = l;
+    sp.N = tg_n(l);
+    sp.batch = i;
+    P.splits.push_back(sp);
+    rows.push_back(rr);
+  }
+  add_chunks(P, j0, rows, ST_SPLIT);
+}
+
+// One grouped tensor-core pass over every problem's A: form 0 C = A W (W^T
+// from Omega^T when omega, else the split of Z), form 1 C = A^T W (W^T the
+// split of Y).  Output C = Y (form 0) or Z (form 1).  Tasks ordered by
+// decreasing contraction length, so that the CTAs' round-robin shares are even.
+void add_tc_pass(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<ProbBufs>& b,
+                 int form, bool omega, bool encode) {
+  Stage st{ST_TCG, (int)P.tgt.size(), 0, 0};
+  st.first2 = (int)P.tgp.size();
+  st.form = form;
+  st.nwt = omega ? 1 : 2;
+  std::vector<TgTask> tasks;
+  std::vector<int> cost;
+  for (int i = 0; i < batch; ++i) {
+    const int l = it[i].k + p;
+    const int64_t m = it[i].m, n = it[i].n;
+    TgProb pr;
+    pr.C = form == 0 ? b[i].Y : b[i].Z;
+    pr.ldc = l;
+    pr.M = (int)(form == 0 ? m : n);
+    pr.K = (int)(form == 0 ? n : m);
+    pr.ncol = l;
+    pr.N = tg_n(l);
+    P.tgp.push_back(pr);
+    CUtensorMap mp[3];
+    memset(mp, 0, sizeof(mp));
+    if (encode) {
+      const uint16_t* whi = form == 1 ? b[i].Yh : (omega ? b[i].Oh : b[i].Zh);
+      const uint16_t* wlo = form == 1 ? b[i].Yl : (omega ? nullptr : b[i].Zl);
+      if (!tg_encode_maps(form, st.nwt, b[i].Ap, m, n, pad4(n), whi, wlo, pr.K, pr.N,
+                          pad8(pr.K), mp))
+        P.map_fail = true;
+    }
+    for (int t = 0; t < 3; ++t) P.tgm.push_back(mp[t]);
+    for (int r0 = 0; r0 < pr.M; r0 += 128) {
+      tasks.push_back(TgTask{i, r0});
+      cost.push_back(pr.K);
+    }
+  }
+  std::vector<int> order(tasks.size());
+  for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  for (int t : order) P.tgt.push_back(tasks[t]);
+  st.count = (int)P.tgt.size() - st.first;
+  if (st.count > 0) P.stages.push_back(st);
 }
 
 // CholeskyQR2 of X (rows x l per problem, ld l) in place, through Xt; with
@@ -164,10 +263,11 @@ void add_orth(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<
 
 // Carves the per-problem buffers and the plan; returns the workspace bytes.
 size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A, float* U,
-             double* S, float* V, char* base, Plan& P, char** tables) {
+             double* S, float* V, char* base, Plan& P, char** tables, bool tc) {
   Carve cv;
   cv.base = base;
   std::vector<ProbBufs> b(batch);
+  const bool enc = base != nullptr;   // tensor maps need the device addresses
   for (int i = 0; i < batch; ++i) {
     const int64_t m = it[i].m, n = it[i].n;
     const int l = it[i].k + p;
@@ -186,42 +286,106 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
     b[i].Uh = cv.take<float>((size_t)l * l);
     b[i].Vh = cv.take<float>((size_t)l * l);
     b[i].Sh = cv.take<double>((size_t)l);
+    b[i].Ap = nullptr;
+    b[i].Oh = b[i].Yh = b[i].Yl = b[i].Zh = b[i].Zl = nullptr;
+    if (tc) {
+      const int N = tg_n(l);
+      b[i].Ap = cv.take<float>((size_t)m * pad4(n));
+      b[i].Oh = cv.take<uint16_t>((size_t)N * pad8(n));
+      b[i].Yh = cv.take<uint16_t>((size_t)N * pad8(m));
+      b[i].Yl = cv.take<uint16_t>((size_t)N * pad8(m));
+      b[i].Zh = cv.take<uint16_t>((size_t)N * pad8(n));
+      b[i].Zl = cv.take<uint16_t>((size_t)N * pad8(n));
+    }
+  }
+  if (tc) {
+    // A at a 16-byte pitch, then Omega^T of every problem
+    std::vector<int64_t> rows;
+    for (int i = 0; i < batch; ++i) {
+      TgPad pd;
+      pd.src = A ? A + it[i].a_off : nullptr;
+      pd.dst = b[i].Ap;
+      pd.rows = it[i].m;
+      pd.cols = it[i].n;
+      pd.lds = it[i].n;
+      pd.ldd = pad4(it[i].n);
+      P.pads.push_back(pd);
+      rows.push_back(it[i].m);
+    }
+    add_chunks(P, 0, rows, ST_PAD);
+    rows.clear();
+    const int j0 = (int)P.splits.size();
+    for (int i = 0; i < batch; ++i) {
+      const int l = it[i].k + p;
+      TgSplit sp;
+      sp.W = nullptr;
+      sp.ldw = 0;
+      sp.hi = b[i].Oh;
+      sp.lo = nullptr;
+      sp.rows = it[i].n;
+      sp.ldt = pad8(it[i].n);
+      sp.l = l;
+      sp.N = tg_n(l);
+      sp.batch = i;
+      P.splits.push_back(sp);
+      rows.push_back(it[i].n);
+    }
+    add_chunks(P, j0, rows, ST_OMT);
   }
   // Y = A Omega (Sec. 3.1, Fig. 1 step 2)
   std::vector<BGemm> gs;
-  for (int i = 0; i < batch; ++i) {
-    const int l = it[i].k + p;
-    gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 0, nullptr, 0, b[i].Y, l,
-                         it[i].m, l, it[i].n, l, i));
+  if (tc) {
+    add_tc_pass(P, batch, it, p, b, 0, true, enc);
+  } else {
+    for (int i = 0; i < batch; ++i) {
+      const int l = it[i].k + p;
+      gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 0, nullptr, 0, b[i].Y, l,
+                           it[i].m, l, it[i].n, l, i));
+    }
+    add_gemm_stage(P, gs);
   }
-  add_gemm_stage(P, gs);
   // power scheme, orthonormalising before every product (Alg. 5, s = 1)
   for (int j = 0; j < q; ++j) {
     add_orth(P, batch, it, p, b, false, false);
     gs.clear();
-    for (int i = 0; i < batch; ++i) {   // Z = A^T Y
+    if (tc) {                           // Z = A^T Y
+      add_split(P, batch, it, p, b, false);
+      add_tc_pass(P, batch, it, p, b, 1, false, enc);
+    } else {
+      for (int i = 0; i < batch; ++i) {
+        const int l = it[i].k + p;
+        gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 1, b[i].Y, l, b[i].Z, l,
+                             it[i].n, l, it[i].m, l, i));
+      }
+      add_gemm_stage(P, gs);
+    }
+    add_orth(P, batch, it, p, b, true, false);
+    gs.clear();
+    if (tc) {                           // Y = A Z
+      add_split(P, batch, it, p, b, true);
+      add_tc_pass(P, batch, it, p, b, 0, false, enc);
+    } else {
+      for (int i = 0; i < batch; ++i) {
+        const int l = it[i].k + p;
+        gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 0, b[i].Z, l, b[i].Y, l,
+                             it[i].m, l, it[i].n, l, i));
+      }
+      add_gemm_stage(P, gs);
+    }
+  }
+  add_orth(P, batch, it, p, b, false, false);   // Q = orth(Y)
+  gs.clear();
+  if (tc) {                                     // Bt = A^T Q
+    add_split(P, batch, it, p, b, false);
+    add_tc_pass(P, batch, it, p, b, 1, false, enc);
+  } else {
+    for (int i = 0; i < batch; ++i) {
       const int l = it[i].k + p;
       gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 1, b[i].Y, l, b[i].Z, l,
                            it[i].n, l, it[i].m, l, i));
     }
     add_gemm_stage(P, gs);
-    add_orth(P, batch, it, p, b, true, false);
-    gs.clear();
-    for (int i = 0; i < batch; ++i) {   // Y = A Z
-      const int l = it[i].k + p;
-      gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 0, b[i].Z, l, b[i].Y, l,
-                           it[i].m, l, it[i].n, l, i));
-    }
-    add_gemm_stage(P, gs);
   }
-  add_orth(P, batch, it, p, b, false, false);   // Q = orth(Y)
-  gs.clear();
-  for (int i = 0; i < batch; ++i) {             // Bt = A^T Q
-    const int l = it[i].k + p;
-    gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 1, b[i].Y, l, b[i].Z, l,
-                         it[i].n, l, it[i].m, l, i));
-  }
-  add_gemm_stage(P, gs);
   add_orth(P, batch, it, p, b, true, true);     // Bt = Qh Rh
   {
     Stage st{ST_SVD, (int)P.svds.size(), batch, 0};   // Rh = Uh diag(Sh) Vh^T
@@ -270,6 +434,12 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
   cv.take<BSvd>(P.svds.size());
   cv.take<BSign>(P.signs.size());
   cv.take<BSum>(P.sums.size());
+  cv.take<TgProb>(P.tgp.size());
+  cv.take<TgTask>(P.tgt.size());
+  cv.take<CUtensorMap>(P.tgm.size());
+  cv.take<TgPad>(P.pads.size());
+  cv.take<TgSplit>(P.splits.size());
+  cv.take<int2>(P.chunks.size());
   return cv.off + 256;
 }
 
@@ -285,7 +455,8 @@ size_t rsvd_svd_batched_workspace_size(int batch, const rsvd_batch_item* items, 
   if (!items_ok(batch, items, p, q)) return 0;
   Plan P;
   char* tables = nullptr;
-  return build(batch, items, p, q, nullptr, nullptr, nullptr, nullptr, nullptr, P, &tables);
+  return build(batch, items, p, q, nullptr, nullptr, nullptr, nullptr, nullptr, P, &tables,
+               true);
 }
 
 rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int q,
@@ -296,11 +467,12 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
   Plan dry;
   char* t0 = nullptr;
   const size_t need = build(batch, items, p, q, nullptr, nullptr, nullptr, nullptr, nullptr, dry,
-                            &t0);
+                            &t0, true);
   if (need > work_bytes) return RSVD_ERR_WORKSPACE;
   Plan P;
   char* tables = nullptr;
-  build(batch, items, p, q, A, U, S, V, (char*)work, P, &tables);
+  build(batch, items, p, q, A, U, S, V, (char*)work, P, &tables, true);
+  if (P.map_fail) return RSVD_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   if (d_info && cudaMemsetAsync(d_info, 0, sizeof(int), s) != cudaSuccess) return RSVD_ERR_CUDA;
   // upload the tables (same carving as in build)
@@ -314,6 +486,12 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
   BSvd* dv = cv.take<BSvd>(P.svds.size());
   BSign* dsg = cv.take<BSign>(P.signs.size());
   BSum* dsu = cv.take<BSum>(P.sums.size());
+  TgProb* dtp = cv.take<TgProb>(P.tgp.size());
+  TgTask* dtt = cv.take<TgTask>(P.tgt.size());
+  CUtensorMap* dtm = cv.take<CUtensorMap>(P.tgm.size());
+  TgPad* dpd = cv.take<TgPad>(P.pads.size());
+  TgSplit* dsp = cv.take<TgSplit>(P.splits.size());
+  int2* dch = cv.take<int2>(P.chunks.size());
 #define UPLOAD(dst, vec)                                                                 \
   if (!vec.empty() && cudaMemcpyAsync(dst, vec.data(), vec.size() * sizeof(vec[0]),      \
                                       cudaMemcpyHostToDevice, s) != cudaSuccess)         \
@@ -325,6 +503,12 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
   UPLOAD(dv, P.svds);
   UPLOAD(dsg, P.signs);
   UPLOAD(dsu, P.sums);
+  UPLOAD(dtp, P.tgp);
+  UPLOAD(dtt, P.tgt);
+  UPLOAD(dtm, P.tgm);
+  UPLOAD(dpd, P.pads);
+  UPLOAD(dsp, P.splits);
+  UPLOAD(dch, P.chunks);
 #undef UPLOAD
   for (const Stage& st : P.stages) {
     cudaError_t e = cudaSuccess;
@@ -337,6 +521,13 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
         break;
       case ST_SIGN: e = launch_sign_batched(dsg + st.first, st.count, s); break;
       case ST_SUM: e = launch_sum_batched(dsu + st.first, st.count, s); break;
+      case ST_TCG:
+        e = launch_tc_group(st.form, st.nwt, dtp + st.first2, dtt + st.first, st.count,
+                            dtm + 3 * (int64_t)st.first2, d_info, s);
+        break;
+      case ST_PAD: e = launch_pad_rows_batched(dpd, dch + st.first, st.count, s); break;
+      case ST_SPLIT: e = launch_split_t_batched(dsp, dch + st.first, st.count, s); break;
+      case ST_OMT: e = launch_omega_t_batched(dsp, dch + st.first, st.count, seed, s); break;
       default: break;
     }
     if (e != cudaSuccess) return RSVD_ERR_CUDA;
