@@ -496,8 +496,12 @@ rsvd_status rsvd_test_set_barrier_wait(long long cycles, int withhold);
  * A, U, V, S are device buffers holding all problems at the given element
  * offsets; outputs must not overlap.  Omega of problem i is the Philox stream
  * of `seed` with the problem index as the counter's batch word (counter (row,
- * column / 4, 0, i)), rounded to bf16 as on the FP32 path.  Products are fp32
- * (SIMT), the l x l factorisations fp32 with the CholeskyQR shift fallback.
+ * column / 4, 0, i)), rounded to bf16 as on the FP32 path.  The passes over A
+ * and the CholeskyQR steps of the power scheme run as grouped tcgen05 launches
+ * (bf16 split products, fp32 accumulation, as rsvd_svd's tensor-core path);
+ * the final orthonormalisations of Y and Bt and the lifts of U and V are plain
+ * fp32 products, the l x l factorisations fp32 with the CholeskyQR shift
+ * fallback.
  * Sign rule and ordering as rsvd_svd.  The work buffer (256-byte aligned)
  * holds per-problem scratch and the task tables, which are copied from the
  * host with cudaMemcpyAsync on `stream` (no host synchronisation).
@@ -511,6 +515,18 @@ typedef struct {
 } rsvd_batch_item;
 
 size_t rsvd_svd_batched_workspace_size(int batch, const rsvd_batch_item* items, int p, int q);
+/* The choices of the batched path's tile autotuner so far in this process
+ * (not part of the paper's method).  The plain fp32 GEMMs of the batch
+ * (Gram slices, applies and lifts of the final orthonormalisations, and the
+ * passes over A when the tensor-core grouped passes do not apply) run on
+ * blocks of 64, 128 or 256 output rows; the first call that meets a class
+ * (kind: 0 pass over A, 1 Gram slice, 2 apply, 3 lift, 4 sketch; and width N)
+ * times every valid height on its own GEMMs of the class and keeps the
+ * fastest.  That call synchronises its stream once per new class; later calls
+ * do not.  Every height gives bit-identical results.  Writes up to `cap`
+ * entries: kind, width, chosen rows, and ms[3 i + h] the time of height
+ * 64 << h (-1 when not valid); returns the number of classes. */
+int rsvd_batched_tuning(int cap, int* kind, int* width, int* rows, float* ms);
 rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int q,
                              uint64_t seed, const float* A, float* U, double* S, float* V,
                              void* work, size_t work_bytes, int* d_info, void* stream);

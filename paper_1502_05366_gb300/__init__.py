@@ -112,6 +112,8 @@ _SIGS = {
                                                   _c_int]),
     "rsvd_svd_batched": (_c_int, [_c_int, ctypes.POINTER(BatchItem), _c_int, _c_int, _c_u64, _vp,
                                   _vp, _vp, _vp, _vp, _c_size, _vp, _vp]),
+    "rsvd_batched_tuning": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                     ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float)]),
     "rsvd_cpqr_id_f32": (_c_int, [_c_int, _c_i64, _c_int, _vp, _c_i64, _vp, _vp, _c_i64, _vp,
                                   _vp, _c_size, _vp, _vp]),
     "rsvd_id_tol_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_int,
@@ -836,6 +838,26 @@ class BatchPlan:
         V = self.V[self.v_off[i]:self.v_off[i] + n * k].view(n, k)
         S = self.S[self.s_off[i]:self.s_off[i] + k]
         return U, S, V
+
+
+TUNE_KINDS = {0: "pass over A", 1: "Gram slice", 2: "apply R^-1", 3: "lift", 4: "sketch"}
+
+
+def batched_tuning():
+    """The batched path's tile autotuner choices so far (rsvd_batched_tuning):
+    one dict per GEMM class with the kind, the width N, the chosen block height
+    and the measured ms of heights 64, 128, 256 (None where not valid)."""
+    n = lib().rsvd_batched_tuning(0, None, None, None, None)
+    if n <= 0:
+        return []
+    kind = (_c_int * n)()
+    width = (_c_int * n)()
+    rows = (_c_int * n)()
+    ms = (ctypes.c_float * (3 * n))()
+    lib().rsvd_batched_tuning(n, kind, width, rows, ms)
+    return [{"kind": TUNE_KINDS.get(kind[i], kind[i]), "width": width[i], "rows": rows[i],
+             "ms": [ms[3 * i + h] if ms[3 * i + h] >= 0 else None for h in range(3)]}
+            for i in range(n)]
 
 
 def svd_batched(mats, ks, p, q, seed, check=True):

@@ -13,6 +13,11 @@
 // arithmetic is that of k_tc.cu: a = a0 + a1 (bf16 hi, lo), products a0 w0 +
 // a1 w0 (+ a0 w1 for a stored W), fp32 accumulation in tensor memory.
 //
+// The CholeskyQR steps of the batch run here too: the Gram X^T X (form 1,
+// W = X) and the apply X R^-1 (form 0, W = R^-1 in three bf16 terms), and the
+// lifts U = Q Vh, V = Qh Uh (form 0): X has an l-float pitch, so these take
+// TMA maps of X itself when l is a multiple of 4.
+//
 // Roles (256 threads): warp 0 TMA producer, warp 1 MMA issuer and TMEM owner,
 // warps 4-7 converters (fp32 A rows -> bf16 hi/lo in TMEM) and the epilogue of
 // each task (TMEM -> C_i rows).  The MMA width N_i = round_up(l_i, 16) is the
@@ -38,6 +43,11 @@ constexpr int GB_BK = 32;                      // K per stage
 constexpr int GB_ST = 4;                       // stages
 constexpr int GB_ASTAGE = GB_BM * GB_BK * 4;   // 16 KB: the fp32 A tile
 constexpr int GB_WTILE = TG_NMAX * GB_BK * 2;  // 8 KB: one bf16 term of W^T (N <= 128 rows)
+// W terms and products per K-step (the rules of k_tc.cu):
+//   NWT 1         a0 w0 + a1 w0                 (Omega: bf16-exact)
+//   NWT 2         a0 w0 + a1 w0 + a0 w1         (a stored operand)
+//   NWT 2, GRAM   a0 w0 + a1 w0 + a0 w1 + a1 w1 (Gram X^T X: W is X itself)
+//   NWT 3         a0 w0 + a1 w0 + a0 w1 + a0 w2 (the fixed factor R^-1)
 constexpr int GB_NCONV = 4;                    // warps 4..7
 constexpr uint32_t GB_TMEM_COLS = 256;         // accumulator at 0 (<= 128 columns), A stages after
 constexpr uint32_t GB_TMEM_A0 = 128;
@@ -51,7 +61,7 @@ __host__ __device__ constexpr int gb_stage_bytes(int nwt) { return GB_ASTAGE + n
 size_t gb_smem(int nwt) { return 1024 + (size_t)GB_ST * gb_stage_bytes(nwt) + (3 * GB_ST + 2) * 8 + 16; }
 }  // namespace
 
-template <int FORM, int NWT>
+template <int FORM, int NWT, bool GRAM>
 __global__ void __launch_bounds__(256, 1)
     tc_group_kernel(const TgProb* __restrict__ probs, const TgTask* __restrict__ tasks, int ntasks,
                     const CUtensorMap* __restrict__ maps, int* d_info) {
@@ -104,10 +114,11 @@ __global__ void __launch_bounds__(256, 1)
       for (int t = blockIdx.x; t < ntasks && ok; t += G) {
         const TgTask tk = tasks[t];
         const TgProb pr = probs[tk.prob];
-        const CUtensorMap* mA = maps + 3 * (int64_t)tk.prob;
+        const CUtensorMap* mA = maps + 4 * (int64_t)tk.prob;
         prefetch_map(mA);
         prefetch_map(mA + 1);
-        if (NWT == 2) prefetch_map(mA + 2);
+        if (NWT >= 2) prefetch_map(mA + 2);
+        if (NWT == 3) prefetch_map(mA + 3);
         const int kiters = (pr.K + GB_BK - 1) / GB_BK;
         const uint32_t bytes = (uint32_t)GB_ASTAGE + (uint32_t)NWT * (uint32_t)pr.N * GB_BK * 2u;
         for (int kc = 0; kc < kiters; ++kc) {
@@ -122,7 +133,8 @@ __global__ void __launch_bounds__(256, 1)
           else
             tma_load_2d_hint(st, mA, &full[s], tk.r0, kc * GB_BK, pol_a);
           tma_load_2d_hint(st + GB_ASTAGE, mA + 1, &full[s], kc * GB_BK, 0, pol_w);
-          if (NWT == 2) tma_load_2d_hint(st + GB_ASTAGE + GB_WTILE, mA + 2, &full[s], kc * GB_BK, 0, pol_w);
+          if (NWT >= 2) tma_load_2d_hint(st + GB_ASTAGE + GB_WTILE, mA + 2, &full[s], kc * GB_BK, 0, pol_w);
+          if (NWT == 3) tma_load_2d_hint(st + GB_ASTAGE + 2 * GB_WTILE, mA + 3, &full[s], kc * GB_BK, 0, pol_w);
           ++issued;
           if (++s == GB_ST) {
             s = 0;
@@ -176,7 +188,12 @@ __global__ void __launch_bounds__(256, 1)
             const uint32_t alo = a_col + 16u + 8u * kk;
             mma_ts(tmem, ahi, bhi, idesc, (first && kk == 0) ? 0u : 1u);
             mma_ts(tmem, alo, bhi, idesc, 1u);
-            if (NWT == 2) mma_ts(tmem, ahi, sw64_desc(wbase + GB_WTILE + 32u * kk), idesc, 1u);
+            if (NWT >= 2) {
+              const uint64_t b1 = sw64_desc(wbase + GB_WTILE + 32u * kk);
+              mma_ts(tmem, ahi, b1, idesc, 1u);
+              if (GRAM) mma_ts(tmem, alo, b1, idesc, 1u);
+            }
+            if (NWT == 3) mma_ts(tmem, ahi, sw64_desc(wbase + 2 * GB_WTILE + 32u * kk), idesc, 1u);
           }
           mma_commit(&done[s]);
           if (last) {
@@ -319,9 +336,13 @@ __global__ void __launch_bounds__(256) split_t_batched_kernel(const TgSplit* __r
     if (kk >= kr) continue;
     const float v = j < jb.l ? tile[kk][j] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    reinterpret_cast<__nv_bfloat16*>(jb.hi)[(int64_t)j * jb.ldt + k0 + kk] = h;
-    reinterpret_cast<__nv_bfloat16*>(jb.lo)[(int64_t)j * jb.ldt + k0 + kk] =
-        __float2bfloat16_rn(v - __bfloat162float(h));
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1);
+    const int64_t o = (int64_t)j * jb.ldt + k0 + kk;
+    reinterpret_cast<__nv_bfloat16*>(jb.hi)[o] = h;
+    reinterpret_cast<__nv_bfloat16*>(jb.lo)[o] = lo;
+    if (jb.lo2)   // third term: the rest of the 24 bits
+      reinterpret_cast<__nv_bfloat16*>(jb.lo2)[o] = __float2bfloat16_rn(r1 - __bfloat162float(lo));
   }
 }
 
@@ -359,9 +380,9 @@ __global__ void __launch_bounds__(256) omega_t_batched_kernel(const TgSplit* __r
 // ------------------------------- host side ---------------------------------
 
 bool tg_encode_maps(int form, int nwt, const float* Ap, int64_t m, int64_t n, int64_t ldap,
-                    const void* whi, const void* wlo, int64_t K, int N, int64_t ldt,
-                    CUtensorMap out[3]) {
-  memset(out, 0, 3 * sizeof(CUtensorMap));
+                    const void* whi, const void* wlo, const void* wlo2, int64_t K, int N,
+                    int64_t ldt, CUtensorMap out[4]) {
+  memset(out, 0, 4 * sizeof(CUtensorMap));
   bool ok;
   if (form == 0)   // rows of 32 fp32 (128 bytes), swizzled
     ok = encode_2d(&out[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Ap, (uint64_t)n, (uint64_t)m,
@@ -370,31 +391,37 @@ bool tg_encode_maps(int form, int nwt, const float* Ap, int64_t m, int64_t n, in
     ok = encode_2d(&out[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Ap, (uint64_t)n, (uint64_t)m,
                    (uint64_t)ldap, GB_BM, GB_BK, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!ok) return false;
-  const void* wp[2] = {whi, wlo};
+  const void* wp[3] = {whi, wlo, wlo2};
   for (int t = 0; t < nwt; ++t) {
     if (!wp[t]) return false;
     ok = encode_2d(&out[1 + t], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, wp[t], (uint64_t)K,
                    (uint64_t)N, (uint64_t)ldt, GB_BK, (uint32_t)N, CU_TENSOR_MAP_SWIZZLE_64B);
     if (!ok) return false;
   }
-  if (nwt < 2) out[2] = out[1];
+  for (int t = nwt; t < 3; ++t) out[1 + t] = out[1];
   return true;
 }
 
-cudaError_t launch_tc_group(int form, int nwt, const TgProb* probs, const TgTask* tasks,
-                            int ntasks, const CUtensorMap* maps, int* d_info, cudaStream_t s) {
+cudaError_t launch_tc_group(int form, int nwt, bool gram, const TgProb* probs,
+                            const TgTask* tasks, int ntasks, const CUtensorMap* maps, int* d_info,
+                            cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   const int G = std::min(ntasks, device_sm_count());
   const size_t smem = gb_smem(nwt);
   void (*kern)(const TgProb*, const TgTask*, int, const CUtensorMap*, int*) = nullptr;
-  if (form == 0 && nwt == 1) kern = tc_group_kernel<0, 1>;
-  else if (form == 0 && nwt == 2) kern = tc_group_kernel<0, 2>;
-  else if (form == 1 && nwt == 2) kern = tc_group_kernel<1, 2>;
+  if (form == 0 && nwt == 1 && !gram) kern = tc_group_kernel<0, 1, false>;
+  else if (form == 0 && nwt == 2 && !gram) kern = tc_group_kernel<0, 2, false>;
+  else if (form == 0 && nwt == 3 && !gram) kern = tc_group_kernel<0, 3, false>;
+  else if (form == 1 && nwt == 2 && !gram) kern = tc_group_kernel<1, 2, false>;
+  else if (form == 1 && nwt == 2 && gram) kern = tc_group_kernel<1, 2, true>;
   else return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const int cls = form == 1 ? RSVD_TRACE_AT_W : (nwt == 1 ? RSVD_TRACE_A_OMEGA : RSVD_TRACE_A_W);
+  const int cls = gram ? RSVD_TRACE_GRAM
+                      : (nwt == 3 ? RSVD_TRACE_APPLY
+                                  : (form == 1 ? RSVD_TRACE_AT_W
+                                               : (nwt == 1 ? RSVD_TRACE_A_OMEGA : RSVD_TRACE_A_W)));
   const int tr = trace_begin(cls, s);
   kern<<<G, 256, smem, s>>>(probs, tasks, ntasks, maps, d_info);
   count_launch();

@@ -327,23 +327,26 @@ struct TgPad {    // rows x cols fp32 copied from pitch lds to pitch ldd
   float* dst;
   int64_t rows, cols, lds, ldd;
 };
-struct TgSplit {  // W (rows x l, ld ldw) -> bf16 hi / lo of W^T (N x ldt); Omega^T: W = null
+struct TgSplit {  // W (rows x l, ld ldw) -> bf16 hi / lo (/ lo2) of W^T (N x ldt); Omega^T: W = null
   const float* W;
   int64_t ldw;
   uint16_t* hi;
   uint16_t* lo;
+  uint16_t* lo2;  // third term (R^-1), or null
   int64_t rows, ldt;
   int l, N, batch;
 };
-// Tensor maps of one problem (A, W^T hi, W^T lo) for form 0 / 1; A padded to
-// pitch ldap (a multiple of 4), W^T with pitch ldt (a multiple of 8).
+// Tensor maps of one problem (A, then up to three bf16 terms of W^T) for form
+// 0 / 1; A with pitch ldap (a multiple of 4), W^T with pitch ldt (a multiple of 8).
 bool tg_encode_maps(int form, int nwt, const float* Ap, int64_t m, int64_t n, int64_t ldap,
-                    const void* whi, const void* wlo, int64_t K, int N, int64_t ldt,
-                    CUtensorMap out[3]);
-// nwt: 1 = one bf16 term of W (Omega, bf16-exact), 2 = hi and lo terms.
-// maps: 3 per problem, 64-byte aligned, in device memory.
-cudaError_t launch_tc_group(int form, int nwt, const TgProb* probs, const TgTask* tasks,
-                            int ntasks, const CUtensorMap* maps, int* d_info, cudaStream_t s);
+                    const void* whi, const void* wlo, const void* wlo2, int64_t K, int N,
+                    int64_t ldt, CUtensorMap out[4]);
+// nwt: 1 = one bf16 term of W (Omega, bf16-exact), 2 = hi and lo, 3 = R^-1's
+// three terms; gram: W is A itself (nwt 2, the a1 w1 product kept).
+// maps: 4 per problem, 64-byte aligned, in device memory.
+cudaError_t launch_tc_group(int form, int nwt, bool gram, const TgProb* probs,
+                            const TgTask* tasks, int ntasks, const CUtensorMap* maps, int* d_info,
+                            cudaStream_t s);
 // chunks: (job, first row), 32 rows each
 cudaError_t launch_pad_rows_batched(const TgPad* jobs, const int2* chunks, int nchunks,
                                     cudaStream_t s);

@@ -7,6 +7,8 @@
 // workspace once per call.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -35,6 +37,7 @@ struct ProbBufs {
   // grouped tensor-core passes: A at a 16-byte pitch, the bf16 operands
   float* Ap;
   uint16_t *Oh, *Yh, *Yl, *Zh, *Zl;   // Omega^T; hi / lo of Y^T and of Z^T
+  uint16_t* Rw[3];                    // R^-1 in three bf16 terms (transposed)
 };
 
 // A Gram of a tall sample runs as one GEMM per slice of this many rows (split
@@ -72,6 +75,8 @@ struct Plan {
   std::vector<TgSplit> splits;
   std::vector<int2> chunks;   // pad, split and omega chunks: (job, first row)
   bool map_fail = false;      // a tensor map could not be encoded
+  std::vector<int> gkind;     // tuner class kind of every SIMT GEMM
+  int64_t tune_cap = 0;       // tasks of all SIMT GEMMs at the smallest height
 };
 
 bool items_ok(int batch, const rsvd_batch_item* it, int p, int q) {
@@ -86,15 +91,46 @@ bool items_ok(int batch, const rsvd_batch_item* it, int p, int q) {
   return true;
 }
 
-// One GEMM per problem; tasks over blocks of output rows whose height follows
-// the width, one launch per height.
-void add_gemm_stage(Plan& P, const std::vector<BGemm>& gs) {
+// ---------------------------------------------------------------------------
+// Tile autotuner of the grouped SIMT GEMM (bgemm_kernel): a task is a block of
+// 64, 128 or 256 output rows by 128, 64 or 32 columns.  The block height of
+// every GEMM class (kind: sketch or pass over A, Gram slice, apply, lift; and
+// its width N) is measured the first time a call meets the class: each valid
+// height runs the class's GEMMs of that call (CUDA events, after one warm-up
+// launch) and the fastest is kept for the life of the process.  Every height
+// computes each output entry by the same sequence of fused multiply-adds, so
+// the choice changes the time only, never the result.
+// ---------------------------------------------------------------------------
+enum GemmKind { GK_PASS = 0, GK_GRAM = 1, GK_APPLY = 2, GK_LIFT = 3, GK_SKETCH = 4 };
+struct TuneEntry {
+  int rows;
+  float ms[3];   // measured time of heights 64, 128, 256 (-1: not valid)
+};
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, TuneEntry> g_tune;   // (kind, N) -> choice
+
+inline bool rows_valid(int rows, int N) { return N <= 8192 / rows; }
+int tuned_rows(int kind, int N) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto f = g_tune.find(std::make_pair(kind, N));
+  return f != g_tune.end() ? f->second.rows : bgemm_rows(N);
+}
+
+// One GEMM per problem; tasks over blocks of output rows, one launch per
+// block height; the height of each GEMM is the tuner's choice for its class.
+void add_gemm_stage(Plan& P, const std::vector<BGemm>& gs, int kind) {
   const int g0 = (int)P.gemms.size();
   for (const BGemm& g : gs) P.gemms.push_back(g);
+  std::vector<int> h(gs.size());
+  for (size_t i = 0; i < gs.size(); ++i) {
+    h[i] = tuned_rows(kind, gs[i].N);
+    P.gkind.push_back(kind);
+    P.tune_cap += (gs[i].M + 63) / 64;
+  }
   for (int rows = 64; rows <= 256; rows *= 2) {
     Stage st{ST_GEMM, (int)P.tasks.size(), 0, rows};
     for (int i = 0; i < (int)gs.size(); ++i) {
-      if (bgemm_rows(gs[i].N) != rows) continue;
+      if (h[i] != rows) continue;
       for (int r0 = 0; r0 < gs[i].M; r0 += rows) P.tasks.push_back(make_int2(g0 + i, r0));
     }
     st.count = (int)P.tasks.size() - st.first;
@@ -147,6 +183,7 @@ void add_split(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector
     sp.ldw = l;
     sp.hi = on_z ? b[i].Zh : b[i].Yh;
     sp.lo = on_z ? b[i].Zl : b[i].Yl;
+    sp.lo2 = nullptr;
     sp.rows = rr;
     sp.ldt = pad8(rr);
     sp.l = l;
@@ -158,41 +195,45 @@ void add_split(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector
   add_chunks(P, j0, rows, ST_SPLIT);
 }
 
-// One grouped tensor-core pass over every problem's A: form 0 C = A W (W^T
-// from Omega^T when omega, else the split of Z), form 1 C = A^T W (W^T the
-// split of Y).  Output C = Y (form 0) or Z (form 1).  Tasks ordered by
+// One grouped tensor-core launch: C_i = A_i W_i (form 0) or A_i^T W_i (form 1)
+// per problem, W_i^T in nwt bf16 terms (w[0..nwt)).  Tasks ordered by
 // decreasing contraction length, so that the CTAs' round-robin shares are even.
-void add_tc_pass(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<ProbBufs>& b,
-                 int form, bool omega, bool encode) {
+struct TcSpec {
+  const float* A;
+  int64_t arows, acols, lda;   // A as stored (row-major, pitch lda: a multiple of 4)
+  const uint16_t* w[3];
+  int64_t ldt;                 // pitch of the W^T terms (a multiple of 8)
+  float* C;
+  int64_t ldc;
+  int M, K, ncol, N;
+};
+void add_tc_stage(Plan& P, int form, int nwt, bool gram, const std::vector<TcSpec>& specs,
+                  bool encode) {
   Stage st{ST_TCG, (int)P.tgt.size(), 0, 0};
   st.first2 = (int)P.tgp.size();
   st.form = form;
-  st.nwt = omega ? 1 : 2;
+  st.nwt = nwt;
+  st.rows = gram ? 1 : 0;
   std::vector<TgTask> tasks;
   std::vector<int> cost;
-  for (int i = 0; i < batch; ++i) {
-    const int l = it[i].k + p;
-    const int64_t m = it[i].m, n = it[i].n;
+  for (size_t i = 0; i < specs.size(); ++i) {
+    const TcSpec& sp = specs[i];
     TgProb pr;
-    pr.C = form == 0 ? b[i].Y : b[i].Z;
-    pr.ldc = l;
-    pr.M = (int)(form == 0 ? m : n);
-    pr.K = (int)(form == 0 ? n : m);
-    pr.ncol = l;
-    pr.N = tg_n(l);
+    pr.C = sp.C;
+    pr.ldc = sp.ldc;
+    pr.M = sp.M;
+    pr.K = sp.K;
+    pr.ncol = sp.ncol;
+    pr.N = sp.N;
     P.tgp.push_back(pr);
-    CUtensorMap mp[3];
+    CUtensorMap mp[4];
     memset(mp, 0, sizeof(mp));
-    if (encode) {
-      const uint16_t* whi = form == 1 ? b[i].Yh : (omega ? b[i].Oh : b[i].Zh);
-      const uint16_t* wlo = form == 1 ? b[i].Yl : (omega ? nullptr : b[i].Zl);
-      if (!tg_encode_maps(form, st.nwt, b[i].Ap, m, n, pad4(n), whi, wlo, pr.K, pr.N,
-                          pad8(pr.K), mp))
-        P.map_fail = true;
-    }
-    for (int t = 0; t < 3; ++t) P.tgm.push_back(mp[t]);
+    if (encode && !tg_encode_maps(form, nwt, sp.A, sp.arows, sp.acols, sp.lda, sp.w[0], sp.w[1],
+                                  sp.w[2], sp.K, sp.N, sp.ldt, mp))
+      P.map_fail = true;
+    for (int t = 0; t < 4; ++t) P.tgm.push_back(mp[t]);
     for (int r0 = 0; r0 < pr.M; r0 += 128) {
-      tasks.push_back(TgTask{i, r0});
+      tasks.push_back(TgTask{(int)i, r0});
       cost.push_back(pr.K);
     }
   }
@@ -202,6 +243,156 @@ void add_tc_pass(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vect
   for (int t : order) P.tgt.push_back(tasks[t]);
   st.count = (int)P.tgt.size() - st.first;
   if (st.count > 0) P.stages.push_back(st);
+}
+
+// One pass over every problem's A (A at its 16-byte pitch copy): form 0
+// C = A W (W^T from Omega^T when omega, else the split of Z), form 1
+// C = A^T W (W^T the split of Y); C = Y (form 0) or Z (form 1).
+void add_tc_pass(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<ProbBufs>& b,
+                 int form, bool omega, bool encode) {
+  std::vector<TcSpec> specs;
+  for (int i = 0; i < batch; ++i) {
+    const int l = it[i].k + p;
+    const int64_t m = it[i].m, n = it[i].n;
+    TcSpec sp;
+    sp.A = b[i].Ap;
+    sp.arows = m;
+    sp.acols = n;
+    sp.lda = pad4(n);
+    sp.w[0] = form == 1 ? b[i].Yh : (omega ? b[i].Oh : b[i].Zh);
+    sp.w[1] = form == 1 ? b[i].Yl : (omega ? nullptr : b[i].Zl);
+    sp.w[2] = nullptr;
+    sp.C = form == 0 ? b[i].Y : b[i].Z;
+    sp.ldc = l;
+    sp.M = (int)(form == 0 ? m : n);
+    sp.K = (int)(form == 0 ? n : m);
+    sp.ldt = pad8(sp.K);
+    sp.ncol = l;
+    sp.N = tg_n(l);
+    specs.push_back(sp);
+  }
+  add_tc_stage(P, form, omega ? 1 : 2, false, specs, encode);
+}
+
+// R^-1 of every problem in three bf16 terms, transposed: row j of the split
+// is column j of R^-1.
+void add_rinv_split(Plan& P, int batch, const rsvd_batch_item* it, int p,
+                    std::vector<ProbBufs>& b) {
+  const int j0 = (int)P.splits.size();
+  std::vector<int64_t> rows;
+  for (int i = 0; i < batch; ++i) {
+    const int l = it[i].k + p;
+    TgSplit sp;
+    sp.W = b[i].Rinv;
+    sp.ldw = l;
+    sp.hi = b[i].Rw[0];
+    sp.lo = b[i].Rw[1];
+    sp.lo2 = b[i].Rw[2];
+    sp.rows = l;
+    sp.ldt = pad8(l);
+    sp.l = l;
+    sp.N = tg_n(l);
+    sp.batch = i;
+    P.splits.push_back(sp);
+    rows.push_back(l);
+  }
+  add_chunks(P, j0, rows, ST_SPLIT);
+}
+
+// CholeskyQR2 on the tensor cores: per pass the split of the current X, the
+// Gram X^T X, the Cholesky factor and inverse (one CTA a problem), the split
+// of R^-1, the apply X R^-1.  X has pitch l (a multiple of 4: TMA).
+void add_orth_tc(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<ProbBufs>& b,
+                 bool on_z, bool want_R, bool encode) {
+  for (int pass = 0; pass < 2; ++pass) {
+    // split of src
+    {
+      const int j0 = (int)P.splits.size();
+      std::vector<int64_t> rows;
+      for (int i = 0; i < batch; ++i) {
+        const int l = it[i].k + p;
+        const int64_t rr = on_z ? it[i].n : it[i].m;
+        TgSplit sp;
+        sp.W = pass == 0 ? (on_z ? b[i].Z : b[i].Y) : (on_z ? b[i].Zt : b[i].Yt);
+        sp.ldw = l;
+        sp.hi = on_z ? b[i].Zh : b[i].Yh;
+        sp.lo = on_z ? b[i].Zl : b[i].Yl;
+        sp.lo2 = nullptr;
+        sp.rows = rr;
+        sp.ldt = pad8(rr);
+        sp.l = l;
+        sp.N = tg_n(l);
+        sp.batch = i;
+        P.splits.push_back(sp);
+        rows.push_back(rr);
+      }
+      add_chunks(P, j0, rows, ST_SPLIT);
+    }
+    std::vector<TcSpec> gram, apply;
+    Stage sc{ST_CHOL, (int)P.chols.size(), batch, 0};
+    for (int i = 0; i < batch; ++i) {
+      const int l = it[i].k + p;
+      const int64_t rr = on_z ? it[i].n : it[i].m;
+      float* X = on_z ? b[i].Z : b[i].Y;
+      float* Xt = on_z ? b[i].Zt : b[i].Yt;
+      float* src = pass == 0 ? X : Xt;
+      float* dst = pass == 0 ? Xt : X;
+      TcSpec g;
+      g.A = src;
+      g.arows = rr;
+      g.acols = l;
+      g.lda = l;
+      g.w[0] = on_z ? b[i].Zh : b[i].Yh;
+      g.w[1] = on_z ? b[i].Zl : b[i].Yl;
+      g.w[2] = nullptr;
+      g.ldt = pad8(rr);
+      g.C = b[i].G;
+      g.ldc = l;
+      g.M = l;
+      g.K = (int)rr;
+      g.ncol = l;
+      g.N = tg_n(l);
+      gram.push_back(g);
+      BChol c;
+      c.G = b[i].G;
+      c.R = (want_R && pass == 0) ? b[i].Racc : b[i].R;
+      c.Rinv = b[i].Rinv;
+      c.l = l;
+      P.chols.push_back(c);
+      TcSpec a;
+      a.A = src;
+      a.arows = rr;
+      a.acols = l;
+      a.lda = l;
+      a.w[0] = b[i].Rw[0];
+      a.w[1] = b[i].Rw[1];
+      a.w[2] = b[i].Rw[2];
+      a.ldt = pad8(l);
+      a.C = dst;
+      a.ldc = l;
+      a.M = (int)rr;
+      a.K = l;
+      a.ncol = l;
+      a.N = tg_n(l);
+      apply.push_back(a);
+    }
+    add_tc_stage(P, 1, 2, true, gram, encode);
+    P.stages.push_back(sc);
+    add_rinv_split(P, batch, it, p, b);
+    add_tc_stage(P, 0, 3, false, apply, encode);
+  }
+  if (want_R) {
+    Stage st{ST_TRMM, (int)P.trmms.size(), batch, 0};
+    for (int i = 0; i < batch; ++i) {
+      BTrmm t;
+      t.R = b[i].R;
+      t.Racc = b[i].Racc;
+      t.tmp = b[i].tmp;
+      t.l = it[i].k + p;
+      P.trmms.push_back(t);
+    }
+    P.stages.push_back(st);
+  }
 }
 
 // CholeskyQR2 of X (rows x l per problem, ld l) in place, through Xt; with
@@ -242,10 +433,10 @@ void add_orth(Plan& P, int batch, const rsvd_batch_item* it, int p, std::vector<
       P.chols.push_back(c);
       apply.push_back(gemm_of(src, l, 0, b[i].Rinv, l, dst, l, rows, l, l, l, i));
     }
-    add_gemm_stage(P, gram);
+    add_gemm_stage(P, gram, GK_GRAM);
     P.stages.push_back(ss);
     P.stages.push_back(sc);
-    add_gemm_stage(P, apply);
+    add_gemm_stage(P, apply, GK_APPLY);
   }
   if (want_R) {
     Stage st{ST_TRMM, (int)P.trmms.size(), batch, 0};
@@ -296,8 +487,24 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
       b[i].Yl = cv.take<uint16_t>((size_t)N * pad8(m));
       b[i].Zh = cv.take<uint16_t>((size_t)N * pad8(n));
       b[i].Zl = cv.take<uint16_t>((size_t)N * pad8(n));
+      for (int t = 0; t < 3; ++t) b[i].Rw[t] = cv.take<uint16_t>((size_t)N * pad8(l));
+    } else {
+      for (int t = 0; t < 3; ++t) b[i].Rw[t] = nullptr;
     }
   }
+  // the CholeskyQR steps take TMA maps of the samples, whose pitch (l
+  // floats) must be a multiple of 16 bytes
+  bool tc_orth = tc;
+  for (int i = 0; i < batch && tc_orth; ++i) tc_orth = ((it[i].k + p) % 4) == 0;
+  // the orthonormalisations of the power scheme only need a well-conditioned
+  // basis of the span: tensor cores; Q and Qh, which the returned U and V are
+  // lifted from, keep fp32 products
+  auto orth = [&](bool on_z, bool want_R, bool final_q) {
+    if (tc_orth && !final_q)
+      add_orth_tc(P, batch, it, p, b, on_z, want_R, enc);
+    else
+      add_orth(P, batch, it, p, b, on_z, want_R);
+  };
   if (tc) {
     // A at a 16-byte pitch, then Omega^T of every problem
     std::vector<int64_t> rows;
@@ -322,6 +529,7 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
       sp.ldw = 0;
       sp.hi = b[i].Oh;
       sp.lo = nullptr;
+      sp.lo2 = nullptr;
       sp.rows = it[i].n;
       sp.ldt = pad8(it[i].n);
       sp.l = l;
@@ -342,11 +550,11 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
       gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 0, nullptr, 0, b[i].Y, l,
                            it[i].m, l, it[i].n, l, i));
     }
-    add_gemm_stage(P, gs);
+    add_gemm_stage(P, gs, GK_SKETCH);
   }
   // power scheme, orthonormalising before every product (Alg. 5, s = 1)
   for (int j = 0; j < q; ++j) {
-    add_orth(P, batch, it, p, b, false, false);
+    orth(false, false, false);
     gs.clear();
     if (tc) {                           // Z = A^T Y
       add_split(P, batch, it, p, b, false);
@@ -357,9 +565,9 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
         gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 1, b[i].Y, l, b[i].Z, l,
                              it[i].n, l, it[i].m, l, i));
       }
-      add_gemm_stage(P, gs);
+      add_gemm_stage(P, gs, GK_PASS);
     }
-    add_orth(P, batch, it, p, b, true, false);
+    orth(true, false, false);
     gs.clear();
     if (tc) {                           // Y = A Z
       add_split(P, batch, it, p, b, true);
@@ -370,10 +578,10 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
         gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 0, b[i].Z, l, b[i].Y, l,
                              it[i].m, l, it[i].n, l, i));
       }
-      add_gemm_stage(P, gs);
+      add_gemm_stage(P, gs, GK_PASS);
     }
   }
-  add_orth(P, batch, it, p, b, false, false);   // Q = orth(Y)
+  orth(false, false, true);                     // Q = orth(Y)
   gs.clear();
   if (tc) {                                     // Bt = A^T Q
     add_split(P, batch, it, p, b, false);
@@ -384,9 +592,9 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
       gs.push_back(gemm_of(A ? A + it[i].a_off : nullptr, it[i].n, 1, b[i].Y, l, b[i].Z, l,
                            it[i].n, l, it[i].m, l, i));
     }
-    add_gemm_stage(P, gs);
+    add_gemm_stage(P, gs, GK_PASS);
   }
-  add_orth(P, batch, it, p, b, true, true);     // Bt = Qh Rh
+  orth(true, true, true);                       // Bt = Qh Rh
   {
     Stage st{ST_SVD, (int)P.svds.size(), batch, 0};   // Rh = Uh diag(Sh) Vh^T
     for (int i = 0; i < batch; ++i) {
@@ -402,14 +610,17 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
     P.stages.push_back(st);
   }
   gs.clear();
-  for (int i = 0; i < batch; ++i) {   // U = Q Vh(:, :k), V = Qh Uh(:, :k)
+  // U = Q Vh(:, :k), V = Qh Uh(:, :k): plain fp32 (the returned vectors keep
+  // 24 bits; the split products hold Q to 16)
+  for (int i = 0; i < batch; ++i) {
     const int l = it[i].k + p, k = it[i].k;
     gs.push_back(gemm_of(b[i].Y, l, 0, b[i].Vh, l, U ? U + it[i].u_off : nullptr, k, it[i].m, k,
                          l, k, i));
     gs.push_back(gemm_of(b[i].Z, l, 0, b[i].Uh, l, V ? V + it[i].v_off : nullptr, k, it[i].n, k,
                          l, k, i));
   }
-  add_gemm_stage(P, gs);
+  add_gemm_stage(P, gs, GK_LIFT);
+
   {
     Stage st{ST_SIGN, (int)P.signs.size(), batch, 0};
     for (int i = 0; i < batch; ++i) {
@@ -428,7 +639,7 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
   // the tables themselves
   *tables = cv.base ? cv.base + ((cv.off + 255) & ~(size_t)255) : nullptr;
   cv.take<BGemm>(P.gemms.size());
-  cv.take<int2>(P.tasks.size());
+  cv.take<int2>((size_t)std::max<int64_t>((int64_t)P.tasks.size(), P.tune_cap));   // any heights
   cv.take<BChol>(P.chols.size());
   cv.take<BTrmm>(P.trmms.size());
   cv.take<BSvd>(P.svds.size());
@@ -440,6 +651,7 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
   cv.take<TgPad>(P.pads.size());
   cv.take<TgSplit>(P.splits.size());
   cv.take<int2>(P.chunks.size());
+  cv.take<int2>((size_t)P.tune_cap);   // the tuner's candidate task lists
   return cv.off + 256;
 }
 
@@ -450,6 +662,22 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
 using namespace rsvd;
 
 extern "C" {
+
+int rsvd_batched_tuning(int cap, int* kind, int* width, int* rows, float* ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int i = 0;
+  for (const auto& kv : g_tune) {
+    if (i < cap) {
+      if (kind) kind[i] = kv.first.first;
+      if (width) width[i] = kv.first.second;
+      if (rows) rows[i] = kv.second.rows;
+      if (ms)
+        for (int h = 0; h < 3; ++h) ms[3 * i + h] = kv.second.ms[h];
+    }
+    ++i;
+  }
+  return i;
+}
 
 size_t rsvd_svd_batched_workspace_size(int batch, const rsvd_batch_item* items, int p, int q) {
   if (!items_ok(batch, items, p, q)) return 0;
@@ -480,7 +708,7 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
   cv.base = (char*)work;
   cv.off = (size_t)(tables - (char*)work);
   BGemm* dg = cv.take<BGemm>(P.gemms.size());
-  int2* dt = cv.take<int2>(P.tasks.size());
+  int2* dt = cv.take<int2>((size_t)std::max<int64_t>((int64_t)P.tasks.size(), P.tune_cap));
   BChol* dc = cv.take<BChol>(P.chols.size());
   BTrmm* dm = cv.take<BTrmm>(P.trmms.size());
   BSvd* dv = cv.take<BSvd>(P.svds.size());
@@ -510,6 +738,76 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
   UPLOAD(dsp, P.splits);
   UPLOAD(dch, P.chunks);
 #undef UPLOAD
+  int2* dtune = cv.take<int2>((size_t)P.tune_cap);
+  // classes of SIMT GEMMs not tuned yet: time each valid block height on this
+  // call's GEMMs of the class, keep the fastest, then rebuild the plan with
+  // the choices (the tables are uploaded again below)
+  {
+    std::map<std::pair<int, int>, std::vector<int>> todo;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      for (size_t g = 0; g < P.gemms.size(); ++g) {
+        const auto key = std::make_pair(P.gkind[g], P.gemms[g].N);
+        if (!g_tune.count(key)) todo[key].push_back((int)g);
+      }
+    }
+    if (!todo.empty()) {
+      cudaEvent_t e0, e1;
+      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return RSVD_ERR_CUDA;
+      std::vector<std::pair<std::pair<int, int>, TuneEntry>> found;
+      for (const auto& kv : todo) {
+        TuneEntry te;
+        te.rows = bgemm_rows(kv.first.second);
+        float best = -1.f;
+        for (int hi = 0; hi < 3; ++hi) {
+          const int rows = 64 << hi;
+          te.ms[hi] = -1.f;
+          if (!rows_valid(rows, kv.first.second)) continue;
+          std::vector<int2> tl;
+          for (int g : kv.second)
+            for (int r0 = 0; r0 < P.gemms[g].M; r0 += rows) tl.push_back(make_int2(g, r0));
+          if (tl.empty() || (int64_t)tl.size() > P.tune_cap) continue;
+          if (cudaMemcpyAsync(dtune, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                              s) != cudaSuccess ||
+              launch_bgemm(dg, dtune, (int)tl.size(), rows, seed, s) != cudaSuccess ||
+              cudaEventRecord(e0, s) != cudaSuccess ||
+              launch_bgemm(dg, dtune, (int)tl.size(), rows, seed, s) != cudaSuccess ||
+              cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return RSVD_ERR_CUDA;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          te.ms[hi] = ms;
+          if (best < 0.f || ms < best) {
+            best = ms;
+            te.rows = rows;
+          }
+        }
+        found.push_back(std::make_pair(kv.first, te));
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto& f : found) g_tune.emplace(f.first, f.second);
+      }
+      // the plan again, with the tuned heights (same tables, same carving)
+      Plan P2;
+      char* tables2 = nullptr;
+      build(batch, items, p, q, A, U, S, V, (char*)work, P2, &tables2, true);
+      if (P2.map_fail || tables2 != tables || (int64_t)P2.tasks.size() > P.tune_cap)
+        return RSVD_ERR_CUDA;
+      if (!P2.tasks.empty() &&
+          cudaMemcpyAsync(dt, P2.tasks.data(), P2.tasks.size() * sizeof(int2),
+                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return RSVD_ERR_CUDA;
+      P.stages = P2.stages;
+      P.tasks = P2.tasks;
+    }
+  }
   for (const Stage& st : P.stages) {
     cudaError_t e = cudaSuccess;
     switch (st.kind) {
@@ -522,8 +820,8 @@ rsvd_status rsvd_svd_batched(int batch, const rsvd_batch_item* items, int p, int
       case ST_SIGN: e = launch_sign_batched(dsg + st.first, st.count, s); break;
       case ST_SUM: e = launch_sum_batched(dsu + st.first, st.count, s); break;
       case ST_TCG:
-        e = launch_tc_group(st.form, st.nwt, dtp + st.first2, dtt + st.first, st.count,
-                            dtm + 3 * (int64_t)st.first2, d_info, s);
+        e = launch_tc_group(st.form, st.nwt, st.rows != 0, dtp + st.first2, dtt + st.first,
+                            st.count, dtm + 4 * (int64_t)st.first2, d_info, s);
         break;
       case ST_PAD: e = launch_pad_rows_batched(dpd, dch + st.first, st.count, s); break;
       case ST_SPLIT: e = launch_split_t_batched(dsp, dch + st.first, st.count, s); break;

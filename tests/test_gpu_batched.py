@@ -72,3 +72,29 @@ def test_svd_batched_rejects_bad_items():
         rs.svd_batched([A], [50], 8, 1, 1)          # l = 58 > n
     with pytest.raises(rs.RsvdError):
         rs.svd_batched([torch.zeros(300, 200, device=DEV)], [125], 8, 1, 1)   # l > 128
+
+
+def test_batched_autotuner_choices_and_repeatability():
+    """The tile autotuner keeps, per GEMM class, the fastest valid block height
+    it measured; a later call with the tuned heights in place gives the same
+    bits (every height computes each entry by the same multiply-adds)."""
+    p, q, seed = 8, 1, 0x70E
+    sizes = [(700, 300, 8), (900, 500, 16), (400, 300, 32), (1200, 640, 64)]
+    mats = [torch.from_numpy(make_matrix_np(m, n, spectrum("expk", min(n, 6 * k), k),
+                                            seed=90 + i, dtype="float32")).to(DEV)
+            for i, (m, n, k) in enumerate(sizes)]
+    first = rs.svd_batched(mats, [s[2] for s in sizes], p, q, seed)
+    tune = rs.batched_tuning()
+    assert tune, "no tuned class"
+    for t in tune:
+        assert t["rows"] in (64, 128, 256)
+        valid = [(ms, 64 << h) for h, ms in enumerate(t["ms"]) if ms is not None]
+        assert valid, t
+        assert min(valid)[1] == t["rows"] or min(valid)[0] == t["ms"][t["rows"].bit_length() - 7], t
+        # a block is 8192 / rows columns wide: only heights whose block covers N
+        for h, ms in enumerate(t["ms"]):
+            assert (ms is not None) == (t["width"] <= 8192 // (64 << h)), t
+    second = rs.svd_batched(mats, [s[2] for s in sizes], p, q, seed)
+    for a, b in zip(first, second):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
