@@ -495,6 +495,8 @@ def batched_line(rs, args, world, dev, peaks, peak_kind, name="c4_f32_batched512
     torch.cuda.synchronize()
     rs.check_info(plan.info, "batched warmup")
     stream = torch.cuda.current_stream()
+    rs.trace_enable(True)
+    rs.trace_read()
     launches0 = rs.kernel_launch_count()
     barrier(world)
     torch.cuda.synchronize()
@@ -507,6 +509,8 @@ def batched_line(rs, args, world, dev, peaks, peak_kind, name="c4_f32_batched512
     torch.cuda.synchronize()
     barrier(world)
     launches = (rs.kernel_launch_count() - launches0) / args.steps
+    trace = rs.trace_read()
+    rs.trace_enable(False)
     rs.check_info(plan.info, "batched steps")
     ms_b = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     # the same problems through the single-problem FP32 path, one call each
@@ -529,6 +533,20 @@ def batched_line(rs, args, world, dev, peaks, peak_kind, name="c4_f32_batched512
     a_bytes = sum(4.0 * m * n for m, n in zip(ms, ns))
     gbs = (2 * q + 2) * a_bytes / (ms_b * 1e-3) / 1e9
     eb, es = float(np.mean(errs_b)), float(np.mean(errs_s))
+    # the grouped tensor-core passes over A (trace classes of the library's stream)
+    tc_cls = [c for c in ("a_omega", "a_w", "at_w") if c in trace]
+    tc_ms = sum(trace[c][0] for c in tc_cls) / args.steps
+    tc_n = sum(trace[c][1] for c in tc_cls) / args.steps
+    tc_pass = None
+    if tc_n > 0 and tc_ms > 0:
+        g = tc_n * a_bytes / (tc_ms * 1e-3) / 1e9
+        tc_pass = {"kernel": "tc_group_kernel (grouped tcgen05, one launch per pass over all A_i)",
+                   "passes": tc_n, "ms_per_pass": tc_ms / tc_n, "achieved": g,
+                   "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": g / peaks["hbm_gbs"],
+                   "peak_source": peak_kind + " STREAM-style copy",
+                   "work": "one read of every A_i (4 B per entry) per pass"}
+    classes = {c: {"ms_per_step": trace[c][0] / args.steps,
+                   "launches_per_step": trace[c][1] / args.steps} for c in trace}
     return {
         "workload": "%s: %d FP32 problems, m in [%d, %d], n in [%d, %d], k in %s, p = %d, q = %d, "
                     "sigma_j = exp(-j/k)" % (name, len(ms), min(ms), max(ms), min(ns), max(ns),
@@ -545,6 +563,9 @@ def batched_line(rs, args, world, dev, peaks, peak_kind, name="c4_f32_batched512
         "a_pass_hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_kind + " STREAM-style copy",
                        "work": "(2q + 2) reads of every A_i per step (4 B per entry), whole-step time"},
+        "tc_pass_hbm": tc_pass,
+        "kernels": classes,
+        "autotuner": rs.batched_tuning(),
     }
 
 

@@ -83,12 +83,23 @@ typedef enum {
   RSVD_PREC_TC = 0,   /* FP32 inputs: tcgen05 tensor-core products of bf16 splits
                          (two-term split of each fp32 operand, fp32 accumulation) */
   RSVD_PREC_SIMT = 1, /* FP32 inputs: plain fp32 FMA kernels (slower; cross-check) */
-  RSVD_PREC_MIXED = 2 /* FP32 or BF16 inputs, tensor cores: the passes of the power
+  RSVD_PREC_MIXED = 2,/* FP32 or BF16 inputs, tensor cores: the passes of the power
                          scheme (Z = A^T Y, Y = A Z) take one bf16 term of A and of the
                          stored operand, one product per K-step; the sketch
                          Y = A Omega, the orthonormalisations and Bt = A^T Q keep the
                          RSVD_PREC_TC arithmetic (the subspace iteration tolerates
                          bf16 rounding, the projection onto it does not) */
+  RSVD_PREC_FP8 = 3   /* FP32 or BF16 inputs, tensor cores: the sketch Y = A Omega
+                         takes A and Omega quantised to FP8 E4M3 (round to nearest
+                         even, saturating at 448) with one power-of-two scale per
+                         block of 32 entries along the contraction, 2^ceil(log2(
+                         amax / 448)) (the block-scaled 8-bit format); a scaled
+                         E4M3 value is exact in bf16, so the products run as bf16
+                         tensor-core products with fp32 accumulation and give the
+                         FP8 sketch's values.  Omega is rounded to bf16 before its
+                         quantisation (as on the FP32 path) and its quantised
+                         transpose is generated once per call into the workspace.
+                         Every other product as RSVD_PREC_TC. */
 } rsvd_precision;
 
 /* Options.  Pass NULL for the defaults set by rsvd_opts_default(). */
@@ -353,6 +364,13 @@ rsvd_status rsvd_svd_vjp(int64_t m, int64_t n, int k, int p, int q, uint64_t see
  * Intended for checking the stream; the path never stores Omega. */
 rsvd_status rsvd_omega(int64_t n, int l, uint64_t seed, int dtype, void* Omega,
                        int64_t ldo, void* stream);
+
+/* Omega of the FP8 sketch (RSVD_PREC_FP8), n x l floats (ldo >= l): the bf16
+ * Omega of rsvd_omega quantised to E4M3 with one power-of-two scale per block
+ * of 32 rows of each column, times that scale, exactly as the sketch uses it.
+ * Intended for checking. */
+rsvd_status rsvd_omega_fp8(int64_t n, int l, uint64_t seed, float* Omega, int64_t ldo,
+                           void* stream);
 
 /* The raw Philox4x32-10 words behind Omega: out is n x ceil(l/4) x 4 uint32,
  * word t of counter (i, q, 0, 0) at out[(i*ceil(l/4) + q)*4 + t]. */

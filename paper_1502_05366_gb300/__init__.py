@@ -24,7 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librsvd.so")
 
 F32, F64, BF16 = 0, 1, 2
-PREC_TC, PREC_SIMT, PREC_MIXED = 0, 1, 2
+PREC_TC, PREC_SIMT, PREC_MIXED, PREC_FP8 = 0, 1, 2, 3
 
 STATUS = {
     0: "RSVD_OK", 1: "RSVD_ERR_INVALID_ARG", 2: "RSVD_ERR_WORKSPACE", 3: "RSVD_ERR_CUDA",
@@ -82,6 +82,7 @@ _SIGS = {
                                  _vp, _vp, _c_i64, _vp, _c_size, _vp, _vp, _OPTP]),
     "rsvd_omega": (_c_int, [_c_i64, _c_int, _c_u64, _c_int, _vp, _c_i64, _vp]),
     "rsvd_omega_words": (_c_int, [_c_i64, _c_int, _c_u64, _vp, _vp]),
+    "rsvd_omega_fp8": (_c_int, [_c_i64, _c_int, _c_u64, _vp, _c_i64, _vp]),
     "rsvd_sample_workspace_size": (_c_size, [_c_i64, _c_i64, _c_int, _c_int, _OPTP]),
     "rsvd_sample": (_c_int, [_c_i64, _c_i64, _c_int, _c_u64, _c_int, _vp, _c_i64, _vp, _c_i64,
                              _vp, _c_size, _vp, _OPTP]),
@@ -664,6 +665,15 @@ def omega(n, l, seed, dtype, device="cuda"):
     Om = torch.empty(n, l, dtype=dtype, device=device)
     dt = {torch.float32: F32, torch.float64: F64}[dtype]
     _raise(lib().rsvd_omega(n, l, seed, dt, _ptr(Om), l, _stream()), "rsvd_omega")
+    return Om
+
+
+def omega_fp8(n, l, seed, device="cuda"):
+    """Omega of the FP8 sketch (rsvd_omega_fp8): n x l float32, the bf16 Omega
+    quantised to E4M3 with a power-of-two scale per 32-row block of each column."""
+    torch = _torch()
+    Om = torch.empty(n, l, dtype=torch.float32, device=device)
+    _raise(lib().rsvd_omega_fp8(n, l, seed, _ptr(Om), l, _stream()), "rsvd_omega_fp8")
     return Om
 
 

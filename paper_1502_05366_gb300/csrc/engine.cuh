@@ -27,7 +27,7 @@ static bool read_opts(const rsvd_opts* o, Opts* out) {
   if (o) {
     if (o->s < 1 || o->max_sweeps < 1 || o->max_sweeps > 1000) return false;
     if (o->precision != RSVD_PREC_TC && o->precision != RSVD_PREC_SIMT &&
-        o->precision != RSVD_PREC_MIXED)
+        o->precision != RSVD_PREC_MIXED && o->precision != RSVD_PREC_FP8)
       return false;
     for (int i = 0; i < 13; ++i)
       if (o->reserved[i] != 0) return false;
@@ -96,6 +96,18 @@ struct Engine {
     sms = device_sm_count();
   }
 
+  // FP8 sketch (RSVD_PREC_FP8): the quantised Omega^T (L x omq_ld bf16),
+  // generated once per call by the first sketch product.
+  uint16_t* omq = nullptr;
+  int64_t omq_ld = 0;
+  bool omq_done = false;
+  void take_omq(int64_t n, int L) {
+    if (tc && o.precision == RSVD_PREC_FP8) {
+      omq_ld = pad8(n);
+      omq = c.template take<uint16_t>((size_t)L * omq_ld);
+    }
+  }
+
   // Split-transposed bf16 operand buffers (L x ld rows).
   struct Split {
     void* hi = nullptr;
@@ -117,11 +129,25 @@ struct Engine {
                      int64_t a_cols, bool omega, uint64_t seed, int lvalid, const Split* w,
                      const T* Wsimt, int64_t ldws, T* out, int64_t ldo, int ncols, Split* out_split,
                      float* part, const int* skip, bool a_bf16 = false) {
+    // the FP8 sketch exists on the tensor-core path only
+    if (omega && o.precision == RSVD_PREC_FP8 && !tc) return RSVD_ERR_UNSUPPORTED;
     if (tc) {
       TcGemm g{};
       g.form = 0;
       g.a_bf16 = a_bf16 ? 1 : 0;
       g.omega = omega ? 1 : 0;
+      if (omega && o.precision == RSVD_PREC_FP8) {
+        // Y = q(A) q(Omega): A quantised by the GEMM's converters, Omega^T
+        // quantised once into the workspace
+        if (!omq && !c.dry) return RSVD_ERR_INVALID_ARG;
+        if (!omq_done) {
+          LK(launch_omega_fp8_t(K, lvalid, L, seed, omq, omq_ld, c.stream));
+          omq_done = true;
+        }
+        g.omega = 0;
+        g.q8 = 1;
+        w = nullptr;
+      }
       g.seed = seed;
       g.rows = rows;
       g.K = K;
@@ -136,6 +162,12 @@ struct Engine {
       g.Wlo2 = w ? w->lo2 : nullptr;
       g.wterms = (w && !w->lo) ? 1 : ((w && w->lo2) ? 3 : 2);
       g.ldw = w ? w->ld : 0;
+      if (g.q8) {
+        g.Whi = omq;
+        g.Wlo = g.Wlo2 = nullptr;
+        g.wterms = 1;
+        g.ldw = omq_ld;
+      }
       g.part = part;
       g.out = (float*)out;
       g.ldo = ldo;
@@ -345,6 +377,7 @@ struct Engine {
     }
     b.slabs = se ? c.template take<T>(se) : nullptr;
     b.ob = take_orth_bufs(L);
+    take_omq(n, L);
     return b;
   }
 
@@ -814,7 +847,7 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // TMA-addressable (16-byte aligned base and rows).
 static bool want_tc(int dtype, const Opts& o, int l, const void* A, int64_t lda) {
   if (dtype != RSVD_F32 && dtype != RSVD_BF16) return false;
-  if (o.precision != RSVD_PREC_TC && o.precision != RSVD_PREC_MIXED) return false;
+  if (o.precision == RSVD_PREC_SIMT) return false;
   if (padL(l) > 1024) return false;   // widths above 256 run in column chunks
   if (A && !aligned16(A)) return false;
   if (lda % (dtype == RSVD_BF16 ? 8 : 4) != 0) return false;

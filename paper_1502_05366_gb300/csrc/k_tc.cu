@@ -39,6 +39,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "fp8.cuh"
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -70,7 +71,7 @@ __device__ __forceinline__ int64_t sk_start(int64_t b, int64_t total, int64_t G)
   return (b * total) / G;
 }
 
-template <int FORM, int NW, bool ABF>
+template <int FORM, int NW, bool ABF, bool Q8 = false>
 __global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                    const __grid_constant__ CUtensorMap mapW0,
@@ -246,7 +247,36 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_after();
       const unsigned char* st = dsm + s * SB;
       const uint32_t a_col = tmem + TMEM_A0 + 32u * (uint32_t)s;
-      if (ABF) {
+      if (Q8) {
+        // FP8 sketch (form 0): the row's 32 values of this K-chunk are one
+        // block; quantised to E4M3 with its scale, exact in bf16 (one term)
+        float x[32];
+        if (ABF) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint4 v = *reinterpret_cast<const uint4*>(st + sw64_off((uint32_t)r, (uint32_t)c));
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              x[8 * c + 2 * e] = __uint_as_float(wv[e] << 16);
+              x[8 * c + 2 * e + 1] = __uint_as_float(wv[e] & 0xffff0000u);
+            }
+          }
+        } else {
+          const unsigned char* row = st + r * 128;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 v = *reinterpret_cast<const float4*>(row + ((c ^ (r & 7)) << 4));
+            x[4 * c] = v.x;
+            x[4 * c + 1] = v.y;
+            x[4 * c + 2] = v.z;
+            x[4 * c + 3] = v.w;
+          }
+        }
+        uint32_t hi[16];
+        e4m3_block_bf16(x, hi);
+        tmem_st16(lane_base + a_col, hi);
+      } else if (ABF) {
         // bf16 A: the tile row (form 0, 64-byte swizzled rows of 32 values) or
         // column (form 1, plain 32 x 128 tile) goes to TMEM as it is
         uint32_t hi[16];
@@ -543,16 +573,17 @@ cudaError_t launch_tc_reduce(const TcParams& P, int G, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int FORM, int NW, bool ABF = false>
+template <int FORM, int NW, bool ABF = false, bool Q8 = false>
 static cudaError_t launch_form(const CUtensorMap& ma, const CUtensorMap* mw, const TcParams& P,
                                int G, size_t smem, cudaStream_t s) {
-  auto kern = tc_gemm_kernel<FORM, NW, ABF>;
+  auto kern = tc_gemm_kernel<FORM, NW, ABF, Q8>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   // trace classes (include/rsvd.h): 0 A Omega, 1 A W, 2 A^T W, 3 Gram, 4 orth apply
-  const int cls = FORM == 1 ? (NW == 4 ? RSVD_TRACE_GRAM : RSVD_TRACE_AT_W)
-                            : (NW == 3 ? RSVD_TRACE_APPLY : RSVD_TRACE_A_W);
+  const int cls = Q8 ? RSVD_TRACE_A_OMEGA
+                     : (FORM == 1 ? (NW == 4 ? RSVD_TRACE_GRAM : RSVD_TRACE_AT_W)
+                                  : (NW == 3 ? RSVD_TRACE_APPLY : RSVD_TRACE_A_W));
   const int tr = trace_begin(cls, s);
   kern<<<G, 256, smem, s>>>(ma, mw[0], mw[1], mw[2], P);
   count_launch();
@@ -590,8 +621,9 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   if (!tc_supported(g.L)) return cudaErrorInvalidValue;
   if (g.form == 1 && g.omega) return cudaErrorInvalidValue;
   if (g.form == 0 && g.omega) return launch_tc_omega(g, s);
+  if (g.q8 && (g.form != 0 || g.wterms != 1 || g.gram)) return cudaErrorInvalidValue;
   // the passes over A with a stored operand: two M-tiles per CTA (k_tc2.cu)
-  if (tc_unit_supported(g)) return launch_tc_unit(g, s);
+  if (!g.q8 && tc_unit_supported(g)) return launch_tc_unit(g, s);
   int64_t tiles, kiters, total, G;
   int maxseg;
   const int sms = device_sm_count();
@@ -662,7 +694,10 @@ cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s) {
   const size_t smem = (size_t)stages_for(nw) * stage_bytes(g.L, nw) + 1024 /*align*/ +
                       (4 * MAXST + 2) * 8 + 16;
   cudaError_t e;
-  if (nw == 1)
+  if (g.q8)
+    e = abf ? launch_form<0, 1, true, true>(ma, mw, P, (int)G, smem, s)
+            : launch_form<0, 1, false, true>(ma, mw, P, (int)G, smem, s);
+  else if (nw == 1)
     e = g.form == 0 ? (abf ? launch_form<0, 1, true>(ma, mw, P, (int)G, smem, s)
                            : launch_form<0, 1, false>(ma, mw, P, (int)G, smem, s))
                     : (abf ? launch_form<1, 1, true>(ma, mw, P, (int)G, smem, s)

@@ -14,6 +14,13 @@ template <typename T>
 cudaError_t launch_omega(int64_t n, int l, uint64_t seed, T* Om, int64_t ldo, cudaStream_t s,
                          uint32_t tag = 0);
 cudaError_t launch_omega_words(int64_t n, int l, uint64_t seed, uint32_t* out, cudaStream_t s);
+// Omega of the FP8 sketch (k_fp8.cu): bf16 Gaussians quantised to E4M3 with a
+// power-of-two scale per 32-row block of each column; transposed bf16 (L x ldt,
+// rows >= l zero; L a multiple of 4) or n x l floats (checking aid).
+cudaError_t launch_omega_fp8_t(int64_t n, int l, int L, uint64_t seed, uint16_t* out, int64_t ldt,
+                               cudaStream_t s);
+cudaError_t launch_omega_fp8(int64_t n, int l, uint64_t seed, float* out, int64_t ldo,
+                             cudaStream_t s);
 
 // ----- SIMT GEMMs (k_simt.cu) ----------------------------------------------
 // C (M x N) = A (M x K) * B (K x N); B = Omega(seed) when B == nullptr, with
@@ -221,6 +228,9 @@ struct TcGemm {
   int* d_info;
   int drain;            // stored-operand passes: K-chunks per TMEM accumulation run
                         // (0 = one run per stream-K segment); see tc_unit_kernel
+  int q8;               // form 0, one stored W term: every 32-value K-chunk of each A
+                        // row quantised to E4M3 with its power-of-two scale (fp8.cuh)
+                        // before the product (the FP8 sketch; W = its quantised Omega^T)
 };
 size_t tc_part_bytes(int64_t rows, int64_t K, int L);
 cudaError_t launch_tc_gemm(const TcGemm& g, cudaStream_t s);

@@ -254,6 +254,7 @@ static size_t ws_query(int64_t m, int64_t n, int k, int p, int q, int dtype,
   Opts o;
   if (!read_opts(opts, &o) || !base_args_ok(m, n, k, p, q, dtype)) return 0;
   const bool tc = want_tc(dtype, o, k + p, nullptr, 0);
+  if (o.precision == RSVD_PREC_FP8 && !tc) return 0;   // FP8 sketch: tensor cores only
   if (dtype == RSVD_F64) return size_all<double>(o, false, m, n, k, p, want);
   if (dtype == RSVD_BF16) return tc ? size_all<float>(o, true, m, n, k, p, want) : 0;
   // Both variants may be chosen at call time (alignment of A): report the max.
@@ -345,6 +346,7 @@ static size_t ws_query_ext(int64_t m, int64_t n, int kmax, int p, int q, int dty
     return c.off + 256;
   };
   const bool tc = want_tc(dtype, o, kmax + p, nullptr, 0);
+  if (o.precision == RSVD_PREC_FP8 && !tc) return 0;   // FP8 sketch: tensor cores only
   if (dtype == RSVD_F64) return one(false, double{});
   if (dtype == RSVD_BF16) return tc ? one(true, float{}) : 0;
   const size_t s1 = one(false, float{});
@@ -663,6 +665,7 @@ size_t rsvd_qb_adaptive_workspace_size(int64_t m, int64_t n, int b, int M, int q
   if (!read_opts(opts, &o) || !qb_adaptive_args_ok(m, n, b, M, q, dtype)) return 0;
   if (dtype == RSVD_F64) return size_qb_adaptive<double>(o, false, m, n, b, M);
   const bool tc = want_tc(dtype, o, b, nullptr, 0);
+  if (o.precision == RSVD_PREC_FP8 && !tc) return 0;   // FP8 sketch: tensor cores only
   size_t s1 = size_qb_adaptive<float>(o, false, m, n, b, M);
   size_t s2 = tc ? size_qb_adaptive<float>(o, true, m, n, b, M) : 0;
   return s1 > s2 ? s1 : s2;
@@ -722,6 +725,7 @@ static rsvd_status sample_impl(Ctx& c, const Opts& o, bool tc, int64_t m, int64_
   Engine<T> e(c, o, tc);
   const int L = padL(l);
   float* part = tc ? c.template take<float>(tc_part_bytes(m, n, L) / sizeof(float)) : nullptr;
+  e.take_omq(n, L);
   if (c.dry) return RSVD_OK;
   if (c.off > c.cap) return RSVD_ERR_WORKSPACE;
   return e.gemm_n(m, n, L, A, lda, m, n, true, seed, l, nullptr, nullptr, 0, Y, ldy, l, nullptr,
@@ -849,6 +853,15 @@ rsvd_status rsvd_omega(int64_t n, int l, uint64_t seed, int dtype, void* Omega, 
   return e == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
 }
 
+rsvd_status rsvd_omega_fp8(int64_t n, int l, uint64_t seed, float* Omega, int64_t ldo,
+                           void* stream) {
+  if (n < 1 || l < 1 || l > 4096 || !Omega || ldo < l || n > 0xffffffffLL)
+    return RSVD_ERR_INVALID_ARG;
+  return launch_omega_fp8(n, l, seed, Omega, ldo, (cudaStream_t)stream) == cudaSuccess
+             ? RSVD_OK
+             : RSVD_ERR_CUDA;
+}
+
 rsvd_status rsvd_omega_words(int64_t n, int l, uint64_t seed, uint32_t* out, void* stream) {
   if (n < 1 || l < 1 || !out || ((uintptr_t)out & 15u)) return RSVD_ERR_INVALID_ARG;
   if (n > 0xffffffffLL) return RSVD_ERR_INVALID_ARG;
@@ -866,6 +879,7 @@ size_t rsvd_sample_workspace_size(int64_t m, int64_t n, int l, int dtype, const 
   Ctx c;
   const bool tc = want_tc(dtype, o, l, nullptr, 0);
   if (dtype == RSVD_BF16 && !tc) return 0;
+  if (o.precision == RSVD_PREC_FP8 && !tc) return 0;   // FP8 sketch: tensor cores only
   if (dtype == RSVD_F64)
     sample_impl<double>(c, o, false, m, n, l, 0, nullptr, n, nullptr, l);
   else

@@ -506,9 +506,16 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
       add_orth(P, batch, it, p, b, on_z, want_R);
   };
   if (tc) {
-    // A at a 16-byte pitch, then Omega^T of every problem
+    // A at a 16-byte pitch (a copy unless the problem's rows already are:
+    // n a multiple of 4 and A_i 16-byte aligned), then Omega^T of every problem
     std::vector<int64_t> rows;
+    const int j0p = (int)P.pads.size();
     for (int i = 0; i < batch; ++i) {
+      const float* Ai = A ? A + it[i].a_off : nullptr;
+      if (Ai && it[i].n % 4 == 0 && ((uintptr_t)Ai & 15u) == 0) {
+        b[i].Ap = const_cast<float*>(Ai);   // read in place (TMA loads only)
+        continue;
+      }
       TgPad pd;
       pd.src = A ? A + it[i].a_off : nullptr;
       pd.dst = b[i].Ap;
@@ -519,7 +526,7 @@ size_t build(int batch, const rsvd_batch_item* it, int p, int q, const float* A,
       P.pads.push_back(pd);
       rows.push_back(it[i].m);
     }
-    add_chunks(P, 0, rows, ST_PAD);
+    add_chunks(P, j0p, rows, ST_PAD);
     rows.clear();
     const int j0 = (int)P.splits.size();
     for (int i = 0; i < batch; ++i) {

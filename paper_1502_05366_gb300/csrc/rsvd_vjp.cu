@@ -274,6 +274,7 @@ size_t rsvd_svd_vjp_workspace_size(int64_t m, int64_t n, int k, int p, int q, in
   if (!read_opts(opts, &o) || !vjp_args_ok(m, n, k, p, q, dtype)) return 0;
   if (dtype == RSVD_F64) return vjp_size<double>(o, false, m, n, k, p, q);
   const bool tc = want_tc(dtype, o, k + p, nullptr, 0);
+  if (o.precision == RSVD_PREC_FP8 && !tc) return 0;   // FP8 sketch: tensor cores only
   const size_t s1 = vjp_size<float>(o, false, m, n, k, p, q);
   const size_t s2 = tc ? vjp_size<float>(o, true, m, n, k, p, q) : 0;
   return s1 > s2 ? s1 : s2;

@@ -96,8 +96,14 @@ def test_bf16_and_mixed_workspace_queries(lib):
     mixed = rs.make_opts(precision=rs.PREC_MIXED)
     assert lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.F32, ctypes.byref(mixed)) > 0
     bad = rs.make_opts()
-    bad.precision = 3
+    bad.precision = 4
     assert lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.F32, ctypes.byref(bad)) == 0
+    # the FP8 sketch: tensor-core path only (FP32 or BF16 A), with its Omega^T
+    fp8 = rs.make_opts(precision=rs.PREC_FP8)
+    plain = lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.F32, None)
+    assert lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.F32, ctypes.byref(fp8)) > plain
+    assert lib.rsvd_svd_workspace_size(3000, 2000, 40, 10, 2, rs.F64, ctypes.byref(fp8)) == 0
+    assert lib.rsvd_sample_workspace_size(3000, 2000, 50, rs.F64, ctypes.byref(fp8)) == 0
     # widths above 256 (column chunks) up to 1024 on the tensor-core path
     assert lib.rsvd_svd_workspace_size(100000, 50000, 500, 50, 2, rs.BF16, None) > 0
     assert lib.rsvd_svd_workspace_size(100000, 50000, 1000, 50, 2, rs.BF16, None) == 0
