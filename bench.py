@@ -435,13 +435,17 @@ def mixed_precision_line(rs, A, plan32, cfg, args, seed, world, dev, ms32, peaks
     path's (equal-error comparison):
       bf16_storage        A held as bf16 (RSVD_BF16), RSVD_PREC_TC arithmetic;
       bf16_storage_mixed  A as bf16 and single-term bf16 power scheme (RSVD_PREC_MIXED);
-      f32_mixed           fp32 A, single-term bf16 power scheme (RSVD_PREC_MIXED)."""
+      f32_mixed           fp32 A, single-term bf16 power scheme (RSVD_PREC_MIXED);
+      f32_fp8_sketch      fp32 A, the sketch Y = A Omega on E4M3-quantised A and Omega
+                          with 32-entry block scales (RSVD_PREC_FP8);
+      bf16_fp8_sketch     the same with A held as bf16."""
     import torch
     m, n, k, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["q"]
     flops = step_flops(m, n, k, p, q)
     e32 = rel_err_device(rs, A, plan32.U, plan32.S, plan32.V)
     Ab = A.to(torch.bfloat16)
     mixed_opts = rs.make_opts(precision=rs.PREC_MIXED)
+    fp8_opts = rs.make_opts(precision=rs.PREC_FP8)
     out = {"rel_err_fp32": e32,
            "rel_err_definition": "||A - U S V^T||_F / ||A||_F against the FP32 A",
            "fp32_ms_per_step": ms32}
@@ -453,7 +457,13 @@ def mixed_precision_line(rs, A, plan32, cfg, args, seed, world, dev, ms32, peaks
              "A in bf16 and RSVD_PREC_MIXED: the power scheme's passes take one bf16 term "
              "of the stored operand (one product per K-step); Bt = A^T Q split"),
             ("f32_mixed", A, mixed_opts, 4,
-             "fp32 A and RSVD_PREC_MIXED: the power scheme's passes take a0 w0 only")):
+             "fp32 A and RSVD_PREC_MIXED: the power scheme's passes take a0 w0 only"),
+            ("f32_fp8_sketch", A, fp8_opts, 4,
+             "fp32 A and RSVD_PREC_FP8: the sketch on E4M3-quantised A and Omega (one "
+             "power-of-two scale per 32 entries along the contraction), products of the exact "
+             "dequantised values on the bf16 tensor cores; the rest as the FP32 path"),
+            ("bf16_fp8_sketch", Ab, fp8_opts, 2,
+             "A in bf16 and RSVD_PREC_FP8: the FP8 sketch of the bf16 values")):
         ms, trace, plan = _time_variant(rs, Ad, opts, cfg, args, seed, world, dev)
         e = rel_err_device(rs, A, plan.U, plan.S, plan.V)
         pass_ms = sum(v[0] for c, v in trace.items()
