@@ -402,11 +402,18 @@ __global__ void __launch_bounds__(256, 1)
 // is handled by the first boundary inside it; the block sums one 32 x 32
 // sub-tile over the contributing CTAs in increasing order and writes the fp32
 // output and, when requested, the transposed bf16 split (padding zero).
-__global__ void tc_reduce_kernel(TcParams P, int G) {
+// The boundaries that start a split tile (the only ones with work), found on
+// the host; n = 0: every boundary b = blockIdx.y + 1 (more than 256 CTAs).
+struct RedList {
+  int n;
+  int b[256];
+};
+
+__global__ void tc_reduce_kernel(TcParams P, int G, const __grid_constant__ RedList R) {
   if (P.skip && *P.skip) return;
   __shared__ float tile_s[32][33];
   __shared__ int64_t s_base[1024];
-  const int64_t b = (int64_t)blockIdx.y + 1;
+  const int64_t b = R.n > 0 ? (int64_t)R.b[blockIdx.y] : (int64_t)blockIdx.y + 1;
   const int64_t sb = (b * P.total) / G;
   const int64_t t = sb / P.kiters;
   if (sb == t * P.kiters) return;                           // boundary at a tile start
@@ -565,9 +572,26 @@ size_t tc_part_bytes(int64_t rows, int64_t K, int L) {
 
 cudaError_t launch_tc_reduce(const TcParams& P, int G, cudaStream_t s) {
   if (G <= 1) return cudaSuccess;
-  dim3 rgrid((unsigned)((P.bm / 32) * ceil_div(P.L, 32)), (unsigned)(G - 1));
+  // the kernel's own test, on the host: boundary b = start of CTA b works iff
+  // it falls inside a tile and is the first boundary inside that tile
+  RedList R;
+  R.n = 0;
+  int ny = G - 1;
+  if (G - 1 <= 256) {
+    for (int64_t b = 1; b < G; ++b) {
+      const int64_t sb = (b * P.total) / G;
+      const int64_t t = sb / P.kiters;
+      if (sb == t * P.kiters) continue;
+      const int64_t sprev = ((b - 1) * P.total) / G;
+      if (b - 1 >= 1 && sprev > t * P.kiters) continue;
+      R.b[R.n++] = (int)b;
+    }
+    if (R.n == 0) return cudaSuccess;   // no tile is split between CTAs
+    ny = R.n;
+  }
+  dim3 rgrid((unsigned)((P.bm / 32) * ceil_div(P.L, 32)), (unsigned)ny);
   const int tr = trace_begin(RSVD_TRACE_REDUCE, s);
-  tc_reduce_kernel<<<rgrid, dim3(32, 8), 0, s>>>(P, G);
+  tc_reduce_kernel<<<rgrid, dim3(32, 8), 0, s>>>(P, G, R);
   count_launch();
   trace_end(tr, s);
   return cudaGetLastError();
