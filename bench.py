@@ -487,6 +487,134 @@ def mixed_precision_line(rs, A, plan32, cfg, args, seed, world, dev, ms32, peaks
     return out
 
 
+C3_NAME = "c3_bf16_100000x50000"
+C3_GOLDEN = os.path.join(ROOT, "tests", "golden", "c3_reduced_oracle.txt")
+C3_RANKS = (1, 10, 50, 100, 200, 300, 400, 500)
+
+
+def load_c3_golden(path=C3_GOLDEN):
+    """(sizes, values) of the stored FP64-oracle results for the reduced matrix of
+    the mixed-precision recipe: sizes from the '# m .. n ..' header line, values
+    rel_err_<A> (float) and sigma_<A> (array) for A = f32 and bf16."""
+    meta, vals = {}, {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# m "):
+                t = line[2:].split()
+                meta = {t[i]: t[i + 1] for i in range(0, len(t) - 1, 2)}
+            elif line.startswith("#") or not line.strip():
+                continue
+            else:
+                key, *v = line.split()
+                vals[key] = (np.array([float(x) for x in v]) if key.startswith("sigma_")
+                             else float(v[0]))
+    return meta, vals
+
+
+def c3_variants(rs):
+    """(name, storage, opts, description) of the mixed-precision workload's forms."""
+    import torch
+    mixed = rs.make_opts(precision=rs.PREC_MIXED)
+    fp8 = rs.make_opts(precision=rs.PREC_FP8)
+    return (
+        ("f32", torch.float32, None,
+         "fp32 A; split-bf16 tensor-core products, fp32 accumulation (the plain FP32 path)"),
+        ("bf16", torch.bfloat16, None,
+         "A stored as bf16; exact bf16 products, fp32 accumulation; Bt = A^T Q with Q split "
+         "into bf16 terms"),
+        ("bf16_mixed", torch.bfloat16, mixed,
+         "A as bf16; the power scheme's passes take one bf16 term of the stored operand"),
+        ("bf16_fp8_sketch", torch.bfloat16, fp8,
+         "A as bf16; the sketch Y = A Omega on E4M3-quantised A and Omega with one power-of-two "
+         "scale per 32 entries along the contraction"),
+        ("f32_fp8_sketch", torch.float32, fp8,
+         "fp32 A; the same FP8 sketch"),
+    )
+
+
+def c3_line(rs, args, world, dev, peaks, peak_kind):
+    """The mixed-precision workload (m = 100000, n = 50000, k = 500, p = 50, q = 2,
+    sigma_j = exp(-j/100) + 1e-3 on r = 2000 directions, 1e-4 noise) in each form
+    of c3_variants: the whole step (QB + SVD + ID + CUR) timed like the main line
+    at full size and judged by ||A - U S V^T||_F / ||A||_F against the FP32 A
+    (equal-error comparison).  The error against the FP64 oracle at every rank
+    i <= k is taken on the reduced matrix of the same recipe whose oracle results
+    are stored (tests/golden/c3_reduced_oracle.txt): each form's sigma_i against
+    the oracle's on the same storage, and its relative error against the oracle's."""
+    import torch
+    from types import SimpleNamespace
+    from synth import config as get_config, make_matrix_np, make_matrix_torch, spectrum
+    cfg = get_config(C3_NAME)
+    m, n, k, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["q"]
+    seed = cfg["omega_seed"]
+    sig = spectrum(cfg["spectrum"], cfg["r"])
+    sub = SimpleNamespace(steps=min(args.steps, 2), warmup=max(args.warmup, 3))
+    out = {"workload": C3_NAME, "m": m, "n": n, "k": k, "p": p, "q": q,
+           "spectrum": "sigma_j = exp(-j/100) + 1e-3, r = %d, noise %g" % (cfg["r"], cfg["noise"]),
+           "steps": sub.steps, "warmup": sub.warmup,
+           "rel_err_definition": "||A - U S V^T||_F / ||A||_F against the FP32 A"}
+
+    # ---- error against the FP64 oracle at every rank (reduced matrix) ----
+    meta, gold = load_c3_golden()
+    mr, nr = int(meta["m"]), int(meta["n"])
+    A32r = torch.from_numpy(make_matrix_np(mr, nr, sig, noise=cfg["noise"], seed=cfg["a_seed"],
+                                           dtype="float32")).to(dev)
+    Abr = A32r.to(torch.bfloat16)          # round to nearest even, as the stored oracle input
+    vs_oracle = {"sizes": "m=%d n=%d k=%d p=%d q=%d, same spectrum, noise and seeds" % (mr, nr, k, p, q),
+                 "oracle_rel_err": {"f32": gold["rel_err_f32"], "bf16": gold["rel_err_bf16"]},
+                 "ranks_reported": list(C3_RANKS)}
+    for name, dt, opts, _ in c3_variants(rs):
+        Ar = Abr if dt == torch.bfloat16 else A32r
+        ref = gold["sigma_bf16" if dt == torch.bfloat16 else "sigma_f32"]
+        plan = rs.Plan(mr, nr, k, p, q, dt, dev, opts)
+        plan.run(Ar, seed)
+        torch.cuda.synchronize()
+        rs.check_info(plan.info, "c3 reduced " + name)
+        S = plan.S.double().cpu().numpy()
+        rel = np.abs(S - ref) / ref
+        e = rel_err_device(rs, A32r, plan.U, plan.S, plan.V)
+        oe = gold["rel_err_bf16" if dt == torch.bfloat16 else "rel_err_f32"]
+        vs_oracle[name] = {
+            "sigma_rel_err_max": float(rel.max()),
+            "sigma_rel_err_median": float(np.median(rel)),
+            "sigma_rel_err_at_rank": [float(rel[i - 1]) for i in C3_RANKS],
+            "rel_err": e, "rel_err_vs_oracle": e / oe}
+        del plan
+    del A32r, Abr
+    torch.cuda.empty_cache()
+    out["vs_fp64_oracle"] = vs_oracle
+
+    # ---- full size: timing and the equal-error comparison ----
+    A32 = make_matrix_torch(m, n, sig, noise=cfg["noise"], seed=cfg["a_seed"], dtype="float32",
+                            device=dev)
+    Ab = A32.to(torch.bfloat16)
+    torch.cuda.synchronize()
+    flops = step_flops(m, n, k, p, q)
+    ms32 = None
+    for name, dt, opts, what in c3_variants(rs):
+        Ad = Ab if dt == torch.bfloat16 else A32
+        ms, trace, plan = _time_variant(rs, Ad, opts, cfg, sub, seed, world, dev)
+        e = rel_err_device(rs, A32, plan.U, plan.S, plan.V)
+        del plan
+        ms, value = whole_job(flops, ms, world, dev)
+        if ms32 is None:
+            ms32 = ms
+        pass_ms = sum(v[0] for c, v in trace.items()
+                      if c in ("a_omega", "a_w", "at_w")) / sub.steps
+        elem = 2 if dt == torch.bfloat16 else 4
+        out[name] = {
+            "what": what, "value": value, "unit": UNIT, "ms_per_step": ms,
+            "speedup_vs_fp32": ms32 / ms, "rel_err": e,
+            "a_pass_ms_per_step": pass_ms,
+            "a_pass_gbs": ((2 * q + 2) * a_pass_bytes(m, n, elem) / (pass_ms * 1e-3) / 1e9
+                           if pass_ms else None),
+            "kernels": {c: round(v[0] / sub.steps, 3) for c, v in trace.items()}}
+    out["rel_err_fp32"] = out["f32"]["rel_err"]
+    del A32, Ab
+    torch.cuda.empty_cache()
+    return out
+
+
 def batched_line(rs, args, world, dev, peaks, peak_kind, name="c4_f32_batched512"):
     """The batched workload (512 FP32 problems of uneven sizes): the batched
     call timed like the main line, against the same problems run one by one
@@ -635,6 +763,8 @@ def main():
                     help="skip the BF16-storage (mixed precision) measurement")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-workload (512 small problems) measurement")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the mixed-precision workload (100000 x 50000, l = 550)")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the blocked adaptive QB (Alg. 7) measurement")
     args = ap.parse_args()
@@ -750,6 +880,14 @@ def main():
     if not args.no_adaptive and tdt == torch.float32:
         adaptive = adaptive_line(rs, A, cfg, args, world, dev, peaks, peak_kind)
 
+    c3 = None
+    if not args.no_c3 and cfg["name"] != C3_NAME:
+        # the main workload's buffers are released first (A32 + its bf16 copy
+        # of the mixed-precision workload hold 30 GB)
+        del plan
+        torch.cuda.empty_cache()
+        c3 = c3_line(rs, args, world, dev, peaks, peak_kind)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -785,6 +923,7 @@ def main():
             "mixed": mixed,
             "batched": batched,
             "adaptive_qb": adaptive,
+            "mixed_c3": c3,
         }
         print(json.dumps(line))
     if world > 1:
