@@ -16,8 +16,10 @@ rsvd     the algorithms of Voronin & Martinsson (RSVDPACK), step by step in
          adaptive QB to a tolerance of Algorithm 7, the parallel blocked QB of
          Algorithm 8, the randomized ID from the left sketch (Sec. 3.5) and
          the reverse-mode derivative of Algorithm 5 with Omega fixed.
+jacobi   the one-sided Jacobi SVD (Hestenes) of the l x l core of Alg. 5,
+         round-robin pair order, Demmel-Veselic stopping rule.
 quant    the E4M3 format, its round-to-nearest-even quantiser with block
          scales, and the FP8 sketch of the dequantised operands (the reading
          of the FP8 sketch; the paper fixes no reduced precision).
 """
-from . import philox, quant, rsvd  # noqa: F401
+from . import jacobi, philox, quant, rsvd  # noqa: F401

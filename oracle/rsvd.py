@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Every function takes the
 stored input promoted to float64 and follows the paper's steps in the paper's
-order; library primitives (matmul, LAPACK Householder QR, LAPACK SVD,
-triangular solve) serve as single steps.  Nothing here is blocked, fused or
+order; library primitives (matmul, LAPACK Householder QR, triangular solve)
+serve as single steps, and the SVD of the l x l core is the one-sided Jacobi
+method of ``oracle/jacobi.py``.  Nothing here is blocked, fused or
 reordered.
 
 Readings of points the paper leaves open (each is also taken by the CUDA side):
@@ -24,6 +25,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from . import philox
+from .jacobi import svd_jacobi
 
 
 # ---------------------------------------------------------------------------
@@ -87,8 +89,7 @@ def normalize_signs(U, V):
 def svd_from_qb(Q, Bt, k):
     """Steps after the QB step of Alg. 5: QR of Bt, SVD of the l x l R-hat, lift."""
     Qh, Rh = qr_pos(Bt)                             # [Q^, R^] = qr(Bt, 0)
-    Uh, S, VhT = np.linalg.svd(Rh)                  # R^ = U^ Sigma V^*
-    Vh = VhT.T
+    Uh, S, Vh = svd_jacobi(Rh)                      # R^ = U^ Sigma V^* (one-sided Jacobi)
     U = Q @ Vh[:, :k]                               # U_k = Q V^
     V = Qh @ Uh[:, :k]                              # V_k = Q^ U^
     U, V = normalize_signs(U, V)
@@ -241,8 +242,7 @@ def rsvd_vjp(A, k, p, q, seed, gU, gS, gV, rounding="f64", Omega=None):
     Q, Rq = qr_pos(Y)
     Bt = A.T @ Q
     Qh, Rh = qr_pos(Bt)
-    Uh, S, VhT = np.linalg.svd(Rh)
-    Vh = VhT.T
+    Uh, S, Vh = svd_jacobi(Rh)
     U = Q @ Vh[:, :k]
     V = Qh @ Uh[:, :k]
     signs = np.ones(k)
