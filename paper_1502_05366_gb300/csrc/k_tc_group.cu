@@ -13,10 +13,12 @@
 // arithmetic is that of k_tc.cu: a = a0 + a1 (bf16 hi, lo), products a0 w0 +
 // a1 w0 (+ a0 w1 for a stored W), fp32 accumulation in tensor memory.
 //
-// The CholeskyQR steps of the batch run here too: the Gram X^T X (form 1,
-// W = X) and the apply X R^-1 (form 0, W = R^-1 in three bf16 terms), and the
-// lifts U = Q Vh, V = Qh Uh (form 0): X has an l-float pitch, so these take
-// TMA maps of X itself when l is a multiple of 4.
+// The CholeskyQR steps of the power scheme run here too: the Gram X^T X
+// (form 1, W = X) and the apply X R^-1 (form 0, W = R^-1 in three bf16
+// terms); X has an l-float pitch, so these take TMA maps of X itself when
+// every l is a multiple of 4.  The final orthonormalisations and the lifts
+// U = Q Vh, V = Qh Uh stay on the fp32 SIMT GEMM (the split products hold Q
+// to 16 bits, short of the orthogonality the returned U and V need).
 //
 // Roles (256 threads): warp 0 TMA producer, warp 1 MMA issuer and TMEM owner,
 // warps 4-7 converters (fp32 A rows -> bf16 hi/lo in TMEM) and the epilogue of
