@@ -5,9 +5,12 @@
 // (CholeskyQR2/3).  A pass whose Gram has a pivot below tau * max(diag G),
 // tau = 4 l eps, is redone with a diagonal shift (shifted CholeskyQR, Fukaya et
 // al. 2020), the shift growing tenfold per retry; any shifted pass, or a second
-// pass whose Gram is far from I, requests the third pass.  One CTA holds the
-// matrix in shared memory: 384 threads on register tiles for fp32 up to
-// l = 224, else 256 threads (global memory beyond the shared-memory limit).
+// pass whose Gram is far from I, requests the third pass.  fp32 up to l = 224:
+// one CTA of 384 threads on register tiles with the matrix in shared memory;
+// fp32 beyond: a cooperative grid of 32 x 32 block tasks (chol_coop_kernel);
+// fp64: one CTA of 256 threads (global memory beyond the shared-memory limit).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -23,9 +26,13 @@ template <> __device__ __forceinline__ double eps_of<double>() { return 1.110223
 
 // Global fallback when l x l does not fit in shared memory: the matrix plus a
 // 32 x l block-row buffer for the blocked inverse.
+size_t chol_coop_scratch_bytes(int l);
 size_t chol_scratch_bytes(int l, int elem) {
   const size_t b = (size_t)l * l * elem;
-  return b <= SMEM_LIMIT ? 0 : b + (size_t)32 * l * elem;
+  const size_t g = b <= SMEM_LIMIT ? 0 : b + (size_t)32 * l * elem;
+  // fp32: the cooperative kernel's header, padded matrix and inverse
+  if (elem == 4) return std::max(g, chol_coop_scratch_bytes(l));
+  return g;
 }
 
 template <typename T>
@@ -1063,6 +1070,406 @@ cudaError_t launch_trmm_batched(const BTrmm* tasks, int batch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Cooperative blocked Cholesky and inverse of an fp32 Gram over many CTAs
+// (l beyond the one-CTA shared-memory kernel, up to 1024).  The padded matrix
+// lp x lp (lp = l rounded up to 32, identity on the padding) lives in the
+// global scratch with its inverse X beside it; every phase is a set of 32 x 32
+// block tasks spread over the grid, separated by bounded grid barriers:
+//   D(k)   the diagonal block: R_kk by warp 0 in registers (lane c holds
+//          column c; pivots not above thr stop the attempt), then
+//          X_kk = R_kk^-1 by back substitution (lane c: column c);
+//   P(k)   R_kj = X_kk^T A_kj for the blocks right of the diagonal;
+//   U(k)   A_ij -= R_ki^T R_kj for k < i <= j; CTA 0 first updates block
+//          (k+1, k+1) and factors it (D(k+1)), so one barrier per phase;
+//   inverse, by block diagonals d = 1, 2, ..:
+//          X_ij = -X_ii (sum over m = i+1..j of R_im X_mj), j = i + d.
+// The shifted retries, the flags of CholeskyQR2/3 and the outputs are those of
+// chol_body.  Every wait is bounded: on expiry RSVD_ERR_TIMEOUT is recorded and
+// each CTA leaves at its next barrier.
+// ---------------------------------------------------------------------------
+#ifndef CHOL_COOP_MIN_L
+#define CHOL_COOP_MIN_L 225               // below: the one-CTA shared-memory kernels
+#endif
+namespace {
+constexpr int CC_T = 256;                 // threads per CTA
+constexpr long long CC_SPIN = 4000000000LL;
+constexpr int CC_ATTEMPTS = 12;          // shifted retries, as chol_body
+struct CoopHdr {
+  unsigned bar;                  // grid barrier counter
+  unsigned md_bits;              // max diagonal of G (bits of a non-negative float)
+  unsigned dev_bits;             // max |G - I|
+  int bad;                       // a non-finite entry
+  int fail[CC_ATTEMPTS];         // a pivot of the attempt was not above thr (one slot per
+                                 // attempt: nothing is reset while another CTA may read it)
+};
+inline int coop_lp(int l) { return (l + 31) & ~31; }
+}  // namespace
+
+size_t chol_coop_scratch_bytes(int l) {
+  const size_t lp = (size_t)coop_lp(l);
+  return 256 + 2 * lp * lp * sizeof(float);
+}
+
+__device__ __forceinline__ unsigned cc_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// false when the wait ran out (the caller leaves)
+__device__ bool cc_barrier(CoopHdr* h, unsigned target, int* d_info) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&h->bar, 1u);
+    const long long t0 = clock64();
+    int ok = 1;
+    unsigned it = 0;
+    while (cc_ld_acquire(&h->bar) < target) {
+      __nanosleep(64);
+      if (((++it) & 255u) == 0 && clock64() - t0 > CC_SPIN) {
+        set_info(d_info, RSVD_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// A 32 x 32 block (row-major in the lp-wide matrix M at block (bi, bj)) into
+// shared memory, read through L2 (other CTAs wrote it before the barrier).
+__device__ __forceinline__ void cc_load(float (*T)[33], const float* M, int lp, int bi, int bj) {
+  for (int e = threadIdx.x; e < 1024; e += CC_T) {
+    const int r = e >> 5, c = e & 31;
+    T[r][c] = __ldcg(M + (size_t)(32 * bi + r) * lp + 32 * bj + c);
+  }
+}
+
+// acc[w] = sum_t A[t][r] B[t][c0 + w]  (A^T B), thread: r = tid / 8, c0 = 4 (tid % 8)
+__device__ __forceinline__ void cc_atb(const float (*A)[33], const float (*B)[33], float acc[4]) {
+  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+#pragma unroll 8
+  for (int t = 0; t < 32; ++t) {
+    const float a = A[t][r];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) acc[w] = fmaf(a, B[t][c0 + w], acc[w]);
+  }
+}
+// acc[w] += sum_t A[r][t] B[t][c0 + w]  (A B)
+__device__ __forceinline__ void cc_ab(const float (*A)[33], const float (*B)[33], float acc[4]) {
+  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+#pragma unroll 8
+  for (int t = 0; t < 32; ++t) {
+    const float a = A[r][t];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) acc[w] = fmaf(a, B[t][c0 + w], acc[w]);
+  }
+}
+__device__ __forceinline__ void cc_store(float* M, int lp, int bi, int bj, const float acc[4]) {
+  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+  float* d = M + (size_t)(32 * bi + r) * lp + 32 * bj + c0;
+  *reinterpret_cast<float4*>(d) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+
+// D(k): factor the (updated) diagonal block k, write R_kk into S and X_kk into
+// X; on a pivot not above thr set *fail.  The whole CTA enters.
+__device__ void cc_diag(float* S, float* X, int lp, int k, float thr, int* fail,
+                        float (*Rs)[33]) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  __syncthreads();
+  if (tid < 32) {
+    float d[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      d[i] = (i <= lane) ? __ldcg(S + (size_t)(32 * k + i) * lp + 32 * k + lane) : 0.f;
+    int failed = -1;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      if (failed < 0) {
+        const float piv = __shfl_sync(0xffffffffu, d[jj], jj);
+        if (!(piv > thr)) {
+          failed = jj;
+        } else {
+          const float r = sqrtf(piv);
+          float rj = d[jj];
+          if (lane == jj) rj = r;
+          else if (lane > jj) rj = rj / r;
+          d[jj] = rj;
+#pragma unroll
+          for (int i = jj + 1; i < 32; ++i) {
+            const float ri = __shfl_sync(0xffffffffu, rj, i);
+            if (lane >= i) d[i] -= ri * rj;
+          }
+        }
+      }
+    }
+    if (failed >= 0) {
+      if (lane == 0) atomicExch(fail, 1);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        Rs[i][lane] = (i <= lane) ? d[i] : 0.f;
+        if (i <= lane) S[(size_t)(32 * k + i) * lp + 32 * k + lane] = d[i];
+      }
+      __syncwarp();
+      // column c = lane of X_kk = R_kk^-1: x_c = 1 / r_cc, then upward
+      float x[32];
+#pragma unroll
+      for (int i = 31; i >= 0; --i) {
+        if (i > lane) {
+          x[i] = 0.f;
+        } else if (i == lane) {
+          x[i] = 1.f / Rs[i][i];
+        } else {
+          float acc = 0.f;
+#pragma unroll
+          for (int m = i + 1; m < 32; ++m)
+            if (m <= lane) acc = fmaf(Rs[i][m], x[m], acc);
+          x[i] = -acc / Rs[i][i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) X[(size_t)(32 * k + i) * lp + 32 * k + lane] = x[i];
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void cc_identity_rows(const CholArgs& a) {
+  const int L = a.L;
+  for (int i = blockIdx.x; i < L; i += gridDim.x)
+    for (int c = threadIdx.x; c < L; c += CC_T) {
+      const size_t t = (size_t)i * L + c;
+      const float v = (i == c) ? 1.f : 0.f;
+      if (a.R) ((float*)a.R)[t] = v;
+      if (a.Rinv) ((float*)a.Rinv)[t] = v;
+      if (a.Whi) {
+        ((__nv_bfloat16*)a.Whi)[t] = __float2bfloat16_rn(v);
+        ((__nv_bfloat16*)a.Wlo)[t] = __float2bfloat16_rn(0.f);
+        ((__nv_bfloat16*)a.Wlo2)[t] = __float2bfloat16_rn(0.f);
+      }
+    }
+}
+
+__global__ void __launch_bounds__(CC_T) chol_coop_kernel(CholArgs a, int lp) {
+  __shared__ float As[32][33], Bs[32][33];
+  __shared__ float s_red[2][CC_T / 32];
+  __shared__ int s_bad;
+  const int l = a.l, L = a.L, nb = lp / 32, G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  CoopHdr* h = reinterpret_cast<CoopHdr*>(a.scratch);
+  float* S = reinterpret_cast<float*>(reinterpret_cast<char*>(a.scratch) + 256);
+  float* X = S + (size_t)lp * lp;
+  const float* Gm = (const float*)a.G;
+  unsigned epoch = 0;
+  if (a.skip_idx >= 0 && a.flags && a.flags[a.skip_idx] == 1) {   // pass not needed: R = I
+    cc_identity_rows(a);
+    return;
+  }
+  // scale of G, its distance to I and non-finite entries (rows over the CTAs)
+  {
+    float md = 0.f, dev = 0.f;
+    int bad = 0;
+    for (int i = b; i < l; i += G)
+      for (int c = tid; c < l; c += CC_T) {
+        const float g = Gm[(size_t)i * a.ldg + c];
+        if (!isfinite(g)) bad = 1;
+        if (i == c) md = fmaxf(md, g);
+        dev = fmaxf(dev, fabsf(g - (i == c ? 1.f : 0.f)));
+      }
+    if (tid == 0) s_bad = 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+      dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    }
+    __syncthreads();
+    if (bad) s_bad = 1;
+    if ((tid & 31) == 0) {
+      s_red[0][tid >> 5] = md;
+      s_red[1][tid >> 5] = dev;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < CC_T / 32; ++w) {
+        md = fmaxf(md, s_red[0][w]);
+        dev = fmaxf(dev, s_red[1][w]);
+      }
+      atomicMax(&h->md_bits, __float_as_uint(md));
+      atomicMax(&h->dev_bits, __float_as_uint(dev));
+      if (s_bad) atomicOr(&h->bad, 1);
+    }
+  }
+  if (!cc_barrier(h, ++epoch * G, a.d_info)) return;
+  const float maxdiag = __uint_as_float(__ldcg(&h->md_bits));
+  const float gdev = __uint_as_float(__ldcg(&h->dev_bits));
+  if (b == 0 && tid == 0 && __ldcg(&h->bad)) set_info(a.d_info, RSVD_ERR_NUMERIC);
+  if (!(maxdiag > 0.f)) {                        // X = 0 or non-finite: no basis
+    if (b == 0 && tid == 0) set_info(a.d_info, RSVD_ERR_NOT_SPD);
+    cc_identity_rows(a);
+    return;
+  }
+  const float thr = 4.f * (float)l * 5.9604645e-8f * maxdiag;
+  float shift = 0.f;
+  int used_shift = 0;
+  bool ok = false;
+  for (int attempt = 0; attempt < CC_ATTEMPTS && !ok; ++attempt) {
+    int* fail = &h->fail[attempt];
+    // S = G + shift I, maxdiag on the padding's diagonal (above thr, decoupled
+    // from the rest; its factor never reaches the outputs); X = 0
+    for (int i = b; i < lp; i += G)
+      for (int c = tid; c < lp; c += CC_T) {
+        float v;
+        if (i < l && c < l) v = Gm[(size_t)i * a.ldg + c] + ((i == c) ? shift : 0.f);
+        else v = (i == c) ? maxdiag : 0.f;
+        S[(size_t)i * lp + c] = v;
+        X[(size_t)i * lp + c] = 0.f;
+      }
+    if (!cc_barrier(h, ++epoch * G, a.d_info)) return;
+    if (b == 0) cc_diag(S, X, lp, 0, thr, fail, As);
+    if (!cc_barrier(h, ++epoch * G, a.d_info)) return;
+    ok = __ldcg(fail) == 0;
+    for (int k = 0; ok && k + 1 < nb; ++k) {
+      // P(k): R_kj = X_kk^T A_kj
+      for (int j = k + 1 + b; j < nb; j += G) {
+        cc_load(As, X, lp, k, k);
+        cc_load(Bs, S, lp, k, j);
+        __syncthreads();
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        cc_atb(As, Bs, acc);
+        __syncthreads();
+        cc_store(S, lp, k, j, acc);
+      }
+      if (!cc_barrier(h, ++epoch * G, a.d_info)) return;
+      // U(k): A_ij -= R_ki^T R_kj, k < i <= j.  Task 0 is block (k+1, k+1):
+      // CTA 0 updates it and factors it (D(k+1)) and takes nothing else; the
+      // other tasks go to CTAs 1 .. G-1 (all to CTA 0 when G = 1)
+      const int m = nb - k - 1;                  // trailing block rows
+      const int ntask = m * (m + 1) / 2;
+      const int first = (G == 1 || b == 0) ? 0 : b;
+      const int stride = (G == 1) ? 1 : (b == 0 ? ntask : G - 1);
+      for (int t = first; t < ntask; t += stride) {
+        // task t -> (i, j): row-major over the upper triangle of the trailing blocks
+        int i = 0, rem = t;
+        while (rem >= m - i) {
+          rem -= m - i;
+          ++i;
+        }
+        const int bi = k + 1 + i, bj = bi + rem;
+        cc_load(As, S, lp, k, bi);
+        cc_load(Bs, S, lp, k, bj);
+        __syncthreads();
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        cc_atb(As, Bs, acc);
+        const int r = tid >> 3, c0 = (tid & 7) * 4;
+        float* d = S + (size_t)(32 * bi + r) * lp + 32 * bj + c0;
+        const float4 o = __ldcg(reinterpret_cast<const float4*>(d));
+        __syncthreads();
+        *reinterpret_cast<float4*>(d) =
+            make_float4(o.x - acc[0], o.y - acc[1], o.z - acc[2], o.w - acc[3]);
+        if (t == 0) cc_diag(S, X, lp, k + 1, thr, fail, As);
+      }
+      if (!cc_barrier(h, ++epoch * G, a.d_info)) return;
+      ok = __ldcg(fail) == 0;
+    }
+    if (!ok) {
+      shift = (shift == 0.f) ? thr : shift * 10.f;
+      used_shift = 1;
+    }
+  }
+  if (!ok) {
+    if (b == 0 && tid == 0) set_info(a.d_info, RSVD_ERR_NOT_SPD);
+    cc_identity_rows(a);
+    return;
+  }
+  if (b == 0 && tid == 0) chol_update_flags(a, used_shift, (double)l * (double)gdev);
+  // R out (identity on the padding)
+  if (a.R)
+    for (int i = b; i < L; i += G)
+      for (int c = tid; c < L; c += CC_T) {
+        float v;
+        if (i < l && c < l) v = (c >= i) ? __ldcg(S + (size_t)i * lp + c) : 0.f;
+        else v = (i == c) ? 1.f : 0.f;
+        ((float*)a.R)[(size_t)i * L + c] = v;
+      }
+  // inverse by block diagonals
+  for (int dg = 1; dg < nb; ++dg) {
+    for (int i = b; i + dg < nb; i += G) {
+      const int j = i + dg;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int mm = i + 1; mm <= j; ++mm) {
+        cc_load(As, S, lp, i, mm);
+        cc_load(Bs, X, lp, mm, j);
+        __syncthreads();
+        cc_ab(As, Bs, acc);
+        __syncthreads();
+      }
+      // X_ij = -X_ii T
+      {
+        const int r = tid >> 3, c0 = (tid & 7) * 4;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) Bs[r][c0 + w] = acc[w];
+      }
+      cc_load(As, X, lp, i, i);
+      __syncthreads();
+      float o[4] = {0.f, 0.f, 0.f, 0.f};
+      cc_ab(As, Bs, o);
+      __syncthreads();
+#pragma unroll
+      for (int w = 0; w < 4; ++w) o[w] = -o[w];
+      cc_store(X, lp, i, j, o);
+    }
+    if (!cc_barrier(h, ++epoch * G, a.d_info)) return;
+  }
+  if (a.Rinv)
+    for (int i = b; i < L; i += G)
+      for (int c = tid; c < L; c += CC_T) {
+        float v;
+        if (i < l && c < l) v = (c >= i) ? __ldcg(X + (size_t)i * lp + c) : 0.f;
+        else v = (i == c) ? 1.f : 0.f;
+        ((float*)a.Rinv)[(size_t)i * L + c] = v;
+      }
+  if (a.Whi)   // W^T with W = R^{-1}: Wt[j][kk] = X[kk][j], three bf16 terms
+    for (int j = b; j < L; j += G)
+      for (int kk = tid; kk < L; kk += CC_T) {
+        float v;
+        if (j < l && kk < l) v = (j >= kk) ? __ldcg(X + (size_t)kk * lp + j) : 0.f;
+        else v = (j == kk) ? 1.f : 0.f;
+        const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+        const float r1 = v - __bfloat162float(hb);
+        const __nv_bfloat16 mb = __float2bfloat16_rn(r1);
+        const size_t t = (size_t)j * L + kk;
+        ((__nv_bfloat16*)a.Whi)[t] = hb;
+        ((__nv_bfloat16*)a.Wlo)[t] = mb;
+        ((__nv_bfloat16*)a.Wlo2)[t] = __float2bfloat16_rn(r1 - __bfloat162float(mb));
+      }
+}
+
+static cudaError_t launch_chol_coop(const CholArgs& a, cudaStream_t s) {
+  const int lp = coop_lp(a.l), nb = lp / 32;
+  // one CTA per task of the widest phase, leaving room beside a running
+  // cluster kernel (the Jacobi of the combined call)
+  int G = nb * (nb - 1) / 2;
+  const int sms = device_sm_count();
+  if (G > sms - 16) G = sms - 16;
+  if (G < 1) G = 1;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_coop_kernel, CC_T, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  e = cudaMemsetAsync(a.scratch, 0, sizeof(CoopHdr), s);
+  if (e != cudaSuccess) return e;
+  CholArgs b = a;
+  int lpv = lp;
+  void* args[] = {(void*)&b, (void*)&lpv};
+  return cudaLaunchCooperativeKernel((const void*)chol_coop_kernel, dim3((unsigned)G), dim3(CC_T),
+                                     args, 0, s);
+}
+
 template <typename T>
 cudaError_t launch_chol(const CholArgs& a, cudaStream_t s) {
   const size_t bytes = (size_t)a.l * a.l * sizeof(T);
@@ -1070,8 +1477,15 @@ cudaError_t launch_chol(const CholArgs& a, cudaStream_t s) {
   // 16-byte R rows and W rows
   const bool f32 = sizeof(T) == 4 && a.l <= CHF_LMAX && chf_smem(a.l) + 2048 <= 232448 &&
                    a.L % 4 == 0 && (a.Whi == nullptr || a.L % 8 == 0);
+  // fp32 beyond the one-CTA kernel's range: the cooperative kernel (its
+  // scratch is part of every fp32 orth workspace)
+  const bool coop = sizeof(T) == 4 && a.scratch != nullptr && a.l >= CHOL_COOP_MIN_L &&
+                    a.l <= 1024;
   const int tr_ = trace_begin(RSVD_TRACE_CHOL, s);
-  if (f32) {
+  if (coop) {
+    cudaError_t e = launch_chol_coop(a, s);
+    if (e != cudaSuccess) return e;
+  } else if (f32) {
     const size_t dyn = chf_smem(a.l);
     cudaError_t e = cudaFuncSetAttribute(chol_f32_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
