@@ -322,9 +322,15 @@ struct Engine {
       st = gemm_n(rows, L, L, src, L, rows, L, false, 0, L, &w, ob.Rinv, L, dst, L, L, split,
                   part, skip);
       if (st != RSVD_OK) return st;
-      if (skip && tc) {  // pass skipped: the previous Q carried over unchanged
+      // pass skipped: the previous Q carried over unchanged.  Inside the power
+      // scheme a skipped second pass implies a skipped third one (only a
+      // second pass that runs can ask for the third), and the two carries
+      // Y -> X -> Y would cancel: the second pass copies nothing, and the third
+      // copies only when the second one ran (flags[3] != 1).
+      if (skip && tc && !(pass == 2 && !full)) {
         if (!c.dry) {
-          if (!c.run(launch_cond_copy<float>(skip, rows * (int64_t)L, (const float*)src,
+          const int* veto = (pass == 3 && !full) ? ob.flags + 3 : nullptr;
+          if (!c.run(launch_cond_copy<float>(skip, veto, rows * (int64_t)L, (const float*)src,
                                              (float*)dst, c.stream)))
             return RSVD_ERR_CUDA;
         }

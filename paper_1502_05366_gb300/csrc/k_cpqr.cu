@@ -445,18 +445,35 @@ struct CpqrDfCol {
 
   // Returns (on lane 0) the warp's best two residual norms after the step and
   // adds them all, as doubles, to `acc` (lane 0; read in tolerance mode only).
-  template <int S, int NWARP>
+  // VS: the Householder vector is read from shared memory at each use instead
+  // of being held in registers (the 32-slot form, whose registers would
+  // otherwise limit it to 8 warps per SM).
+  template <int S, int NWARP, bool VS>
   __device__ __forceinline__ Top2F run(double& acc) const {
     const DF none{-1.f, 0.f};
     Top2F best{none, 0x7fffffffffffffffLL, none};
     const float tol3z = 1.4901161193847656e-08f;   // sqrt(eps_fp64), as in the FP64 kernel
-    float vh[S], vl[S];
+    constexpr int SV = VS ? 1 : S;
+    float vh[SV], vl[SV];
+    if (!VS) {
 #pragma unroll
-    for (int t = 0; t < S; ++t) {
-      const int i = lane + 32 * t;
-      vh[t] = i < len ? svh[i] : 0.f;
-      vl[t] = i < len ? svl[i] : 0.f;
+      for (int t = 0; t < SV; ++t) {
+        const int i = lane + 32 * t;
+        vh[t] = i < len ? svh[i] : 0.f;
+        vl[t] = i < len ? svl[i] : 0.f;
+      }
     }
+    // slot t of v (zero beyond the active rows)
+    auto vslot = [&](int t, float& h, float& l) {
+      if (VS) {
+        const int i = lane + 32 * t;
+        h = i < len ? svh[i] : 0.f;
+        l = i < len ? svl[i] : 0.f;
+      } else {
+        h = vh[VS ? 0 : t];
+        l = vl[VS ? 0 : t];
+      }
+    };
     for (int64_t c = c0 + warp; c < c1; c += NWARP) {
       // the warp's next column into L1 while this one is processed (rows from
       // j + 1, as needed at the next step too)
@@ -487,10 +504,12 @@ struct CpqrDfCol {
         float sd = 0.f, ed = 0.f, sd2 = 0.f, ed2 = 0.f;
 #pragma unroll
         for (int t = 0; t < S; ++t) {
-          const float ph = __fmul_rn(vh[t], wh[t]);
-          float pe = __fmaf_rn(vh[t], wh[t], -ph);
-          pe = __fmaf_rn(vh[t], wl[t], pe);
-          pe = __fmaf_rn(vl[t], wh[t], pe);
+          float vht, vlt;
+          vslot(t, vht, vlt);
+          const float ph = __fmul_rn(vht, wh[t]);
+          float pe = __fmaf_rn(vht, wh[t], -ph);
+          pe = __fmaf_rn(vht, wl[t], pe);
+          pe = __fmaf_rn(vlt, wh[t], pe);
           float e;
           if (t & 1) {
             df_two_sum(sd2, ph, sd2, e);
@@ -517,10 +536,12 @@ struct CpqrDfCol {
         df_fast_two_sum(qh, qe, th, tl);
 #pragma unroll
         for (int t = 0; t < S; ++t) {
-          const float ph = __fmul_rn(th, vh[t]);
-          float pe = __fmaf_rn(th, vh[t], -ph);
-          pe = __fmaf_rn(th, vl[t], pe);
-          pe = __fmaf_rn(tl, vh[t], pe);
+          float vht, vlt;
+          vslot(t, vht, vlt);
+          const float ph = __fmul_rn(th, vht);
+          float pe = __fmaf_rn(th, vht, -ph);
+          pe = __fmaf_rn(th, vlt, pe);
+          pe = __fmaf_rn(tl, vht, pe);
           float sh, se;
           df_two_sum(wh[t], -ph, sh, se);
           se = __fadd_rn(se, __fsub_rn(wl[t], pe));
@@ -623,6 +644,12 @@ __device__ __forceinline__ bool grid_barrier_warp(unsigned* bar, unsigned target
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
+// Threads of the 32-slot form (256 < r <= 1024); above 256 the Householder
+// vector is read from shared memory (registers for 16 warps).
+#ifndef CPQR_DF_NT32
+#define CPQR_DF_NT32 512
+#endif
+
 // W is COLUMN-major here (element (i, c) in Wh[c*r + i], Wl[c*r + i]), so one
 // warp owns a column per iteration: lane l holds rows j + l + 32 t
 // (t < RPL) of it in registers from the load through the dot product, the
@@ -633,7 +660,7 @@ __device__ __forceinline__ bool grid_barrier_warp(unsigned* bar, unsigned target
 // The residual norms live in a.nrm as double-float pairs: float2 nrm2[c] =
 // (hi, lo) of nu_c^2 (hi = -1 once pivoted), float nref[c] (the value at the
 // last exact computation) at nrm2 + n.
-template <int RPL, int NT>
+template <int RPL, int NT, bool VS>
 __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   float* svh = (float*)dsm;        // Householder vector, hi parts (r entries)
@@ -859,14 +886,14 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
     Top2F best;
     double acc = 0.0;
     switch ((nt + SLOT_STEP<RPL>() - 1) / SLOT_STEP<RPL>()) {
-      case 1: best = cp.template run<1 * SLOT_STEP<RPL>(), NWARP>(acc); break;
-      case 2: best = cp.template run<2 * SLOT_STEP<RPL>(), NWARP>(acc); break;
-      case 3: best = cp.template run<3 * SLOT_STEP<RPL>(), NWARP>(acc); break;
-      case 4: best = cp.template run<4 * SLOT_STEP<RPL>(), NWARP>(acc); break;
-      case 5: best = cp.template run<5 * SLOT_STEP<RPL>(), NWARP>(acc); break;
-      case 6: best = cp.template run<6 * SLOT_STEP<RPL>(), NWARP>(acc); break;
-      case 7: best = cp.template run<7 * SLOT_STEP<RPL>(), NWARP>(acc); break;
-      default: best = cp.template run<8 * SLOT_STEP<RPL>(), NWARP>(acc); break;
+      case 1: best = cp.template run<1 * SLOT_STEP<RPL>(), NWARP, VS>(acc); break;
+      case 2: best = cp.template run<2 * SLOT_STEP<RPL>(), NWARP, VS>(acc); break;
+      case 3: best = cp.template run<3 * SLOT_STEP<RPL>(), NWARP, VS>(acc); break;
+      case 4: best = cp.template run<4 * SLOT_STEP<RPL>(), NWARP, VS>(acc); break;
+      case 5: best = cp.template run<5 * SLOT_STEP<RPL>(), NWARP, VS>(acc); break;
+      case 6: best = cp.template run<6 * SLOT_STEP<RPL>(), NWARP, VS>(acc); break;
+      case 7: best = cp.template run<7 * SLOT_STEP<RPL>(), NWARP, VS>(acc); break;
+      default: best = cp.template run<8 * SLOT_STEP<RPL>(), NWARP, VS>(acc); break;
     }
     if (lane == 0) {
       s_wsum[warp] = acc;
@@ -882,9 +909,9 @@ __global__ void __launch_bounds__(NT) cpqr_df_kernel(CpqrArgs a) {
   if (a.k_out && blockIdx.x == 0 && tid == 0) *a.k_out = steps;
 }
 
-template <int RPL, int NT>
+template <int RPL, int NT, bool VS>
 static cudaError_t launch_cpqr_df_t(const CpqrArgs& a, int sms, cudaStream_t s) {
-  auto kern = cpqr_df_kernel<RPL, NT>;
+  auto kern = cpqr_df_kernel<RPL, NT, VS>;
   // eight SMs are left to the Jacobi SVD (one 8-CTA cluster) that runs beside
   // the CPQR on another stream in the combined SVD + ID/CUR call
   int64_t G = sms > 16 ? sms - 8 : (sms > 1 ? sms - 1 : 1);
@@ -927,8 +954,8 @@ cudaError_t launch_cpqr_df(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   (void)grid_out;
   if (a.r > 1024) return cudaErrorInvalidValue;
   const int sms = device_sm_count();
-  if (a.r <= 256) return launch_cpqr_df_t<8, 768>(a, sms, s);
-  return launch_cpqr_df_t<32, 256>(a, sms, s);
+  if (a.r <= 256) return launch_cpqr_df_t<8, 768, false>(a, sms, s);
+  return launch_cpqr_df_t<32, CPQR_DF_NT32, (CPQR_DF_NT32 > 256)>(a, sms, s);
 }
 
 // S11 (k x k, column-major, upper triangular with beta on the diagonal), the

@@ -335,24 +335,24 @@ cudaError_t launch_add_inplace(int64_t rows, int64_t cols, const T* X, int64_t l
 
 // Copy used when the third CholeskyQR pass is skipped: runs only if *flag == 1.
 template <typename T>
-__global__ void cond_copy_kernel(const int* flag, int64_t count, const T* __restrict__ in,
-                                 T* __restrict__ out) {
-  if (*flag != 1) return;
+__global__ void cond_copy_kernel(const int* flag, const int* veto, int64_t count,
+                                 const T* __restrict__ in, T* __restrict__ out) {
+  if (*flag != 1 || (veto && *veto == 1)) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
        t += (int64_t)gridDim.x * blockDim.x)
     out[t] = in[t];
 }
 
 template <typename T>
-cudaError_t launch_cond_copy(const int* flag, int64_t count, const T* in, T* out,
-                             cudaStream_t s) {
+cudaError_t launch_cond_copy(const int* flag, const int* veto, int64_t count, const T* in,
+                             T* out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  cond_copy_kernel<T><<<grid1d(count), 256, 0, s>>>(flag, count, in, out);
+  cond_copy_kernel<T><<<grid1d(count), 256, 0, s>>>(flag, veto, count, in, out);
   count_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_cond_copy<float>(const int*, int64_t, const float*, float*,
-                                             cudaStream_t);
+template cudaError_t launch_cond_copy<float>(const int*, const int*, int64_t, const float*,
+                                             float*, cudaStream_t);
 
 // Columns j < k of X (rows x k) scaled by 1/S[j] (S double; 0 stays 0).
 template <typename T>

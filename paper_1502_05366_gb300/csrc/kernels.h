@@ -56,9 +56,10 @@ cudaError_t launch_fill(int64_t rows, int64_t cols, T* out, int64_t ldo, T value
 // columns >= cols): the stored-operand form of the tensor-core GEMMs.
 cudaError_t launch_split_transpose(int64_t rows, int cols, int L, const float* X, int64_t ldx,
                                    void* hi, void* lo, int64_t ldt, cudaStream_t s);
+// out = in when *flag == 1 and not (veto && *veto == 1), decided on the device.
 template <typename T>
-cudaError_t launch_cond_copy(const int* flag, int64_t count, const T* in, T* out,
-                             cudaStream_t s);
+cudaError_t launch_cond_copy(const int* flag, const int* veto, int64_t count, const T* in,
+                             T* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scale_cols(int64_t rows, int k, T* X, int64_t ldx, const double* S,
                               cudaStream_t s);

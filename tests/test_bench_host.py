@@ -25,7 +25,7 @@ def test_pass_roofline_is_bytes_of_a_over_the_average_launch():
     assert r["achieved"] == pytest.approx(50000 * 20000 * 4 / 0.6e-3 / 1e9, rel=1e-12)
     assert r["frac"] == pytest.approx(r["achieved"] / 6784.8, rel=1e-12)
     assert r["peak"] == 6784.8
-    assert r["traffic"] == 4106100000.0            # profiles/traffic.txt, per launch
+    assert r["traffic"] == bench.load_traffic()[("a_w", "c2_f32_50000x20000")]   # per launch
     # bf16 storage halves the algorithmic bytes of a pass
     r16 = bench.class_roofline("a_w", trace, dict(CFG, dtype="bfloat16"), PEAKS, "measured",
                                None)

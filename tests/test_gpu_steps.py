@@ -276,7 +276,8 @@ def test_cpqr_id(r, n, k):
 
 
 @pytest.mark.parametrize("r,n,k", [(20, 50, 10), (60, 1000, 50), (220, 5000, 200), (8, 9, 8),
-                                   (33, 4097, 1), (200, 20011, 200), (300, 1500, 280)])
+                                   (33, 4097, 1), (200, 20011, 200), (300, 1500, 280),
+                                   (600, 3001, 550)])
 def test_cpqr_id_f32_double_float(r, n, k):
     """The double-float CPQR of the FP32 path against the FP64 oracle on the same
     fp32 matrix: pivots identical, gaps to 1e-9, T to fp32 rounding."""
