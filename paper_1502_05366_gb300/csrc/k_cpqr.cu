@@ -474,10 +474,13 @@ struct CpqrDfCol {
         l = vl[VS ? 0 : t];
       }
     };
+    // The 32-slot form (VS) prefetches the warp's next column into L1 while
+    // this one is processed; the 8-slot form does not: its pass is
+    // issue-bound, and two prefetches per row slot cost more than the latency
+    // they hid (C2: 9.42 -> 8.77 ms per step without them; the 32-slot form at
+    // r = 550: 100 -> 106 ms without them).
     for (int64_t c = c0 + warp; c < c1; c += NWARP) {
-      // the warp's next column into L1 while this one is processed (rows from
-      // j + 1, as needed at the next step too)
-      if (c + NWARP < c1) {
+      if (VS && c + NWARP < c1) {
 #pragma unroll
         for (int t = 0; t < S; ++t) {
           const int i = lane + 32 * t;
@@ -584,8 +587,7 @@ struct CpqrDfCol {
         if (tol) acc += (double)nv.x + (double)nv.y;
       }
     }
-    // the warp's first column of the next step into L1 (stored rows j + 1 ..)
-    {
+    if (VS) {   // the warp's first column of the next step (stored rows j + 1 ..)
       const int64_t c = c0 + warp;
       if (c < c1) {
 #pragma unroll
