@@ -1042,8 +1042,14 @@ __device__ __forceinline__ float2 df_fms2(float2 s, float2 x, float2 u) {
 __device__ __forceinline__ float2 load_df(const float2* p) { return *p; }
 __device__ __forceinline__ float2 load_df(const float* p) { return make_float2(*p, 0.f); }
 
+#ifndef SOLVE_NC8
+#define SOLVE_NC8 2        // right-hand sides per warp of the 8-slot form
+#endif
+#ifndef SOLVE_MINB
+#define SOLVE_MINB 3       // resident blocks per SM the 8-slot form's registers are set for
+#endif
 template <typename TR, typename TO, int NC, int RPL>
-__global__ void __launch_bounds__(256) upper_solve_df_warp_kernel(
+__global__ void __launch_bounds__(256, RPL <= 8 ? SOLVE_MINB : 2) upper_solve_df_warp_kernel(
     int kk, int64_t ncols, const float2* __restrict__ U, const float2* __restrict__ dinv,
     const TR* __restrict__ rhs, int64_t rs_i, int64_t rs_c, TO* __restrict__ out,
     int64_t os_i, int64_t os_c, int* d_info) {
@@ -1064,45 +1070,53 @@ __global__ void __launch_bounds__(256) upper_solve_df_warp_kernel(
         sh[c][t] = v.x;
         sl[c][t] = v.y;
       }
-    for (int i = kk - 1; i >= 0; --i) {
-      const int owner = i & 31, ti = i >> 5;
-      const float2 di = __ldg(dinv + i);
-      if (di.x == 0.f && grp == 0 && lane == 0) set_info(d_info, RSVD_ERR_NUMERIC);
-      float xh[NC], xl[NC];
+    // steps i = kk - 1 .. 0 by row slot TI = i / 32, top slot first: inside a
+    // slot its index is a compile-time constant, so x_i is read straight from
+    // the owner's register and the slots below TI update without a test
+    // (their rows q < 32 TI <= i)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        float vh = 0.f, vl = 0.f;
+    for (int TI = RPL - 1; TI >= 0; --TI) {
+      if (TI >= nt) continue;                                  // uniform
+      const int itop = min(kk - 1, 32 * TI + 31);
+      for (int i = itop; i >= 32 * TI; --i) {
+        const int owner = i & 31;
+        const float2 di = __ldg(dinv + i);
+        if (di.x == 0.f && grp == 0 && lane == 0) set_info(d_info, RSVD_ERR_NUMERIC);
+        float xh[NC], xl[NC];
 #pragma unroll
-        for (int t = 0; t < RPL; ++t)
-          if (t == ti) {
-            vh = sh[c][t];
-            vl = sl[c][t];
-          }
-        const float2 x = df_mul2(make_float2(vh, vl), di);
-        xh[c] = __shfl_sync(0xffffffffu, x.x, owner);
-        xl[c] = __shfl_sync(0xffffffffu, x.y, owner);
-      }
-      const float2* ucol = U + (int64_t)i * kk;
-      // only the row slots t <= ti hold rows q <= i; ti is the same in every
-      // lane, so leaving the unrolled loop is a uniform branch and the empty
-      // slots cost no issue slots
+        for (int c = 0; c < NC; ++c) {
+          const float2 x = df_mul2(make_float2(sh[c][TI], sl[c][TI]), di);
+          xh[c] = __shfl_sync(0xffffffffu, x.x, owner);
+          xl[c] = __shfl_sync(0xffffffffu, x.y, owner);
+        }
+        const float2* ucol = U + (int64_t)i * kk;
 #pragma unroll
-      for (int t = 0; t < RPL; ++t) {
-        if (t > ti) break;
-        const int q = lane + 32 * t;
-        if (q < i) {
-          const float2 u = __ldg(ucol + q);
+        for (int t = 0; t < TI; ++t) {
+          const float2 u = __ldg(ucol + lane + 32 * t);
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const float2 r = df_fms2(make_float2(sh[c][t], sl[c][t]), make_float2(xh[c], xl[c]), u);
             sh[c][t] = r.x;
             sl[c][t] = r.y;
           }
-        } else if (q == i) {
+        }
+        {
+          const int q = lane + 32 * TI;
+          if (q < i) {
+            const float2 u = __ldg(ucol + q);
 #pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            sh[c][t] = xh[c];
-            sl[c][t] = xl[c];
+            for (int c = 0; c < NC; ++c) {
+              const float2 r =
+                  df_fms2(make_float2(sh[c][TI], sl[c][TI]), make_float2(xh[c], xl[c]), u);
+              sh[c][TI] = r.x;
+              sl[c][TI] = r.y;
+            }
+          } else if (q == i) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              sh[c][TI] = xh[c];
+              sl[c][TI] = xl[c];
+            }
           }
         }
       }
@@ -1147,7 +1161,7 @@ cudaError_t launch_upper_solve_df(int kk, int64_t ncols, const double* S11, cons
                                   int64_t os_c, int* d_info, cudaStream_t s) {
   if (kk <= 0 || ncols <= 0) return cudaSuccess;
   if (kk <= 256)
-    return launch_solve_warp<TR, TO, 4, 8>(kk, ncols, S11, rhs, rs_i, rs_c, out, os_i, os_c,
+    return launch_solve_warp<TR, TO, SOLVE_NC8, 8>(kk, ncols, S11, rhs, rs_i, rs_c, out, os_i, os_c,
                                            d_info, s);
   if (kk <= 1024)
     return launch_solve_warp<TR, TO, 1, 32>(kk, ncols, S11, rhs, rs_i, rs_c, out, os_i, os_c,
