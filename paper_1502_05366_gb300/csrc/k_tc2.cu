@@ -70,6 +70,11 @@ __global__ void __launch_bounds__(U_THREADS, 1)
                    const __grid_constant__ CUtensorMap mapW1, TcParams P) {
   // the second bf16 term of A exists for fp32 A when W has two terms
   constexpr bool ALO = !ABF && NW == 2;
+  // bf16 A in form 0: the TMA lands each stage as two 64-byte-swizzled K-major
+  // M-tiles, the layout the MMA reads, so the MMAs take A straight from the
+  // A ring (released by their commit) and the converter warps only run the
+  // epilogue
+  constexpr bool DA = ABF && FORM == 0;
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
   if (P.skip && *P.skip) return;
   unsigned char* dsm = (unsigned char*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
@@ -97,7 +102,7 @@ __global__ void __launch_bounds__(U_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < U_FST; ++s) {
       mbar_init(&ffull[s], 1);
-      mbar_init(&fempty[s], U_NCONV);
+      mbar_init(&fempty[s], DA ? 1 : U_NCONV);
     }
     for (int s = 0; s < U_BST; ++s) {
       mbar_init(&aready[s], U_NCONV);
@@ -204,8 +209,8 @@ __global__ void __launch_bounds__(U_THREADS, 1)
       int64_t run = -1;   // accumulation runs: one per segment, or `drain` K-chunks each
       int rc = 0;         // K-chunks in the current run
       int64_t kc = it0 % P.kiters;
-      int bs = 0;
-      uint32_t bph = 0;
+      int bs = 0, fs = 0;
+      uint32_t bph = 0, fph = 0;
       for (int64_t it = it0; it < it1; ++it) {
         if (it == it0 || kc == 0) rc = 0;
         if (rc == 0) {
@@ -213,11 +218,19 @@ __global__ void __launch_bounds__(U_THREADS, 1)
           if (run > 0 && !mbar_wait(acc_empty, (uint32_t)((run - 1) & 1), abort_flag, P.d_info))
             break;
         }
-        if (!mbar_wait(&aready[bs], bph, abort_flag, P.d_info)) break;
+        if (DA) {
+          if (!mbar_wait(&ffull[fs], fph, abort_flag, P.d_info)) break;
+        } else {
+          if (!mbar_wait(&aready[bs], bph, abort_flag, P.d_info)) break;
+        }
         if (!mbar_wait(&wfull[bs], bph, abort_flag, P.d_info)) break;
         tc_fence_after();
         const uint32_t base = smem_u32(bring + bs * BSB);
         const uint32_t wbase = base + 4u * U_AT;
+        // M-tile t of A: tiles 2t (hi), 2t + 1 (lo) of the operand stage, or
+        // rows 128 t .. of the landed bf16 stage
+        const uint32_t abase = DA ? smem_u32(fring + fs * U_FBYTES) : base;
+        const uint32_t astride = DA ? (uint32_t)U_AT : 2u * U_AT;
 #pragma unroll
         for (int kk = 0; kk < U_BK / 16; ++kk) {
           const uint64_t bw0 = sw64_desc(wbase + 32u * kk);
@@ -226,7 +239,7 @@ __global__ void __launch_bounds__(U_THREADS, 1)
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
             const uint32_t d = tmem + U_ACC2 * (uint32_t)t;
-            const uint64_t ahi = sw64_desc(base + (uint32_t)(2 * t) * U_AT + 32u * kk);
+            const uint64_t ahi = sw64_desc(abase + (uint32_t)t * astride + 32u * kk);
             mma_ss(d, ahi, bw0, idesc, acc0);
             if (ALO) mma_ss(d, sw64_desc(base + (uint32_t)(2 * t + 1) * U_AT + 32u * kk), bw0,
                             idesc, 1u);
@@ -234,6 +247,7 @@ __global__ void __launch_bounds__(U_THREADS, 1)
           }
         }
         mma_commit(&bdone[bs]);
+        if (DA) mma_commit(&fempty[fs]);
         ++rc;
         const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
         if (seg_end || (P.drain > 0 && rc == P.drain)) {
@@ -244,6 +258,10 @@ __global__ void __launch_bounds__(U_THREADS, 1)
         if (++bs == U_BST) {
           bs = 0;
           bph ^= 1u;
+        }
+        if (DA && ++fs == U_FST) {
+          fs = 0;
+          fph ^= 1u;
         }
       }
     }
@@ -269,6 +287,7 @@ __global__ void __launch_bounds__(U_THREADS, 1)
         rin = 0;
       }
       if (rc == 0) ++run;
+      if (!DA) {
       if (!mbar_wait(&ffull[fs], fph, abort_flag, P.d_info)) break;
       const unsigned char* st = fring + fs * U_FBYTES;
       uint32_t hi[16], lo[16];
@@ -323,6 +342,7 @@ __global__ void __launch_bounds__(U_THREADS, 1)
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&aready[bs]);
+      }
       ++rc;
       const bool seg_end = (it + 1 == it1) || (kc + 1 == P.kiters);
       if (seg_end || (P.drain > 0 && rc == P.drain)) {
