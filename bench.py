@@ -137,8 +137,36 @@ def class_roofline(cls, trace, cfg, peaks, peak_kind, sm_mhz):
     return base
 
 
+# bf16 tensor-core products issued per K-step and output tile by each pass
+# over A on the default path (RSVD_PREC_TC): fp32 A is split a = a0 + a1;
+# Omega is one bf16 term, a stored operand two (w0, w1).
+#   A Omega:      a0 w0 + a1 w0            (bf16 A: a0 w0)
+#   A W, A^T W:   a0 w0 + a1 w0 + a0 w1    (bf16 A: a0 w0 + a0 w1)
+PASS_PRODUCTS = {("a_omega", 4): 2, ("a_w", 4): 3, ("at_w", 4): 3,
+                 ("a_omega", 2): 1, ("a_w", 2): 2, ("at_w", 2): 2}
+
+
+def pass_bounds(cfg, peaks):
+    """Per pass class: the time of its bytes at the measured HBM bandwidth and
+    of its issued bf16 products at the measured sustained bf16 rate (the
+    passes run inside a long step), MMA width N = l rounded up to 16."""
+    m, n, l = cfg["m"], cfg["n"], cfg["k"] + cfg["p"]
+    elem = ELEM[cfg["dtype"]]
+    lpad = (l + 15) // 16 * 16
+    out = {}
+    for c in ("a_omega", "a_w", "at_w"):
+        hbm_ms = a_pass_bytes(m, n, elem) / (peaks["hbm_gbs"] * 1e9) * 1e3
+        tflops = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        tensor_ms = PASS_PRODUCTS[(c, elem)] * 2.0 * m * n * lpad / (tflops * 1e12) * 1e3
+        out[c] = {"hbm_ms": hbm_ms, "tensor_ms": tensor_ms,
+                  "bound": "hbm" if hbm_ms >= tensor_ms else "tensor",
+                  "bound_ms": max(hbm_ms, tensor_ms)}
+    return out
+
+
 def sketch_roofline(trace, cfg, peaks, peak_kind):
-    """The 2q+2 passes over A (a1-a7) against HBM: one read of A per pass."""
+    """The 2q+2 passes over A (a1-a7) against HBM: one read of A per pass;
+    beside it each class against the slower of its two bounds (pass_bounds)."""
     m, n, q = cfg["m"], cfg["n"], cfg["q"]
     cls = [c for c in ("a_omega", "a_w", "at_w") if c in trace]
     ms = sum(trace[c][0] for c in cls)
@@ -147,12 +175,24 @@ def sketch_roofline(trace, cfg, peaks, peak_kind):
         return None
     achieved = nl * a_pass_bytes(m, n, ELEM[cfg["dtype"]]) / (ms * 1e-3) / 1e9
     t = load_traffic()
+    pb = pass_bounds(cfg, peaks)
+    per = {}
+    for c in cls:
+        avg = trace[c][0] / trace[c][1]
+        per[c] = dict(pb[c], measured_ms=avg, frac=pb[c]["bound_ms"] / avg)
+    bound_total = sum(pb[c]["bound_ms"] * trace[c][1] for c in cls)
     return {"kernels": "tc_omega2_kernel (A Omega), tc_unit_kernel (A W, A^T W)",
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "passes_timed": nl,
             "per_class_ms": {c: trace[c][0] / trace[c][1] for c in cls},
             "traffic": {c: t.get((c, cfg["name"])) for c in cls},
-            "peak_source": peak_kind + " STREAM-style copy"}
+            "peak_source": peak_kind + " STREAM-style copy",
+            "slower_bound": {
+                "what": "each class against the slower of its bytes at the measured HBM "
+                        "bandwidth and its issued bf16 products (split arithmetic, "
+                        "PASS_PRODUCTS) at the measured sustained bf16 rate",
+                "per_class": per, "frac": bound_total / ms,
+                "tensor_peak_tflops": peaks.get("bf16_tflops_sustained")}}
 
 
 def qb_sketch_unit(rs, A, cfg, args, seed, world, dev, peaks, peak_kind):

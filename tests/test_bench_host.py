@@ -99,3 +99,28 @@ def test_reference_arm_json_line_single_rank():
     assert d["warmup"] == 1 and d["higher_is_better"] is True and d["data"] == "synthetic"
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["cpu_baseline"]["cores"] >= 1 and "sample" in d["cpu_baseline"]
+
+
+def test_pass_bounds_slower_of_hbm_and_issued_products():
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1500.0}
+    pb = bench.pass_bounds(CFG, peaks)
+    m, n, lpad = 50000, 20000, 224                    # l = 220 rounded up to 16
+    assert pb["a_w"]["hbm_ms"] == pytest.approx(m * n * 4 / 6000e9 * 1e3, rel=1e-12)
+    # fp32 A, stored operand: a0 w0 + a1 w0 + a0 w1 at the sustained rate
+    assert pb["a_w"]["tensor_ms"] == pytest.approx(3 * 2.0 * m * n * lpad / 1500e12 * 1e3,
+                                                   rel=1e-12)
+    assert pb["a_omega"]["tensor_ms"] == pytest.approx(pb["a_w"]["tensor_ms"] * 2 / 3, rel=1e-12)
+    for c in ("a_omega", "a_w", "at_w"):
+        b = pb[c]
+        assert b["bound_ms"] == max(b["hbm_ms"], b["tensor_ms"])
+        assert b["bound"] == ("hbm" if b["hbm_ms"] >= b["tensor_ms"] else "tensor")
+    # bf16 storage halves the bytes and drops the a1 products
+    pb16 = bench.pass_bounds(dict(CFG, dtype="bfloat16"), peaks)
+    assert pb16["a_w"]["hbm_ms"] == pytest.approx(pb["a_w"]["hbm_ms"] / 2, rel=1e-12)
+    assert pb16["a_w"]["tensor_ms"] == pytest.approx(pb["a_w"]["tensor_ms"] * 2 / 3, rel=1e-12)
+    r = bench.sketch_roofline({"a_omega": (1.6, 1), "a_w": (1.7, 2), "at_w": (2.8, 3)}, CFG,
+                              peaks, "measured")
+    sb = r["slower_bound"]
+    assert sb["frac"] == pytest.approx(
+        (pb["a_omega"]["bound_ms"] + 2 * pb["a_w"]["bound_ms"] + 3 * pb["at_w"]["bound_ms"]) / 6.1,
+        rel=1e-12)
