@@ -156,7 +156,8 @@ def pass_bounds(cfg, peaks):
     out = {}
     for c in ("a_omega", "a_w", "at_w"):
         hbm_ms = a_pass_bytes(m, n, elem) / (peaks["hbm_gbs"] * 1e9) * 1e3
-        tflops = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        # the recipe's sustained fallback when the file gives no tensor rate
+        tflops = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0
         tensor_ms = PASS_PRODUCTS[(c, elem)] * 2.0 * m * n * lpad / (tflops * 1e12) * 1e3
         out[c] = {"hbm_ms": hbm_ms, "tensor_ms": tensor_ms,
                   "bound": "hbm" if hbm_ms >= tensor_ms else "tensor",
