@@ -401,7 +401,56 @@ def cpu_oracle_full(A_host, cfg):
     return {"value": fl / dt / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "the full workload (m=%d n=%d k=%d p=%d q=%d, the GPU step's own A in "
                       "FP64): one step of oracle.rsvd + oracle.rcur, %.1f s"
-                      % (m, n, cfg["k"], cfg["p"], cfg["q"], dt)}
+                      % (m, n, cfg["k"], cfg["p"], cfg["q"], dt),
+            "one_thread": cpu_oracle_one_thread()}
+
+
+def oracle_one_thread_child():
+    """--oracle-one-thread: read (config name, A as .npy) from stdin, time the
+    oracle's QB (a1-a7) and one step of oracle.rsvd + oracle.rcur on it, print
+    one JSON line.  The parent starts this process with one BLAS thread."""
+    import io
+    name = sys.stdin.buffer.readline().decode().strip()
+    A = np.load(io.BytesIO(sys.stdin.buffer.read()))
+    from synth import config as get_config
+    from oracle import rsvd as orc
+    cfg = get_config(name)
+    k, p, q, seed = cfg["k"], cfg["p"], cfg["q"], cfg["omega_seed"]
+    rounding = "f64" if cfg["dtype"] == "float64" else "bf16"
+    t0 = time.perf_counter()
+    orc.qb(A, k, p, q, seed, rounding=rounding)
+    t_qb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.rsvd(A, k, p, q, seed, rounding=rounding)
+    orc.rcur(A, k, p, q, seed, rounding=rounding)
+    t_step = time.perf_counter() - t0
+    m, n = A.shape
+    print(json.dumps({"workload": name, "qb_s": t_qb, "step_s": t_step,
+                      "step_tflops": step_flops(m, n, k, p, q) / t_step / 1e12}))
+    return 0
+
+
+def cpu_oracle_one_thread(names=("c1_f64_2000x1000", "c5_f32_8192x4096")):
+    """The oracle with one BLAS thread on the small workloads (their matrices
+    built here with every core and handed over through a pipe)."""
+    import io
+    import subprocess
+    from synth import config as get_config, make_matrix_np, spectrum
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = {}
+    for name in names:
+        c = get_config(name)
+        A = make_matrix_np(c["m"], c["n"], spectrum(c["spectrum"], c["r"]), noise=c["noise"],
+                           seed=c["a_seed"], dtype=c["dtype"]).astype(np.float64)
+        buf = io.BytesIO()
+        np.save(buf, A)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-one-thread"],
+                           input=name.encode() + b"\n" + buf.getvalue(), env=env,
+                           capture_output=True, timeout=600)
+        lines = [ln for ln in r.stdout.decode().splitlines() if ln.startswith("{")]
+        out[name] = json.loads(lines[0]) if r.returncode == 0 and lines else \
+            {"error": r.stderr.decode()[-300:]}
+    return out
 
 
 def run_reference(args, cfg, rank):
@@ -808,7 +857,10 @@ def main():
                     help="skip the mixed-precision workload (100000 x 50000, l = 550)")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the blocked adaptive QB (Alg. 7) measurement")
+    ap.add_argument("--oracle-one-thread", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_one_thread:
+        return oracle_one_thread_child()
 
     from synth import config as get_config
     cfg = get_config(args.config)

@@ -124,3 +124,10 @@ def test_pass_bounds_slower_of_hbm_and_issued_products():
     assert sb["frac"] == pytest.approx(
         (pb["a_omega"]["bound_ms"] + 2 * pb["a_w"]["bound_ms"] + 3 * pb["at_w"]["bound_ms"]) / 6.1,
         rel=1e-12)
+
+
+def test_one_thread_oracle_timing_of_a_small_workload():
+    r = bench.cpu_oracle_one_thread(("c1_f64_2000x1000",))["c1_f64_2000x1000"]
+    assert "error" not in r, r
+    assert r["workload"] == "c1_f64_2000x1000"
+    assert 0 < r["qb_s"] < r["step_s"] and r["step_tflops"] > 0
