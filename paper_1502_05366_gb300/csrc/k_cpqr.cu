@@ -428,6 +428,21 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// Warp-wide best two of (value, index) proposals; every lane ends with it.
+__device__ __forceinline__ Top2F warp_top2f(Top2F v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Top2F w;
+    w.b1.h = __shfl_xor_sync(0xffffffffu, v.b1.h, o);
+    w.b1.l = __shfl_xor_sync(0xffffffffu, v.b1.l, o);
+    w.i1 = __shfl_xor_sync(0xffffffffu, v.i1, o);
+    w.b2.h = __shfl_xor_sync(0xffffffffu, v.b2.h, o);
+    w.b2.l = __shfl_xor_sync(0xffffffffu, v.b2.l, o);
+    v = merge_top2f(v, w);
+  }
+  return v;
+}
+
 struct CpqrDfCol {
   float* Wh;
   float* Wl;
@@ -473,6 +488,68 @@ struct CpqrDfCol {
         h = vh[VS ? 0 : t];
         l = vl[VS ? 0 : t];
       }
+    };
+    // Norm bookkeeping of the pass, batched over up to 32 columns (lane q
+    // holds the q-th column of the batch) instead of run by lane 0 column by
+    // column: the downdate nu^2 - W(j, c)^2 in double-float, the exact
+    // recompute on cancellation (LAPACK safeguard; from the stored column,
+    // the values the lane itself wrote), the new norms and the warp's best
+    // two.  Every column's arithmetic is the one lane 0 ran, the best two do
+    // not depend on the order of merging, and the tolerance sum is taken in
+    // column order, so the results are those of the column-by-column form.
+    float st_nx = 0.f, st_ny = 0.f, st_wh = 0.f, st_wl = 0.f;
+    int64_t st_c = 0;
+    int nst = 0;
+    auto flush = [&]() {
+      if (nst == 0) return;
+      float nh = 0.f, nl = 0.f;
+      int rec = 0;
+      if (lane < nst) {
+        float ph, pe, sh, se;
+        df_sqr(st_wh, st_wl, ph, pe);
+        df_two_sum(st_nx, -ph, sh, se);
+        se = __fadd_rn(se, __fsub_rn(st_ny, pe));
+        df_fast_two_sum(sh, se, nh, nl);
+        rec = (!(nh > tol3z * nref[st_c - cbase]) && j + 1 < r) ? 1 : 0;
+      }
+      unsigned rm = __ballot_sync(0xffffffffu, rec);
+      while (rm) {
+        const int q = __ffs(rm) - 1;
+        rm &= rm - 1;
+        const int64_t cq = __shfl_sync(0xffffffffu, st_c, q);
+        const float* ch = Wh + cq * r + j;
+        const float* cl = Wl + cq * r + j;
+        float qs = 0.f, qe = 0.f;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const int i = lane + 32 * t;
+          if (i >= 1 && i < len) df_acc_sqr(ch[i], cl[i], qs, qe);
+        }
+        df_warp_sum(qs, qe);
+        float h, l;
+        df_fast_two_sum(qs, qe, h, l);
+        if (lane == q) {
+          nh = h;
+          nl = l;
+          nref[st_c - cbase] = h;
+        }
+      }
+      float2 nv = make_float2(0.f, 0.f);
+      Top2F cand{none, 0x7fffffffffffffffLL, none};
+      if (lane < nst) {
+        nv = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
+        nrm2[st_c - cbase] = nv;
+        cand = Top2F{DF{nv.x, nv.y}, st_c, none};
+      }
+      best = merge_top2f(best, warp_top2f(cand));
+      if (tol) {
+        for (int q = 0; q < nst; ++q) {
+          const float a = __shfl_sync(0xffffffffu, nv.x, q);
+          const float b = __shfl_sync(0xffffffffu, nv.y, q);
+          if (lane == 0) acc += (double)a + (double)b;
+        }
+      }
+      nst = 0;
     };
     // The 32-slot form (VS) prefetches the warp's next column into L1 while
     // this one is processed; the 8-slot form does not: its pass is
@@ -556,37 +633,20 @@ struct CpqrDfCol {
           }
         }
       }
-      // residual norm downdate nu^2 - W(j, c)^2 (lane 0 holds row j), in
-      // double-float; exact recompute on cancellation (LAPACK safeguard)
-      float nh = 0.f, nl = 0.f;
-      int recompute = 0;
-      if (lane == 0) {
-        float ph, pe, sh, se;
-        df_sqr(wh[0], wl[0], ph, pe);
-        df_two_sum(nc.x, -ph, sh, se);
-        se = __fadd_rn(se, __fsub_rn(nc.y, pe));
-        df_fast_two_sum(sh, se, nh, nl);
-        recompute = (!(nh > tol3z * nref[c - cbase]) && j + 1 < r) ? 1 : 0;
+      // the column's norm bookkeeping goes to lane nst of the batch: its old
+      // residual norm and the updated W(j, c) (held by lane 0)
+      const float w0h = __shfl_sync(0xffffffffu, wh[0], 0);
+      const float w0l = __shfl_sync(0xffffffffu, wl[0], 0);
+      if (lane == nst) {
+        st_nx = nc.x;
+        st_ny = nc.y;
+        st_wh = w0h;
+        st_wl = w0l;
+        st_c = c;
       }
-      recompute = __shfl_sync(0xffffffffu, recompute, 0);
-      if (recompute) {
-        float qs = 0.f, qe = 0.f;
-#pragma unroll
-        for (int t = 0; t < S; ++t) {
-          const int i = lane + 32 * t;
-          if (i >= 1 && i < len) df_acc_sqr(wh[t], wl[t], qs, qe);
-        }
-        df_warp_sum(qs, qe);
-        df_fast_two_sum(qs, qe, nh, nl);
-        if (lane == 0) nref[c - cbase] = nh;
-      }
-      if (lane == 0) {
-        const float2 nv = nh > 0.f ? make_float2(nh, nl) : make_float2(0.f, 0.f);
-        nrm2[c - cbase] = nv;
-        best = merge_top2f(best, Top2F{DF{nv.x, nv.y}, c, none});
-        if (tol) acc += (double)nv.x + (double)nv.y;
-      }
+      if (++nst == 32) flush();
     }
+    flush();
     if (VS) {   // the warp's first column of the next step (stored rows j + 1 ..)
       const int64_t c = c0 + warp;
       if (c < c1) {
@@ -603,21 +663,6 @@ struct CpqrDfCol {
     return best;
   }
 };
-
-// Warp-wide best two of (value, index) proposals; every lane ends with it.
-__device__ __forceinline__ Top2F warp_top2f(Top2F v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    Top2F w;
-    w.b1.h = __shfl_xor_sync(0xffffffffu, v.b1.h, o);
-    w.b1.l = __shfl_xor_sync(0xffffffffu, v.b1.l, o);
-    w.i1 = __shfl_xor_sync(0xffffffffu, v.i1, o);
-    w.b2.h = __shfl_xor_sync(0xffffffffu, v.b2.h, o);
-    w.b2.l = __shfl_xor_sync(0xffffffffu, v.b2.l, o);
-    v = merge_top2f(v, w);
-  }
-  return v;
-}
 
 // Grid barrier entered by one warp of each CTA (lane 0 arrives and polls);
 // false on every lane when the wait ran out.
