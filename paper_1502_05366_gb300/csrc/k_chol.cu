@@ -291,9 +291,9 @@ __device__ __forceinline__ void tri_tile(int u, int nT, int* ti, int* tc) {
 //       (both in registers, one column per lane; the rows of R_pp and of D_p
 //       are broadcast through shared memory);
 //   (b) the panel row block becomes D_p^T S_panel (4 x 4 register tiles);
-//   (c) the trailing upper triangle is updated with 8 x 8 register tiles,
-//       except the next diagonal block, which warp 0 updates and factors
-//       meanwhile (lookahead).
+//   (c) the next diagonal block is updated by the worker warps and handed to
+//       warp 0, which factors it while the workers update the rest of the
+//       trailing upper triangle with 8 x 8 register tiles (lookahead).
 // Inverse X = R^{-1}, block rows from the bottom:
 //   T = -R(I, I+1:) X(I+1:, :)
 //   X(I, I+1:) = D_I T,  X(I, I) = D_I   (4 x 4 register tiles).
@@ -329,6 +329,40 @@ __device__ void chf_load(const CholArgs& a, float* S, int ld, float shift, float
   const bool vec = (ldg % 4 == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0) &&
                    ldg >= ((l + 3) & ~3);
   const int ne = l * nq;
+  if (vec) {
+    // every 16-byte piece of G in flight at once (cp.async, zero-filled past
+    // column l), then the scan and the shift in shared memory
+    for (int e = tid; e < ne; e += nthr) {
+      const int i = e / nq, c = 4 * (e - (e / nq) * nq);
+      const int nbytes = c < l ? min(16, 4 * (l - c)) : 0;
+      const float* g = G + (int64_t)i * ldg + (c < l ? c : 0);
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(S + i * ld + c);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g), "r"(nbytes)
+                   : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    if (md) {
+      for (int e = tid; e < ne; e += nthr) {
+        const int i = e / nq, c = 4 * (e - (e / nq) * nq);
+        if (c >= l) continue;
+        const float4 v = lds4(S + i * ld + c);
+        const float w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int cc = c + w;
+          if (cc < l) {
+            if (!isfinite(w4[w])) *bad = true;
+            if (cc == i) *md = fmaxf(*md, w4[w]);
+            *dev = fmaxf(*dev, fabsf(w4[w] - (cc == i ? 1.f : 0.f)));
+          }
+        }
+      }
+    }
+    if (shift != 0.f)
+      for (int i = tid; i < l; i += nthr) S[i * ld + i] += shift;
+    return;
+  }
   for (int e0 = tid; e0 < ne; e0 += 8 * nthr) {
     float4 v[8];
 #pragma unroll
@@ -486,32 +520,6 @@ __device__ int chf_diag(float* S, int ld, int p0, int pb, float thr, float* Dc, 
   return -1;
 }
 
-// By warp 0: the update of the diagonal block at (c0, c0), nb1 columns, by the
-// panel rows p0 .. p0 + pb - 1 (lane c owns column c0 + c).
-__device__ void chf_block_update(float* S, int ld, int p0, int pb, int c0, int nb1) {
-  const int lane = threadIdx.x & 31;
-  float acc[NB];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) acc[i] = 0.f;
-  for (int t = 0; t < pb; ++t) {
-    const float* row = S + (p0 + t) * ld + c0;
-    const float xc = lane < nb1 ? row[lane] : 0.f;
-#pragma unroll
-    for (int i4 = 0; i4 < NB / 4; ++i4) {
-      if (4 * i4 < nb1) {
-        const float4 r4 = lds4(row + 4 * i4);
-        acc[4 * i4] = fmaf(r4.x, xc, acc[4 * i4]);
-        acc[4 * i4 + 1] = fmaf(r4.y, xc, acc[4 * i4 + 1]);
-        acc[4 * i4 + 2] = fmaf(r4.z, xc, acc[4 * i4 + 2]);
-        acc[4 * i4 + 3] = fmaf(r4.w, xc, acc[4 * i4 + 3]);
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < NB; ++i)
-    if (i <= lane && lane < nb1) S[(c0 + i) * ld + c0 + lane] -= acc[i];
-}
-
 // Full factorization; returns the failing column or -1 (uniform over the CTA).
 // Lookahead: while other warps apply panel p's update to the trailing matrix,
 // warp 0 applies it to the next diagonal block and factors that block.
@@ -566,9 +574,27 @@ __device__ int chf_factor(float* S, int l, int ld, float thr, float* Dc, float* 
       __syncthreads();
     }
     const int nb1 = min(NB, nt);   // width of the next panel
+    // the next diagonal block's update, spread over the worker warps (one
+    // entry per thread and pass, the products added in the panel's row
+    // order), handed to warp 0 through named barrier 1
+    if ((warp & 3) != 0) {
+      const int nwk = (nthr >> 5) - (nthr >> 7);
+      const int wt = (warp - 1 - (warp >> 2)) * 32 + (tid & 31);
+      for (int o = wt; o < nb1 * nb1; o += nwk * 32) {
+        const int i = o / nb1, c = o - (o / nb1) * nb1;
+        if (c < i) continue;
+        float acc = 0.f;
+        for (int t = 0; t < pb; ++t) {
+          const float* row = S + (p0 + t) * ld + c0;
+          acc = fmaf(row[i], row[c], acc);
+        }
+        S[(c0 + i) * ld + c0 + c] -= acc;
+      }
+      __threadfence_block();
+      asm volatile("bar.arrive 1, %0;" ::"r"(nwk * 32 + 32) : "memory");
+    }
     if (warp == 0) {
-      chf_block_update(S, ld, p0, pb, c0, nb1);
-      __syncwarp();
+      asm volatile("bar.sync 1, %0;" ::"r"((nthr >> 5) * 32 - (nthr >> 7) * 32 + 32) : "memory");
       const int f = chf_diag(S, ld, c0, nb1, thr, Dc, s_dinv, rowbuf);
       if (tid == 0) *s_fail = f < 0 ? -1 : c0 + f;
     } else if ((warp & 3) != 0) {
