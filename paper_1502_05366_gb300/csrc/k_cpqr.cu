@@ -424,6 +424,18 @@ __host__ __device__ constexpr int SLOT_STEP() { return RPL <= 8 ? 1 : RPL / 8; }
 
 // One step's dot products, rank-1 updates and norm downdates over the CTA's
 // columns (one warp per column), with S row slots per lane.
+// The 8-slot form (r <= 256): each warp loads its next column into registers
+// while it processes the current one (CPQR_PIPE), at 16 warps per CTA so
+// that the second set of registers fits (CPQR_NT8).  Measured against no
+// pipelining at 24 warps: 2.78 / 4.46 ms against 2.84 / 4.62 ms per launch on
+// 220 x 20000 / 200 x 50000; 20 or 14 warps with it, or 16 without it, were
+// slower.
+#ifndef CPQR_PIPE
+#define CPQR_PIPE 1
+#endif
+#ifndef CPQR_NT8
+#define CPQR_NT8 512
+#endif
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
@@ -556,6 +568,20 @@ struct CpqrDfCol {
     // issue-bound, and two prefetches per row slot cost more than the latency
     // they hid (C2: 9.42 -> 8.77 ms per step without them; the 32-slot form at
     // r = 550: 100 -> 106 ms without them).
+    // PIPE (8-slot form): the warp's next column is loaded into registers
+    // while this one is processed
+    constexpr bool PIPE = CPQR_PIPE && !VS;
+    constexpr int SP = PIPE ? S : 1;
+    float xh[SP], xl[SP];
+    if (PIPE) {
+      const int64_t cf = c0 + warp;
+#pragma unroll
+      for (int t = 0; t < SP; ++t) {
+        const int i = lane + 32 * t;
+        xh[t] = (cf < c1 && i < len) ? Wh[cf * r + j + i] : 0.f;
+        xl[t] = (cf < c1 && i < len) ? Wl[cf * r + j + i] : 0.f;
+      }
+    }
     for (int64_t c = c0 + warp; c < c1; c += NWARP) {
       if (VS && c + NWARP < c1) {
 #pragma unroll
@@ -567,17 +593,30 @@ struct CpqrDfCol {
           }
         }
       }
+      float wh[S], wl[S];
+      if (PIPE) {
+        const int64_t cn = c + NWARP;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const int i = lane + 32 * t;
+          wh[t] = xh[PIPE ? t : 0];
+          wl[t] = xl[PIPE ? t : 0];
+          xh[PIPE ? t : 0] = (cn < c1 && i < len) ? Wh[cn * r + j + i] : 0.f;
+          xl[PIPE ? t : 0] = (cn < c1 && i < len) ? Wl[cn * r + j + i] : 0.f;
+        }
+      }
       if (c == p) continue;                                  // warp-uniform
       const float2 nc = nrm2[c - cbase];
       if (nc.x < 0.f) continue;                              // already pivoted
       float* colh = Wh + c * r + j;
       float* coll = Wl + c * r + j;
-      float wh[S], wl[S];
+      if (!PIPE) {
 #pragma unroll
-      for (int t = 0; t < S; ++t) {
-        const int i = lane + 32 * t;
-        wh[t] = i < len ? colh[i] : 0.f;
-        wl[t] = i < len ? coll[i] : 0.f;
+        for (int t = 0; t < S; ++t) {
+          const int i = lane + 32 * t;
+          wh[t] = i < len ? colh[i] : 0.f;
+          wl[t] = i < len ? coll[i] : 0.f;
+        }
       }
       if (!zero) {
         // Dot2 in two independent chains (even / odd slots), then joined
@@ -1001,7 +1040,7 @@ cudaError_t launch_cpqr_df(const CpqrArgs& a, int* grid_out, cudaStream_t s) {
   (void)grid_out;
   if (a.r > 1024) return cudaErrorInvalidValue;
   const int sms = device_sm_count();
-  if (a.r <= 256) return launch_cpqr_df_t<8, 768, false>(a, sms, s);
+  if (a.r <= 256) return launch_cpqr_df_t<8, CPQR_NT8, false>(a, sms, s);
   return launch_cpqr_df_t<32, CPQR_DF_NT32, (CPQR_DF_NT32 > 256)>(a, sms, s);
 }
 
