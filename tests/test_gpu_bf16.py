@@ -94,13 +94,14 @@ CASES = [
     ("c2_like_bf16", 3000, 2000, 40, 10, 2, "inv", 1e-4),
     ("c5_like_bf16", 2048, 1024, 64, 16, 2, "sqrtgap64", 0.0),
     ("ragged_bf16", 1001, 776, 13, 5, 1, "logspace3", 1e-5),
+    ("wide_bf16", 520, 2048, 37, 11, 2, "inv", 1e-4),      # m < n
 ]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_svd_id_cur_parity_bf16(case):
     name, m, n, k, p, q, spec, noise = case
-    r = min(m, n) if spec != "inv" else min(2000, n)
+    r = min(m, n) if spec != "inv" else min(2000, m, n)
     A32 = make_matrix_np(m, n, spectrum(spec, r), noise=noise, seed=0xB000 + m, dtype="float32")
     Ab, A64 = _bf16(A32)
     seed = 0x5EED + k

@@ -41,13 +41,18 @@ CASES = [
     ("ragged_f32", 1001, 777, 13, 5, 1, "logspace3", 1e-5, "float32", "tc"),
     ("q0_p0_f32", 900, 600, 20, 0, 0, "logspace4", 0.0, "float32", "tc"),
     ("k1_f64", 300, 200, 1, 4, 2, "logspace2", 0.0, "float64", None),
+    # short and wide A (m < n): the contraction of Bt = A^T Q runs over the short side
+    ("wide_f32", 700, 1900, 30, 10, 1, "logspace3", 1e-5, "float32", "tc"),
+    ("wide_ragged_f32", 517, 2049, 37, 11, 2, "inv", 1e-4, "float32", "tc"),
+    # l = m: Q is square and B = Q^T A keeps all of A
+    ("l_eq_m_f64", 60, 500, 50, 10, 1, "logspace2", 0.0, "float64", None),
 ]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_svd_id_cur_parity(case):
     name, m, n, k, p, q, spec, noise, dtype, prec = case
-    r = min(m, n) if spec != "inv" else min(2000, n)
+    r = min(m, n) if spec != "inv" else min(2000, m, n)
     sig = spectrum(spec, r)
     A = make_matrix_np(m, n, sig, noise=noise, seed=0xA000 + m, dtype=dtype)
     A64 = A.astype(np.float64)
