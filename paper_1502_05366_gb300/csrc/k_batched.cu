@@ -187,19 +187,29 @@ cudaError_t launch_sum_batched(const BSum* tasks, int batch, cudaStream_t s) {
 
 // One CTA per problem: for each column j < k, the row of the largest |V(i, j)|
 // (lowest index on ties) decides the sign; U(:, j) and V(:, j) take it, and
-// S[j] = Sh[j].
+// S[j] = Sh[j].  All k columns at once (k <= BATCH_LMAX <= 256): thread t
+// scans column t % k over the rows t / k, t / k + R, ... (R = 256 / k rows per
+// sweep, so that a warp reads consecutive entries of a row), the R candidates
+// of a column are merged by its thread t < k, and the flips run over U and V
+// in storage order.  The order (|v| descending, row ascending) is total on
+// the non-NaN entries, so the chosen row does not depend on the merge order.
+static_assert(BATCH_LMAX <= 256, "sign_batched_kernel holds one column per thread");
 __global__ void __launch_bounds__(256) sign_batched_kernel(const BSign* __restrict__ tasks) {
   __shared__ float s_best[256];
   __shared__ int64_t s_idx[256];
   __shared__ float s_val[256];
-  __shared__ float s_sign;
+  __shared__ float s_sign[256];
   const BSign tk = tasks[blockIdx.x];
   const int tid = threadIdx.x;
-  for (int j = 0; j < tk.k; ++j) {
-    float best = -1.f, bv = 0.f;
-    int64_t bi = INT64_MAX;
-    for (int64_t i = tid; i < tk.n; i += 256) {
-      const float v = tk.V[i * tk.k + j];
+  const int k = tk.k;
+  if (k < 1 || k > 256) return;
+  const int R = 256 / k;
+  const int j = tid % k, rr = tid / k;
+  float best = -1.f, bv = 0.f;
+  int64_t bi = INT64_MAX;
+  if (rr < R) {
+    for (int64_t i = rr; i < tk.n; i += R) {
+      const float v = tk.V[i * k + j];
       const float a = fabsf(v);
       if (a > best || (a == best && i < bi)) {
         best = a;
@@ -207,33 +217,40 @@ __global__ void __launch_bounds__(256) sign_batched_kernel(const BSign* __restri
         bv = v;
       }
     }
-    s_best[tid] = best;
-    s_idx[tid] = bi;
-    s_val[tid] = bv;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (tid < o) {
-        const float b2 = s_best[tid + o];
-        const int64_t i2 = s_idx[tid + o];
-        if (b2 > s_best[tid] || (b2 == s_best[tid] && i2 < s_idx[tid])) {
-          s_best[tid] = b2;
-          s_idx[tid] = i2;
-          s_val[tid] = s_val[tid + o];
-        }
+  }
+  s_best[tid] = best;
+  s_idx[tid] = bi;
+  s_val[tid] = bv;
+  __syncthreads();
+  if (tid < k) {
+    for (int u = tid + k; u < R * k; u += k) {
+      const float b2 = s_best[u];
+      const int64_t i2 = s_idx[u];
+      if (b2 > best || (b2 == best && i2 < bi)) {
+        best = b2;
+        bi = i2;
+        bv = s_val[u];
       }
-      __syncthreads();
     }
-    if (tid == 0) {
-      s_sign = s_val[0] < 0.f ? -1.f : 1.f;
-      tk.S[j] = tk.Sh[j];
-    }
-    __syncthreads();
-    const float sg = s_sign;
-    if (sg < 0.f) {
-      for (int64_t i = tid; i < tk.m; i += 256) tk.U[i * tk.k + j] = -tk.U[i * tk.k + j];
-      for (int64_t i = tid; i < tk.n; i += 256) tk.V[i * tk.k + j] = -tk.V[i * tk.k + j];
-    }
-    __syncthreads();
+    s_sign[tid] = bv < 0.f ? -1.f : 1.f;
+    tk.S[tid] = tk.Sh[tid];
+  }
+  __syncthreads();
+  // entry e of U or V is in column e % k; the column advances by 256 % k
+  // per sweep
+  const int64_t nu = tk.m * k, nv = tk.n * k;
+  const int adv = 256 % k;
+  int c = tid % k;
+  for (int64_t e = tid; e < nu; e += 256) {
+    if (s_sign[c] < 0.f) tk.U[e] = -tk.U[e];
+    c += adv;
+    if (c >= k) c -= k;
+  }
+  c = tid % k;
+  for (int64_t e = tid; e < nv; e += 256) {
+    if (s_sign[c] < 0.f) tk.V[e] = -tk.V[e];
+    c += adv;
+    if (c >= k) c -= k;
   }
 }
 

@@ -1037,6 +1037,14 @@ __global__ void trmm_upper_kernel(int L, const T* __restrict__ R, const T* __res
 // One CTA per problem of a batch: the factor and inverse of chol_kernel
 // (shifted retries included) on the problem's l x l Gram, without the pass
 // bookkeeping of CholeskyQR2/3 (the batched path always runs two passes).
+// CHB_T = 128 threads: at l <= 128 the panel and trailing-update phases have
+// at most ~100 work items, so a fourth of the generic kernel's 256 threads
+// would idle, and at ~168 registers a thread three 128-thread CTAs fit on an
+// SM against one of 256 (the 512-problem batch in ~1.2 waves instead of 3.5).
+// The inverse keeps at most 32 elements of T per thread in registers, which
+// covers ne <= NB * l for l <= 32 * CHB_T / NB.
+constexpr int CHB_T = 128;
+static_assert(32 * CHB_T >= NB * BATCH_LMAX, "inverse register capacity of the batched Cholesky");
 __global__ void __launch_bounds__(CT) chol_batched_kernel(const BChol* __restrict__ tasks,
                                                           int* d_info) {
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -1068,7 +1076,7 @@ cudaError_t launch_chol_batched(const BChol* tasks, int batch, int lmax, int* d_
     if (e != cudaSuccess) return e;
   }
   const int tr_ = trace_begin(RSVD_TRACE_CHOL, s);
-  chol_batched_kernel<<<batch, dim3(32, CT / 32), dyn, s>>>(tasks, d_info);
+  chol_batched_kernel<<<batch, dim3(32, CHB_T / 32), dyn, s>>>(tasks, d_info);
   count_launch();
   trace_end(tr_, s);
   return cudaGetLastError();
