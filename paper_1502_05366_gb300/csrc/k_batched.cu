@@ -185,6 +185,30 @@ cudaError_t launch_sum_batched(const BSum* tasks, int batch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Negates the entries of the row-major X (cnt entries, k columns) whose column
+// sign is negative, four loads in flight per thread.  Entry e is in column
+// e % k; the column advances by 256 % k per 256-entry sweep.
+__device__ __forceinline__ void flip_columns(float* __restrict__ X, int64_t cnt, int k,
+                                             const float* s_sign) {
+  const int adv = 256 % k;
+  int c = threadIdx.x % k;
+  for (int64_t e0 = threadIdx.x; e0 < cnt; e0 += 4 * 256) {
+    float v[4];
+    bool f[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e0 + 256 * u;
+      f[u] = e < cnt && s_sign[c] < 0.f;
+      v[u] = f[u] ? X[e] : 0.f;
+      c += adv;
+      if (c >= k) c -= k;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (f[u]) X[e0 + 256 * u] = -v[u];
+  }
+}
+
 // One CTA per problem: for each column j < k, the row of the largest |V(i, j)|
 // (lowest index on ties) decides the sign; U(:, j) and V(:, j) take it, and
 // S[j] = Sh[j].  All k columns at once (k <= BATCH_LMAX <= 256): thread t
@@ -208,13 +232,23 @@ __global__ void __launch_bounds__(256) sign_batched_kernel(const BSign* __restri
   float best = -1.f, bv = 0.f;
   int64_t bi = INT64_MAX;
   if (rr < R) {
-    for (int64_t i = rr; i < tk.n; i += R) {
-      const float v = tk.V[i * k + j];
-      const float a = fabsf(v);
-      if (a > best || (a == best && i < bi)) {
-        best = a;
-        bi = i;
-        bv = v;
+    // four rows in flight, compared in increasing row order
+    for (int64_t i0 = rr; i0 < tk.n; i0 += 4 * (int64_t)R) {
+      float vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + (int64_t)u * R;
+        vv[u] = i < tk.n ? tk.V[i * k + j] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + (int64_t)u * R;
+        const float a = fabsf(vv[u]);
+        if (i < tk.n && (a > best || (a == best && i < bi))) {
+          best = a;
+          bi = i;
+          bv = vv[u];
+        }
       }
     }
   }
@@ -236,22 +270,8 @@ __global__ void __launch_bounds__(256) sign_batched_kernel(const BSign* __restri
     tk.S[tid] = tk.Sh[tid];
   }
   __syncthreads();
-  // entry e of U or V is in column e % k; the column advances by 256 % k
-  // per sweep
-  const int64_t nu = tk.m * k, nv = tk.n * k;
-  const int adv = 256 % k;
-  int c = tid % k;
-  for (int64_t e = tid; e < nu; e += 256) {
-    if (s_sign[c] < 0.f) tk.U[e] = -tk.U[e];
-    c += adv;
-    if (c >= k) c -= k;
-  }
-  c = tid % k;
-  for (int64_t e = tid; e < nv; e += 256) {
-    if (s_sign[c] < 0.f) tk.V[e] = -tk.V[e];
-    c += adv;
-    if (c >= k) c -= k;
-  }
+  flip_columns(tk.U, tk.m * k, k, s_sign);
+  flip_columns(tk.V, tk.n * k, k, s_sign);
 }
 
 cudaError_t launch_sign_batched(const BSign* tasks, int batch, cudaStream_t s) {
