@@ -56,6 +56,19 @@ def test_workspace_queries_reject_bad_sizes(lib):
     assert lib.rsvd_svd_id_cur_workspace_size(50000, 20000, 200, 20, 2, rs.F32, None) > 0
 
 
+def test_workspace_queries_wide_shapes(lib):
+    """Short, wide A (m < n) is accepted while l = k + p <= m; the CUR also
+    needs k < m (it selects k of the m rows)."""
+    import paper_1502_05366_gb300 as rs
+    for dt in (rs.F32, rs.F64):
+        assert lib.rsvd_svd_workspace_size(700, 1900, 30, 10, 1, dt, None) > 0
+        assert lib.rsvd_svd_id_cur_workspace_size(517, 2049, 37, 11, 2, dt, None) > 0
+        assert lib.rsvd_svd_workspace_size(60, 500, 50, 10, 1, dt, None) > 0      # l = m
+        assert lib.rsvd_svd_workspace_size(60, 500, 50, 11, 1, dt, None) == 0     # l > m
+        assert lib.rsvd_cur_workspace_size(60, 500, 60, 0, 1, dt, None) == 0      # k = m
+    assert lib.rsvd_svd_id_cur_workspace_size(520, 2048, 37, 11, 2, rs.BF16, None) > 0
+
+
 def test_calls_reject_invalid_arguments_without_launching(lib):
     import paper_1502_05366_gb300 as rs
     vp = ctypes.c_void_p
