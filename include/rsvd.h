@@ -123,7 +123,9 @@ int rsvd_version(void);
 
 /* -------------------------------------------------------------------------
  * Workspace queries.  Return the byte count the matching call needs, or 0
- * when the arguments are invalid.  Host only; nothing is launched.
+ * when the arguments are invalid or outside the call's supported sizes (the
+ * call itself then returns RSVD_ERR_INVALID_ARG or RSVD_ERR_UNSUPPORTED).
+ * Host only; nothing is launched.
  * ------------------------------------------------------------------------- */
 size_t rsvd_qb_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
                               const rsvd_opts* opts);
@@ -175,6 +177,11 @@ rsvd_status rsvd_svd(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, i
  * RSVD_BF16 A, with the reflector scalars in FP64.
  * Out: J  n int32, the column permutation; J[0:k] is the skeleton;
  *      T  k x (n-k) (ldt >= n-k): A(:, J[k+c]) ~ sum_i A(:, J[i]) T[i][c].
+ * Sizes: k < n and k <= 880 (the triangular solve for T holds 32 right-hand
+ * sides of k doubles in one CTA's shared memory); a larger k returns
+ * RSVD_ERR_UNSUPPORTED.  The same
+ * bound holds for every call that forms an ID or a CUR (rsvd_cur,
+ * rsvd_svd_id_cur, the tolerance calls' kmax, rsvd_id_left, rsvd_cpqr_id*).
  * ------------------------------------------------------------------------- */
 rsvd_status rsvd_id(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int dtype,
                     const void* A, int64_t lda, int32_t* J, void* T, int64_t ldt,

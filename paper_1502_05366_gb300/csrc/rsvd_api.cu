@@ -333,7 +333,7 @@ static size_t ws_query_ext(int64_t m, int64_t n, int kmax, int p, int q, int dty
                            const rsvd_opts* opts, bool tolmode, bool cur, bool left) {
   Opts o;
   if (!read_opts(opts, &o) || !base_args_ok(m, n, kmax, p, q, dtype)) return 0;
-  if (kmax >= n || (cur && kmax >= m)) return 0;
+  if (kmax >= n || (cur && kmax >= m) || kmax > UPPER_SOLVE_MAX_K) return 0;
   const double tol = tolmode ? 1.0 : 0.0;
   int32_t* jc = cur ? reinterpret_cast<int32_t*>(16) : nullptr;   // only tested for null
   auto one = [&](bool tc, auto tag) -> size_t {
@@ -517,17 +517,17 @@ size_t rsvd_svd_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dt
 }
 size_t rsvd_id_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
                               const rsvd_opts* opts) {
-  if (k >= n) return 0;
+  if (k >= n || k > UPPER_SOLVE_MAX_K) return 0;
   return ws_query(m, n, k, p, q, dtype, opts, W_ID);
 }
 size_t rsvd_cur_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
                                const rsvd_opts* opts) {
-  if (k >= n || k >= m) return 0;
+  if (k >= n || k >= m || k > UPPER_SOLVE_MAX_K) return 0;
   return ws_query(m, n, k, p, q, dtype, opts, W_ID | W_CUR);
 }
 size_t rsvd_svd_id_cur_workspace_size(int64_t m, int64_t n, int k, int p, int q, int dtype,
                                       const rsvd_opts* opts) {
-  if (k >= n || k >= m) return 0;
+  if (k >= n || k >= m || k > UPPER_SOLVE_MAX_K) return 0;
   return ws_query(m, n, k, p, q, dtype, opts, W_SVD | W_ID | W_CUR);
 }
 

@@ -69,6 +69,37 @@ def test_workspace_queries_wide_shapes(lib):
     assert lib.rsvd_svd_id_cur_workspace_size(520, 2048, 37, 11, 2, rs.BF16, None) > 0
 
 
+def test_id_and_cur_rank_limit(lib):
+    """Every call that forms an ID or a CUR takes k <= 880 (its triangular
+    solve); beyond, the workspace queries return 0 and the calls return
+    RSVD_ERR_UNSUPPORTED before launching anything.  The SVD alone has no
+    such bound."""
+    import paper_1502_05366_gb300 as rs
+    m, n, p, q = 2000, 1500, 0, 1
+    queries = (lib.rsvd_id_workspace_size, lib.rsvd_cur_workspace_size,
+               lib.rsvd_svd_id_cur_workspace_size, lib.rsvd_id_tol_workspace_size,
+               lib.rsvd_cur_tol_workspace_size, lib.rsvd_id_left_workspace_size)
+    for dt in (rs.F32, rs.F64):
+        for f in queries:
+            assert f(m, n, 880, p, q, dt, None) > 0
+            assert f(m, n, 881, p, q, dt, None) == 0
+        assert lib.rsvd_svd_workspace_size(m, n, 881, p, q, dt, None) > 0
+    assert lib.rsvd_cpqr_workspace_size(900, n, 880) > 0
+    assert lib.rsvd_cpqr_workspace_size(900, n, 881) == 0
+    vp = ctypes.c_void_p
+    fake = vp(0x1000)
+    k = 881
+    st = lib.rsvd_id(m, n, k, p, q, 1, rs.F32, fake, n, fake, fake, n - k, fake, 1 << 20, None,
+                     None, None)
+    assert st == 4
+    rank = ctypes.c_int(0)
+    st = lib.rsvd_id_tol(m, n, k, p, q, 1e-3, 1, rs.F32, fake, n, fake, fake, n - 1,
+                         ctypes.byref(rank), fake, 1 << 20, None, None, None)
+    assert st == 4
+    st = lib.rsvd_cpqr_id(900, n, k, fake, n, fake, fake, n - k, None, fake, 1 << 20, None, None)
+    assert st == 4
+
+
 def test_calls_reject_invalid_arguments_without_launching(lib):
     import paper_1502_05366_gb300 as rs
     vp = ctypes.c_void_p
