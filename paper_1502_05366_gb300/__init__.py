@@ -249,6 +249,17 @@ def _work(nbytes, device):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
+# Largest rank of a call that forms an ID or a CUR (the triangular solve for
+# T = S11^-1 S12); the library returns RSVD_ERR_UNSUPPORTED beyond it.
+ID_MAX_K = 880
+
+
+def _no_workspace(where, k):
+    """Raise for a workspace query that returned 0: RSVD_ERR_UNSUPPORTED when
+    the rank is beyond ID_MAX_K, RSVD_ERR_INVALID_ARG otherwise."""
+    raise RsvdError(4 if k > ID_MAX_K else 1, where)
+
+
 def _raise(st, where):
     if st != 0:
         raise RsvdError(st, where)
@@ -361,7 +372,7 @@ def id(A, k, p, q, seed, opts=None, check=True):  # noqa: A001 - the paper's nam
     T = torch.empty(k, max(n - k, 1), dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_id_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
     if ws == 0:
-        raise RsvdError(1, "rsvd_id_workspace_size")
+        _no_workspace("rsvd_id_workspace_size", k)
     W = _work(ws, A.device)
     info = _info(A.device)
     st = lib().rsvd_id(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(J), _ptr(T),
@@ -383,7 +394,7 @@ def cur(A, k, p, q, seed, opts=None, check=True):
     U = torch.empty(k, k, dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_cur_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
     if ws == 0:
-        raise RsvdError(1, "rsvd_cur_workspace_size")
+        _no_workspace("rsvd_cur_workspace_size", k)
     W = _work(ws, A.device)
     info = _info(A.device)
     st = lib().rsvd_cur(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(Jc), _ptr(Ir),
@@ -431,7 +442,7 @@ def id_tol(A, kmax, p, q, tol, seed, opts=None, check=True):
     T = torch.empty(kmax, n - 1, dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_id_tol_workspace_size(m, n, kmax, p, q, dt, _opts_ptr(opts))
     if ws == 0:
-        raise RsvdError(1, "rsvd_id_tol_workspace_size")
+        _no_workspace("rsvd_id_tol_workspace_size", kmax)
     W = _work(ws, A.device)
     info = _info(A.device)
     rank = ctypes.c_int(0)
@@ -456,7 +467,7 @@ def cur_tol(A, kmax, p, q, tol, seed, opts=None, check=True):
     U = torch.empty(kmax, kmax, dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_cur_tol_workspace_size(m, n, kmax, p, q, dt, _opts_ptr(opts))
     if ws == 0:
-        raise RsvdError(1, "rsvd_cur_tol_workspace_size")
+        _no_workspace("rsvd_cur_tol_workspace_size", kmax)
     W = _work(ws, A.device)
     info = _info(A.device)
     rank = ctypes.c_int(0)
@@ -480,7 +491,7 @@ def id_left(A, k, p, q, seed, opts=None, check=True):
     T = torch.empty(k, max(n - k, 1), dtype=_out_dtype(A.dtype), device=A.device)
     ws = lib().rsvd_id_left_workspace_size(m, n, k, p, q, dt, _opts_ptr(opts))
     if ws == 0:
-        raise RsvdError(1, "rsvd_id_left_workspace_size")
+        _no_workspace("rsvd_id_left_workspace_size", k)
     W = _work(ws, A.device)
     info = _info(A.device)
     st = lib().rsvd_id_left(m, n, k, p, q, seed, dt, _ptr(A), A.stride(0), _ptr(J), _ptr(T),
@@ -587,7 +598,7 @@ class Plan:
         self.Ucur = torch.empty(k, k, dtype=dtype, device=dev) if with_cur else None
         ws = lib().rsvd_svd_id_cur_workspace_size(m, n, k, p, q, self.dt, _opts_ptr(opts))
         if ws == 0:
-            raise RsvdError(1, "rsvd_svd_id_cur_workspace_size")
+            _no_workspace("rsvd_svd_id_cur_workspace_size", k)
         self.work = _work(ws, dev)
         self.info = _info(dev)
 
@@ -775,7 +786,7 @@ def cpqr_id(M, k, check=True):
     gaps = torch.empty(k, dtype=torch.float64, device=M.device)
     ws = size_fn(r, n, k)
     if ws == 0:
-        raise RsvdError(1, name.replace("_id", "") + "_workspace_size")
+        _no_workspace(name.replace("_id", "") + "_workspace_size", k)
     W = _work(ws, M.device)
     info = _info(M.device)
     st = fn(r, n, k, _ptr(M), M.stride(0), _ptr(J), _ptr(T), T.stride(0), _ptr(gaps), _ptr(W),

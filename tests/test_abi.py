@@ -98,6 +98,14 @@ def test_id_and_cur_rank_limit(lib):
     assert st == 4
     st = lib.rsvd_cpqr_id(900, n, k, fake, n, fake, fake, n - k, None, fake, 1 << 20, None, None)
     assert st == 4
+    # the binding reports a zero workspace query beyond the bound as unsupported
+    assert rs.ID_MAX_K == 880
+    with pytest.raises(rs.RsvdError) as e:
+        rs._no_workspace("rsvd_id_workspace_size", 881)
+    assert e.value.code == 4
+    with pytest.raises(rs.RsvdError) as e:
+        rs._no_workspace("rsvd_id_workspace_size", 880)
+    assert e.value.code == 1
 
 
 def test_calls_reject_invalid_arguments_without_launching(lib):
