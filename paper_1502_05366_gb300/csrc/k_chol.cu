@@ -1037,10 +1037,11 @@ __global__ void trmm_upper_kernel(int L, const T* __restrict__ R, const T* __res
 // One CTA per problem of a batch: the factor and inverse of chol_kernel
 // (shifted retries included) on the problem's l x l Gram, without the pass
 // bookkeeping of CholeskyQR2/3 (the batched path always runs two passes).
-// CHB_T = 128 threads: at l <= 128 the panel and trailing-update phases have
-// at most ~100 work items, so a fourth of the generic kernel's 256 threads
-// would idle, and at ~168 registers a thread three 128-thread CTAs fit on an
-// SM against one of 256 (the 512-problem batch in ~1.2 waves instead of 3.5).
+// CHB_T = 128 threads: at the batch's widths (l <= 128) the panel solve has at
+// most l - 32 <= 96 columns of work, so half of the generic kernel's 256
+// threads would idle there, and at ~168 registers a thread three 128-thread
+// CTAs fit on an SM against one of 256 (the 512-problem batch in ~1.2 waves
+// instead of 3.5).
 // The inverse keeps at most 32 elements of T per thread in registers, which
 // covers ne <= NB * l for l <= 32 * CHB_T / NB.
 constexpr int CHB_T = 128;
